@@ -1,0 +1,232 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This module holds no sampling arithmetic.  It only makes the inputs the
+sampler consumes: bond-dimension profiles and right-canonical complex site
+tensors (Haar-random isometries), plus the workload recipes that stand in for
+the paper's Gaussian-boson-sampling MPS data, which is not available here.
+
+Conventions
+-----------
+* Site ``k`` holds ``A_k[chi_l, d, chi_r]`` with ``chi_l = b_k`` and
+  ``chi_r = b_{k+1}``; ``b_0 = b_M = 1``.
+* Right-canonical: ``sum_s A_k[:, s, :] A_k[:, s, :]^dagger = I_{chi_l}``.
+  The tensor is the reshaped ``Q`` factor of a QR decomposition of a seeded
+  complex Gaussian ``(d*chi_r) x chi_l`` matrix,
+  ``A[a, s, b] = Q[s*chi_r + b, a]``, with the phases of ``diag(R)`` moved
+  into ``Q`` so that ``diag(R) > 0`` (the Haar-measure convention).
+* Skew: before the QR, the Gaussian rows of physical index ``s`` are scaled
+  by ``exp(-s / skew)``, so low outcomes dominate, as photon-number
+  distributions do in Gaussian boson sampling (Sec. 2.1, Sec. 4.2).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "bond_dims",
+    "isometry",
+    "mps_tensors",
+    "product_state",
+    "ghz_chain",
+    "Workload",
+    "WORKLOADS",
+]
+
+
+def bond_dims(M: int, d: int, chi: int) -> list[int]:
+    """Bond profile ``b_k = min(d^k, d^(M-k), chi)`` for ``k = 0..M``.
+
+    The cap at the chain ends is the exact bond dimension an open chain of
+    ``M`` sites can carry (Sec. 2.2: the bond dimension bounded by the
+    Hilbert-space size of either side).
+    """
+    if M < 1 or d < 2 or chi < 1:
+        raise ValueError("need M >= 1, d >= 2, chi >= 1")
+    out = []
+    for k in range(M + 1):
+        left = 1
+        for _ in range(k):
+            left = min(left * d, chi)
+        right = 1
+        for _ in range(M - k):
+            right = min(right * d, chi)
+        out.append(min(left, right, chi))
+    return out
+
+
+def _gaussian(seed: int, rows: int, cols: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    g = rng.standard_normal((rows, cols, 2))
+    return (g[..., 0] + 1j * g[..., 1]) / math.sqrt(2.0)
+
+
+def _haar_from_gaussian(g, chi_l: int, d: int, chi_r: int, skew: float | None):
+    """QR of the (optionally skewed) Gaussian, reshaped to ``A[chi_l, d, chi_r]``.
+
+    Works for numpy arrays and torch tensors (CPU or CUDA) alike.
+    """
+    is_np = isinstance(g, np.ndarray)
+    if skew:
+        w = np.exp(-np.arange(d) / float(skew)).repeat(chi_r)
+        if is_np:
+            g = g * w[:, None]
+        else:
+            import torch
+
+            g = g * torch.as_tensor(w, dtype=g.real.dtype, device=g.device)[:, None]
+    if is_np:
+        q, r = np.linalg.qr(g, mode="reduced")
+        dg = np.diagonal(r)
+        ph = dg / np.abs(dg)
+        q = q * ph[None, :]
+        # A[a, s, b] = Q[s*chi_r + b, a]
+        return np.ascontiguousarray(q.T.reshape(chi_l, d, chi_r))
+    import torch
+
+    q, r = torch.linalg.qr(g, mode="reduced")
+    dg = torch.diagonal(r)
+    ph = dg / dg.abs()
+    q = q * ph[None, :]
+    return q.transpose(0, 1).reshape(chi_l, d, chi_r).contiguous()
+
+
+def isometry(seed: int, chi_l: int, d: int, chi_r: int, skew: float | None = None,
+             dtype=np.complex128, device: str | None = None):
+    """One right-canonical site tensor ``A[chi_l, d, chi_r]`` (complex).
+
+    ``device=None`` returns a numpy array (complex128 arithmetic, then cast to
+    ``dtype``).  ``device='cuda'`` (or any torch device string) draws the
+    Gaussian with a seeded torch generator on that device and returns a torch
+    complex64 tensor there; that route exists for the large workloads whose
+    QR would take minutes on the host.
+    """
+    if d * chi_r < chi_l:
+        raise ValueError("an isometry needs d*chi_r >= chi_l")
+    if device is None:
+        g = _gaussian(seed, d * chi_r, chi_l)
+        return _haar_from_gaussian(g, chi_l, d, chi_r, skew).astype(dtype, copy=False)
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    re = torch.randn((d * chi_r, chi_l), generator=gen, device=device, dtype=torch.float32)
+    im = torch.randn((d * chi_r, chi_l), generator=gen, device=device, dtype=torch.float32)
+    g = torch.complex(re, im) * (1.0 / math.sqrt(2.0))
+    return _haar_from_gaussian(g, chi_l, d, chi_r, skew)
+
+
+def mps_tensors(M: int, d: int, chi: int, base_seed: int = 1234, skew: float | None = None,
+                pool: int | None = None, dtype=np.complex128, device: str | None = None,
+                bonds: list[int] | None = None):
+    """Site tensors of a random right-canonical MPS.
+
+    Site ``k`` is drawn from seed ``base_seed + k``.  With ``pool=P``, every
+    interior site (``b_k = b_{k+1} = chi``) reuses ``pool[k mod P]`` whose
+    seed is ``base_seed + 1_000_000 + (k mod P)``; end sites keep their own
+    seed.  Returns ``(bond_dims, tensors, site_to_tensor)``, where
+    ``site_to_tensor[k]`` indexes ``tensors`` (identity without a pool).
+    """
+    b = list(bonds) if bonds is not None else bond_dims(M, d, chi)
+    tensors = []
+    index = []
+    pool_slot: dict[int, int] = {}
+    for k in range(M):
+        cl, cr = b[k], b[k + 1]
+        if pool and cl == chi and cr == chi:
+            j = k % pool
+            if j not in pool_slot:
+                pool_slot[j] = len(tensors)
+                tensors.append(isometry(base_seed + 1_000_000 + j, cl, d, cr, skew, dtype, device))
+            index.append(pool_slot[j])
+        else:
+            index.append(len(tensors))
+            tensors.append(isometry(base_seed + k, cl, d, cr, skew, dtype, device))
+    return b, tensors, index
+
+
+def product_state(M: int, probs: np.ndarray, phases_seed: int = 7) -> tuple[list[int], list[np.ndarray]]:
+    """A bond-dimension-1 MPS whose site ``k`` has outcome law ``probs[k]``.
+
+    ``A_k[0, s, 0] = sqrt(probs[k, s]) * exp(i phi)``: right-canonical because
+    ``sum_s |A_k[0, s, 0]|^2 = 1``.  Its outcomes are independent categorical
+    draws, the textbook special case of MPS sampling.
+    """
+    probs = np.asarray(probs, dtype=np.float64)
+    M2, d = probs.shape
+    assert M2 == M
+    rng = np.random.Generator(np.random.PCG64(phases_seed))
+    out = []
+    for k in range(M):
+        ph = np.exp(2j * np.pi * rng.random(d))
+        out.append((np.sqrt(probs[k]) * ph).reshape(1, d, 1).astype(np.complex128))
+    return [1] * (M + 1), out
+
+
+def ghz_chain(M: int, d: int) -> tuple[list[int], list[np.ndarray]]:
+    """The GHZ state ``(|00..0> + |11..1> + ... + |d-1..d-1>)/sqrt(d)`` as an MPS.
+
+    Right-canonical form with bonds ``1, d, d, ..., d, 1``:
+    ``A_0[0, s, s] = 1/sqrt(d)``, ``A_k[s, s, s] = 1`` for interior ``k`` and
+    ``A_{M-1}[s, s, 0] = 1``.  Every sample has all outcomes equal and
+    ``P(s, s, ..., s) = 1/d``.
+    """
+    assert M >= 2
+    b = [1] + [d] * (M - 1) + [1]
+    ts = []
+    a0 = np.zeros((1, d, d), np.complex128)
+    for s in range(d):
+        a0[0, s, s] = 1.0 / math.sqrt(d)
+    ts.append(a0)
+    for _ in range(1, M - 1):
+        a = np.zeros((d, d, d), np.complex128)
+        for s in range(d):
+            a[s, s, s] = 1.0
+        ts.append(a)
+    al = np.zeros((d, d, 1), np.complex128)
+    for s in range(d):
+        al[s, s, 0] = 1.0
+    ts.append(al)
+    return b, ts
+
+
+# ---------------------------------------------------------------------------
+# Workload recipes: synthetic stand-ins for the paper's GBS MPS data
+# (Sec. 4.2, Tables 1-3: d = 3..4, chi up to 10^4, M up to 8176).
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    M: int
+    d: int
+    chi: int
+    N: int
+    skew: float | None
+    pool: int | None = None
+    base_seed: int = 1234
+    sampler_seed: int = 42
+    note: str = ""
+    extra: dict = field(default_factory=dict)
+
+    def bonds(self) -> list[int]:
+        return bond_dims(self.M, self.d, self.chi)
+
+    def flops_per_sample(self) -> float:
+        """Algorithmic real flops of the complex contraction per sample (all sites)."""
+        b = self.bonds()
+        return float(sum(8 * b[k] * self.d * b[k + 1] for k in range(self.M)))
+
+
+WORKLOADS = {
+    "tiny": Workload("tiny", M=12, d=3, chi=16, N=10_000, skew=None,
+                     note="M=12 d=3 chi<=16 unskewed Haar, N=1e4; brute force over 3^12"),
+    "plain": Workload("plain", M=256, d=4, chi=256, N=1 << 17, skew=1.5,
+                      note="M=256 d=4 chi=256 skew exp(-s/1.5), N=2^17, complex64 resident"),
+    "precision": Workload("precision", M=1024, d=4, chi=1024, N=1 << 20, skew=1.5,
+                          note="M=1024 d=4 chi=1024 skew exp(-s/1.5), N=2^20, BF16 split"),
+    "streaming": Workload("streaming", M=2048, d=3, chi=10_000, N=1 << 16, skew=1.5, pool=16,
+                          note="M=2048 d=3 chi=1e4, pool of 16 interior isometries, host-streamed BF16, N=2^16"),
+}

@@ -1,0 +1,218 @@
+"""FP64 CPU oracle for perfect MPS sampling -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg use this package.  The product library (``paper_2512_20064_gb300``) never
+imports it, and the two share no code: the C file ``oracle.c`` restates the
+method (Sec. 2.2 sampling workflow, Algorithm 2, Sec. 3.3.1 per-sample
+scaling) in complex double precision with plain loops, and implements its own
+Philox4x32-10.
+
+Functions
+---------
+``sample``        rows ``n0 .. n0+N-1``: outcomes, log-probabilities and
+                  (optionally) every conditional distribution.
+``replay``        teacher-forced replay: follow given outcomes and report the
+                  oracle's conditionals, its own draw and the CDF margin.
+``born_logprob``  ``log |A_0[s_0] ... A_{M-1}[s_{M-1}]|^2`` (plain definition).
+``brute_force``   ``|psi(s)|^2`` for all ``d^M`` configurations.
+``philox``/``uniform``  the counter-based generator.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``oracle.c`` with gcc (-O2, OpenMP).  Returns the .so path."""
+    src = os.path.join(_HERE, "oracle.c")
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def build_variant(src_text: str, out_path: str) -> str:
+    """Compile a given oracle source text to ``out_path`` (used by the
+    mutation tests, which plant a mistake in a copy of the oracle)."""
+    c = out_path[:-3] + ".c"
+    with open(c, "w") as f:
+        f.write(src_text)
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", out_path, c, "-lm"],
+                   check=True)
+    return out_path
+
+
+def _bind(lib):
+    P = ctypes.POINTER
+    lib.orc_philox4x32_10.argtypes = [P(ctypes.c_uint32), P(ctypes.c_uint32), P(ctypes.c_uint32)]
+    lib.orc_philox4x32_10.restype = None
+    lib.orc_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+    lib.orc_uniform.restype = ctypes.c_double
+    lib.orc_sample.argtypes = [
+        ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p), ctypes.c_uint64, ctypes.c_uint32,
+        ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+    lib.orc_sample.restype = ctypes.c_int
+    lib.orc_born_logprob.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p),
+                                     ctypes.c_void_p]
+    lib.orc_born_logprob.restype = ctypes.c_double
+    lib.orc_brute_force.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p),
+                                    ctypes.c_void_p]
+    lib.orc_brute_force.restype = ctypes.c_int
+    lib.orc_num_threads.argtypes = []
+    lib.orc_num_threads.restype = ctypes.c_int
+    return lib
+
+
+def load_variant(path: str):
+    """Load an oracle shared object built by :func:`build_variant`."""
+    return _bind(ctypes.CDLL(path))
+
+
+def _load(lib=None):
+    global _lib
+    if lib is not None:
+        return lib
+    with _lock:
+        if _lib is None:
+            _lib = _bind(ctypes.CDLL(build()))
+        return _lib
+
+
+class _Chain:
+    """Keeps complex128 copies of the site tensors alive for one C call."""
+
+    def __init__(self, bonds, tensors, site_index=None):
+        self.M = len(bonds) - 1
+        self.bonds = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32))
+        idx = list(range(self.M)) if site_index is None else list(site_index)
+        if len(idx) != self.M:
+            raise ValueError("site_index must have M entries")
+        self.d = None
+        conv = {}
+        arrs = []
+        for k in range(self.M):
+            j = idx[k]
+            if j not in conv:
+                conv[j] = np.ascontiguousarray(np.asarray(tensors[j], dtype=np.complex128))
+            A = conv[j]
+            if A.ndim != 3 or A.shape[0] != bonds[k] or A.shape[2] != bonds[k + 1]:
+                raise ValueError(f"site {k}: shape {A.shape} does not match bonds ({bonds[k]}, {bonds[k+1]})")
+            if self.d is None:
+                self.d = A.shape[1]
+            elif A.shape[1] != self.d:
+                raise ValueError("all sites must share d")
+            arrs.append(A)
+        self._keep = arrs
+        self.ptrs = (ctypes.c_void_p * self.M)(*[a.ctypes.data for a in arrs])
+
+    def bond_ptr(self):
+        return self.bonds.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _vp(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def philox(ctr, key, lib=None) -> np.ndarray:
+    lib = _load(lib)
+    c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(x) & 0xFFFFFFFF for x in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib.orc_philox4x32_10(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def uniform(seed: int, n: int, k: int, job: int = 0, lib=None) -> float:
+    return float(_load(lib).orc_uniform(seed, n, k, job))
+
+
+def num_threads(lib=None) -> int:
+    return int(_load(lib).orc_num_threads())
+
+
+def sample(bonds, tensors, seed: int, N: int, n0: int = 0, job: int = 0, site_index=None,
+           want_probs: bool = False, nthreads: int = 0, lib=None):
+    """Sample rows ``n0..n0+N-1``.  Returns ``(samples[N,M] u8, logprob[N] f64[, probs[N,M,d]])``."""
+    lib = _load(lib)
+    ch = _Chain(bonds, tensors, site_index)
+    M, d = ch.M, ch.d
+    smp = np.zeros((N, M), np.uint8)
+    lp = np.zeros(N, np.float64)
+    pr = np.zeros((N, M, d), np.float64) if want_probs else None
+    rc = lib.orc_sample(M, d, ch.bond_ptr(), ch.ptrs, seed, job, n0, N, _vp(smp), _vp(lp), _vp(pr),
+                        None, None, None, nthreads)
+    if rc != 0:
+        raise RuntimeError(f"orc_sample failed ({rc})")
+    return (smp, lp, pr) if want_probs else (smp, lp)
+
+
+def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=None, nthreads: int = 0, lib=None):
+    """Teacher-forced replay of rows ``rows`` (sample indices) along ``forced[R, M]``.
+
+    Returns a dict with ``probs[R,M,d]`` (the oracle's conditionals along the
+    forced path), ``own[R,M]`` (the outcome the oracle's own uniform picks at
+    each step), ``margin[R,M]`` (distance of that uniform to the nearest
+    interior CDF boundary) and ``logprob[R]`` (sum of log conditionals of the
+    forced outcomes).
+    """
+    lib = _load(lib)
+    ch = _Chain(bonds, tensors, site_index)
+    M, d = ch.M, ch.d
+    rows = np.asarray(rows, dtype=np.int64)
+    forced = np.ascontiguousarray(np.asarray(forced, dtype=np.uint8))
+    R = rows.shape[0]
+    assert forced.shape == (R, M)
+    probs = np.zeros((R, M, d), np.float64)
+    own = np.zeros((R, M), np.uint8)
+    margin = np.zeros((R, M), np.float64)
+    lp = np.zeros(R, np.float64)
+    # rows are arbitrary indices: run each contiguous run of indices as one call
+    i = 0
+    while i < R:
+        j = i + 1
+        while j < R and rows[j] == rows[j - 1] + 1:
+            j += 1
+        rc = lib.orc_sample(M, d, ch.bond_ptr(), ch.ptrs, seed, job, int(rows[i]), j - i, None,
+                            _vp(lp[i:j]), _vp(probs[i:j]), _vp(forced[i:j]), _vp(own[i:j]),
+                            _vp(margin[i:j]), nthreads)
+        if rc != 0:
+            raise RuntimeError(f"orc_sample (replay) failed ({rc})")
+        i = j
+    return {"probs": probs, "own": own, "margin": margin, "logprob": lp}
+
+
+def born_logprob(bonds, tensors, config, site_index=None, lib=None) -> float:
+    lib = _load(lib)
+    ch = _Chain(bonds, tensors, site_index)
+    cfg = np.ascontiguousarray(np.asarray(config, dtype=np.uint8))
+    assert cfg.shape == (ch.M,)
+    return float(lib.orc_born_logprob(ch.M, ch.d, ch.bond_ptr(), ch.ptrs, _vp(cfg)))
+
+
+def brute_force(bonds, tensors, site_index=None, lib=None) -> np.ndarray:
+    """``|psi(s)|^2`` for all configurations, shape ``(d,)*M`` (s_0 first axis)."""
+    lib = _load(lib)
+    ch = _Chain(bonds, tensors, site_index)
+    M, d = ch.M, ch.d
+    if d ** M > 1 << 26:
+        raise ValueError("too many configurations for brute force")
+    out = np.zeros(d ** M, np.float64)
+    rc = lib.orc_brute_force(M, d, ch.bond_ptr(), ch.ptrs, _vp(out))
+    if rc != 0:
+        raise RuntimeError(f"orc_brute_force failed ({rc})")
+    return out.reshape((d,) * M)

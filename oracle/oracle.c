@@ -1,0 +1,337 @@
+/*
+ * FP64 CPU oracle for perfect sampling from a right-canonical complex MPS.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the sampler computes.  It is used by the tests, the
+ * smoke check and the benchmark's CPU-baseline leg; the product library never
+ * links, loads or calls it, and it shares no code with the CUDA path.
+ *
+ * Method (Sec. 2.2, Fig. 1; Algorithm 2 "Measurement"; Sec. 3.3.1 per-sample
+ * scaling), written out exactly in complex double precision:
+ *
+ *   v_0 = [1]                                   (left boundary, b_0 = 1)
+ *   for k = 0 .. M-1:
+ *     y_s[b] = sum_a v_k[a] A_k[a, s, b]         contraction, s < d, b < chi_r
+ *     w_s    = sum_b |y_s[b]|^2                   unnormalised probabilities
+ *     C_s    = w_0 + ... + w_s   (in s order)     cumulative sum, Z = C_{d-1}
+ *     u      = U(seed, n, k, job) in (0,1)        Philox4x32-10 uniform
+ *     s*     = #{ s < d-1 : C_s < u Z }           "sum(threshold > cdf)"
+ *     logp  += log(w_{s*}) - log(Z)
+ *     v_{k+1} = y_{s*} / sqrt(w_{s*})             exact per-sample rescaling
+ *
+ * Readings of the paper taken here (the paper's Vidal-form line
+ * "probs = dot(temp, Lambda)" is read as the squared norm; the garbled slice
+ * "temp[range(N2), :, :samples]" as selecting block s*; the random threshold
+ * as a (0,1) uniform from a counter-based generator keyed by (seed, n, k)).
+ *
+ * Site tensors are passed as interleaved complex doubles, A_k[a][s][b]
+ * row-major with shape (chi_l = bond[k], d, chi_r = bond[k+1]).
+ *
+ * Parity pins for every function are in tests/test_oracle_pins.py: brute
+ * force over all d^M configurations, closed forms, special cases (product
+ * state, GHZ chain), Philox known-answer vectors and marginal statistics.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as  */
+/* easy as 1, 2, 3", SC'11).  Ten rounds of the 4x32 bijection with the      */
+/* published multipliers and Weyl key increments.                            */
+/* ------------------------------------------------------------------------ */
+#define ORC_PHILOX_M0 0xD2511F53u
+#define ORC_PHILOX_M1 0xCD9E8D57u
+#define ORC_PHILOX_W0 0x9E3779B9u
+#define ORC_PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)ORC_PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)ORC_PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += ORC_PHILOX_W0;
+        k1 += ORC_PHILOX_W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The uniform of sample n at site k: key = (seed lo, seed hi), counter =
+ * (n lo, n hi, k, job); u = (53 bits of (x0, x1) + 1/2) * 2^-53, in (0, 1). */
+double orc_uniform(uint64_t seed, uint64_t n, uint32_t k, uint32_t job)
+{
+    uint32_t ctr[4] = {(uint32_t)n, (uint32_t)(n >> 32), k, job};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t x[4];
+    orc_philox4x32_10(ctr, key, x);
+    uint64_t bits = ((uint64_t)x[0] << 21) | (uint64_t)(x[1] >> 11);
+    return ((double)bits + 0.5) * 0x1p-53;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One site of one sample, complex double.                                   */
+/* ------------------------------------------------------------------------ */
+
+/* y[s*chi_r + b] (interleaved re, im) = sum_a v[a] A[a, s, b].  Plain loops. */
+static void orc_contract(const double *v, int chi_l, int d, int chi_r, const double *A, double *y)
+{
+    const int cols = d * chi_r;
+    for (int c = 0; c < cols; ++c) {
+        y[2 * c] = 0.0;
+        y[2 * c + 1] = 0.0;
+    }
+    for (int a = 0; a < chi_l; ++a) {
+        const double vr = v[2 * a], vi = v[2 * a + 1];
+        const double *row = A + (size_t)2 * a * cols;
+        for (int c = 0; c < cols; ++c) {
+            const double ar = row[2 * c], ai = row[2 * c + 1];
+            y[2 * c] += vr * ar - vi * ai;
+            y[2 * c + 1] += vr * ai + vi * ar;
+        }
+    }
+}
+
+/* w_s = sum_b |y_s[b]|^2 */
+static void orc_block_norms(const double *y, int d, int chi_r, double *w)
+{
+    for (int s = 0; s < d; ++s) {
+        double acc = 0.0;
+        for (int b = 0; b < chi_r; ++b) {
+            const double re = y[2 * (s * chi_r + b)], im = y[2 * (s * chi_r + b) + 1];
+            acc += re * re + im * im;
+        }
+        w[s] = acc;
+    }
+}
+
+/* s* = #{ s < d-1 : C_s < u Z } with C the cumulative sum of w in s order. */
+static int orc_draw(const double *w, int d, double u, double *Z_out, double *margin_out)
+{
+    double C[256];
+    double acc = 0.0;
+    for (int s = 0; s < d; ++s) {
+        acc += w[s];
+        C[s] = acc;
+    }
+    const double Z = C[d - 1];
+    const double t = u * Z;
+    int cnt = 0;
+    double margin = INFINITY;
+    for (int s = 0; s < d - 1; ++s) {
+        if (C[s] < t) cnt++;
+        double dist = fabs(t - C[s]) / Z;
+        if (dist < margin) margin = dist;
+    }
+    if (Z_out) *Z_out = Z;
+    if (margin_out) *margin_out = margin;
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sampling                                                                  */
+/* ------------------------------------------------------------------------ */
+
+static int max_bond(int M, const int *bond)
+{
+    int m = 1;
+    for (int k = 0; k <= M; ++k)
+        if (bond[k] > m) m = bond[k];
+    return m;
+}
+
+/*
+ * Sample rows n = n0 .. n0+N-1.  samples[i*M + k] = outcome of row n0+i at
+ * site k; logprob[i] = sum_k log p(s_k | s_<k).  probs (nullable) receives
+ * the normalised conditionals p(s | prefix) = w_s / Z as [i][k][s].
+ * forced (nullable, [N][M]): teacher-forced replay; the row follows the given
+ * outcomes instead of its own draws, while own_draw (nullable, [N][M]) still
+ * records the outcome its own uniform would have picked and margin
+ * (nullable, [N][M]) the distance min_s |u - C_s/Z| of that uniform to the
+ * nearest interior CDF boundary.  Returns 0, or -1 on bad arguments.
+ */
+int orc_sample(int M, int d, const int *bond, const double *const *A, uint64_t seed, uint32_t job,
+               int64_t n0, int64_t N, uint8_t *samples, double *logprob, double *probs,
+               const uint8_t *forced, uint8_t *own_draw, double *margin, int nthreads)
+{
+    if (M < 1 || d < 2 || d > 255 || N < 0 || !bond || !A) return -1;
+    if (bond[0] != 1 || bond[M] != 1) return -1;
+    const int chi = max_bond(M, bond);
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel reduction(| : bad)
+#endif
+    {
+        double *v = (double *)malloc(sizeof(double) * 2 * (size_t)chi);
+        double *y = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi);
+        double *w = (double *)malloc(sizeof(double) * (size_t)d);
+        if (!v || !y || !w) bad = 1;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+        for (int64_t i = 0; i < N; ++i) {
+            if (bad) continue;
+            const uint64_t n = (uint64_t)(n0 + i);
+            v[0] = 1.0;
+            v[1] = 0.0;
+            double lp = 0.0;
+            for (int k = 0; k < M; ++k) {
+                const int cl = bond[k], cr = bond[k + 1];
+                orc_contract(v, cl, d, cr, A[k], y);
+                orc_block_norms(y, d, cr, w);
+                const double u = orc_uniform(seed, n, (uint32_t)k, job);
+                double Z, mg;
+                const int mine = orc_draw(w, d, u, &Z, &mg);
+                const int s = forced ? (int)forced[i * M + k] : mine;
+                if (own_draw) own_draw[i * M + k] = (uint8_t)mine;
+                if (margin) margin[i * M + k] = mg;
+                if (probs)
+                    for (int t = 0; t < d; ++t) probs[((size_t)i * M + k) * d + t] = w[t] / Z;
+                if (s < 0 || s >= d || !(w[s] > 0.0)) {
+                    /* a forced outcome of zero probability: the replay stops */
+                    lp = -INFINITY;
+                    if (samples) samples[i * M + k] = (uint8_t)s;
+                    for (int kk = k + 1; kk < M; ++kk) {
+                        if (samples) samples[i * M + kk] = 0;
+                        if (own_draw) own_draw[i * M + kk] = 0;
+                        if (margin) margin[i * M + kk] = INFINITY;
+                        if (probs)
+                            for (int t = 0; t < d; ++t) probs[((size_t)i * M + kk) * d + t] = NAN;
+                    }
+                    break;
+                }
+                if (samples) samples[i * M + k] = (uint8_t)s;
+                lp += log(w[s]) - log(Z);
+                const double inv = 1.0 / sqrt(w[s]);
+                for (int b = 0; b < cr; ++b) {
+                    v[2 * b] = y[2 * (s * cr + b)] * inv;
+                    v[2 * b + 1] = y[2 * (s * cr + b) + 1] * inv;
+                }
+            }
+            if (logprob) logprob[i] = lp;
+        }
+        free(v);
+        free(y);
+        free(w);
+    }
+    return bad ? -2 : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Closed forms used as pins                                                 */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * log |psi(s)|^2 = log |A_0[s_0] A_1[s_1] ... A_{M-1}[s_{M-1}]|^2 for one
+ * configuration: the Born probability of the plain definition, by a left to
+ * right chain of vector-matrix products with the running norm factored out
+ * (log-norm tracking) so that long chains do not underflow.
+ */
+double orc_born_logprob(int M, int d, const int *bond, const double *const *A, const uint8_t *config)
+{
+    const int chi = max_bond(M, bond);
+    double *r = (double *)calloc(2 * (size_t)chi, sizeof(double));
+    double *t = (double *)calloc(2 * (size_t)chi, sizeof(double));
+    if (!r || !t) {
+        free(r);
+        free(t);
+        return NAN;
+    }
+    r[0] = 1.0;
+    double lognorm = 0.0;
+    for (int k = 0; k < M; ++k) {
+        const int cl = bond[k], cr = bond[k + 1], s = config[k];
+        for (int b = 0; b < cr; ++b) {
+            double re = 0.0, im = 0.0;
+            for (int a = 0; a < cl; ++a) {
+                const double *e = A[k] + 2 * (((size_t)a * d + s) * cr + b);
+                re += r[2 * a] * e[0] - r[2 * a + 1] * e[1];
+                im += r[2 * a] * e[1] + r[2 * a + 1] * e[0];
+            }
+            t[2 * b] = re;
+            t[2 * b + 1] = im;
+        }
+        double nrm2 = 0.0;
+        for (int b = 0; b < cr; ++b) nrm2 += t[2 * b] * t[2 * b] + t[2 * b + 1] * t[2 * b + 1];
+        if (!(nrm2 > 0.0)) {
+            free(r);
+            free(t);
+            return -INFINITY;
+        }
+        lognorm += log(nrm2);
+        const double inv = 1.0 / sqrt(nrm2);
+        for (int b = 0; b < cr; ++b) {
+            r[2 * b] = t[2 * b] * inv;
+            r[2 * b + 1] = t[2 * b + 1] * inv;
+        }
+    }
+    free(r);
+    free(t);
+    return lognorm;
+}
+
+/*
+ * Brute force: |psi(s)|^2 for every configuration, index = sum_k s_k d^(M-1-k)
+ * (s_0 most significant).  Depth-first over prefixes so that each prefix
+ * vector A_0[s_0]...A_k[s_k] is formed once; no normalisation, no sampling.
+ * out has d^M entries.
+ */
+static void orc_bf_rec(int M, int d, const int *bond, const double *const *A, int k, const double *pref,
+                       size_t index, double *out, double *scratch)
+{
+    const int cl = bond[k], cr = bond[k + 1];
+    double *next = scratch; /* 2*cr doubles for this depth */
+    for (int s = 0; s < d; ++s) {
+        for (int b = 0; b < cr; ++b) {
+            double re = 0.0, im = 0.0;
+            for (int a = 0; a < cl; ++a) {
+                const double *e = A[k] + 2 * (((size_t)a * d + s) * cr + b);
+                re += pref[2 * a] * e[0] - pref[2 * a + 1] * e[1];
+                im += pref[2 * a] * e[1] + pref[2 * a + 1] * e[0];
+            }
+            next[2 * b] = re;
+            next[2 * b + 1] = im;
+        }
+        const size_t idx = index * (size_t)d + (size_t)s;
+        if (k == M - 1) {
+            out[idx] = next[0] * next[0] + next[1] * next[1];
+        } else {
+            orc_bf_rec(M, d, bond, A, k + 1, next, idx, out, scratch + 2 * (size_t)cr);
+        }
+    }
+}
+
+int orc_brute_force(int M, int d, const int *bond, const double *const *A, double *out)
+{
+    if (M < 1 || M > 24 || d < 2) return -1;
+    int total_scratch = 0;
+    for (int k = 0; k <= M; ++k) total_scratch += 2 * bond[k];
+    double *scratch = (double *)calloc((size_t)total_scratch + 2, sizeof(double));
+    if (!scratch) return -2;
+    double one[2] = {1.0, 0.0};
+    orc_bf_rec(M, d, bond, A, 0, one, 0, out, scratch);
+    free(scratch);
+    return 0;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,54 @@
+"""What a low-precision store of a site tensor represents -- TEST INFRASTRUCTURE.
+
+The low-precision device paths keep site tensors in bfloat16 (Sec. 3.3.2:
+tensors kept in a 16-bit format for storage and transfer).  To measure their
+arithmetic error rather than their storage error, the oracle is also run on
+the tensors those stores represent.  This module restates the storage format
+from its definition (IEEE-754 binary32 -> bfloat16, round to nearest, ties to
+even) with integer operations on the float32 bit patterns; it shares nothing
+with the CUDA path.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round float32 values to the nearest bfloat16 (ties to even), returned as float32.
+
+    NaN inputs are not expected (site tensors are finite).
+    """
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    u = x.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).reshape(x.shape)
+
+
+def bf16_split(x):
+    """``hi = bf16(x)``, ``lo = bf16(x - hi)``, the difference taken in float32."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    hi = bf16_round(x)
+    lo = bf16_round((x - hi).astype(np.float32))
+    return hi, lo
+
+
+def dequant_bf16(A, planes: int = 1) -> np.ndarray:
+    """The complex128 tensor that a BF16 store of ``A`` represents.
+
+    ``planes=1``: real and imaginary parts each cast to float32, then rounded to
+    bfloat16.  ``planes=2``: each stored as a ``hi + lo`` bfloat16 pair.
+    """
+    A = np.asarray(A)
+    re = np.asarray(A.real, dtype=np.float32)
+    im = np.asarray(A.imag, dtype=np.float32)
+    if planes == 1:
+        return bf16_round(re).astype(np.float64) + 1j * bf16_round(im).astype(np.float64)
+    rh, rl = bf16_split(re)
+    ih, il = bf16_split(im)
+    return (rh.astype(np.float64) + rl.astype(np.float64)) + 1j * (ih.astype(np.float64) + il.astype(np.float64))
+
+
+def complex64_of(A) -> np.ndarray:
+    """The complex128 tensor that a complex64 store of ``A`` represents."""
+    return np.asarray(A).astype(np.complex64).astype(np.complex128)

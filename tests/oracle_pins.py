@@ -1,0 +1,222 @@
+"""Pins for the FP64 oracle: checks against facts fixed by the paper and the mathematics.
+
+Each ``pin_*`` function runs one check against an oracle library (the built
+one by default, or a mutated copy) and returns ``(ok, detail)``.  The tests in
+``test_oracle_pins.py`` require every pin to pass on the real oracle, and
+``test_oracle_mutants.py`` plants mistakes in copies of the oracle and requires
+that some pin fails for each.
+
+What pins what
+--------------
+* ``pin_philox_kat``      -- Philox4x32-10 known-answer vectors (golden file).
+* ``pin_uniform_packing`` -- key/counter packing and the 53-bit mapping, from the
+  same vectors, computed here from the golden numbers (not from the oracle).
+* ``pin_brute_force_normalised`` -- sum of |psi(s)|^2 over all d^M is 1 for a
+  right-canonical MPS (norm of a normalised state).
+* ``pin_conditionals_vs_brute`` -- each conditional p(s | prefix) the sampler
+  reports equals P(prefix, s) / P(prefix) from brute-force summation.
+* ``pin_logprob_vs_brute`` -- exp(sum of log conditionals) equals the brute-force
+  Born probability of the sampled configuration.
+* ``pin_product_state``   -- chi = 1: the conditionals are the given per-site laws
+  and each outcome is the inverse-CDF draw of that law at the sample's uniform.
+* ``pin_ghz``             -- GHZ chain: perfectly correlated outcomes, log p = -log d.
+* ``pin_scale_invariance`` -- multiplying every site tensor by a constant changes
+  neither the outcomes nor the log-probabilities (the normalisation by Z).
+* ``pin_long_chain``      -- 3000 sites: log-probabilities stay finite and equal the
+  closed-form log |A_0[s_0] ... A_{M-1}[s_{M-1}]|^2 (per-sample rescaling).
+* ``pin_marginals``       -- single-site and nearest-pair marginals of 10^5 samples
+  within 5 sigma of brute force (in test_oracle_pins only; slow for mutants).
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+import gen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_kat():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            v = [int(x, 16) for x in line.split()]
+            rows.append((v[0:4], v[4:6], v[6:10]))
+    return rows
+
+
+def _tiny():
+    w = gen.WORKLOADS["tiny"]
+    b, ts, _ = gen.mps_tensors(w.M, w.d, w.chi, base_seed=w.base_seed, skew=w.skew)
+    return b, ts
+
+
+def pin_philox_kat(lib=None):
+    for ctr, key, want in read_kat():
+        got = [int(x) for x in oracle.philox(ctr, key, lib=lib)]
+        if got != want:
+            return False, f"philox({ctr},{key}) = {got} != {want}"
+    return True, ""
+
+
+def pin_uniform_packing(lib=None):
+    """seed = key1:key0, n = ctr1:ctr0, k = ctr2, job = ctr3; u = (x0<<21 | x1>>11) + 1/2 over 2^53."""
+    for ctr, key, want in read_kat():
+        seed = (key[1] << 32) | key[0]
+        n = (ctr[1] << 32) | ctr[0]
+        bits = (want[0] << 21) | (want[1] >> 11)
+        u_want = (bits + 0.5) / float(1 << 53)
+        u = oracle.uniform(seed, n, ctr[2], ctr[3], lib=lib)
+        if u != u_want:
+            return False, f"uniform({seed:#x},{n:#x},{ctr[2]:#x},{ctr[3]:#x}) = {u!r} != {u_want!r}"
+    return True, ""
+
+
+def pin_brute_force_normalised(lib=None):
+    cases = [(_tiny()), gen.mps_tensors(10, 2, 8, base_seed=77)[:2], gen.mps_tensors(7, 4, 12, base_seed=5,
+                                                                                        skew=1.5)[:2]]
+    for b, ts in cases:
+        p = oracle.brute_force(b, ts, lib=lib)
+        if not abs(p.sum() - 1.0) < 1e-12 or p.min() < 0:
+            return False, f"sum |psi|^2 = {p.sum()!r}"
+    return True, ""
+
+
+def _prefix_marg(bf, prefix):
+    return bf[tuple(prefix)].sum()
+
+
+def pin_conditionals_vs_brute(lib=None, rows=40, seed=42):
+    b, ts = _tiny()
+    bf = oracle.brute_force(b, ts)  # the real brute force: this pin checks the sampler
+    smp, lp, pr = oracle.sample(b, ts, seed, rows, want_probs=True, lib=lib)
+    M = len(b) - 1
+    worst = 0.0
+    for i in range(rows):
+        for k in range(M):
+            pre = list(smp[i, :k])
+            den = _prefix_marg(bf, pre)
+            for s in range(bf.shape[0]):
+                num = _prefix_marg(bf, pre + [s])
+                worst = max(worst, abs(pr[i, k, s] - num / den))
+    if not worst < 1e-12:
+        return False, f"max |p_oracle - p_brute| = {worst:.3e}"
+    return True, ""
+
+
+def pin_logprob_vs_brute(lib=None, rows=200, seed=42):
+    b, ts = _tiny()
+    bf = oracle.brute_force(b, ts)
+    smp, lp = oracle.sample(b, ts, seed, rows, lib=lib)
+    for i in range(rows):
+        p = bf[tuple(smp[i])]
+        if not (p > 0 and abs(lp[i] - math.log(p)) < 1e-11):
+            return False, f"row {i}: logp = {lp[i]!r}, log |psi|^2 = {math.log(p) if p > 0 else p!r}"
+        born = oracle.born_logprob(b, ts, smp[i], lib=lib)  # closed form
+        if not abs(born - math.log(p)) < 1e-11:
+            return False, f"row {i}: born_logprob {born!r} vs log brute {math.log(p)!r}"
+    return True, ""
+
+
+def pin_product_state(lib=None, seed=9, N=400):
+    rng = np.random.Generator(np.random.PCG64(3))
+    M, d = 20, 4
+    laws = rng.random((M, d)) ** 2
+    laws[3] = [0.0, 1.0, 0.0, 0.0]          # a certain outcome
+    laws[4] = [0.5, 0.0, 0.0, 0.5]          # zero-probability middle outcomes
+    laws /= laws.sum(axis=1, keepdims=True)
+    b, ts = gen.product_state(M, laws)
+    smp, lp, pr = oracle.sample(b, ts, seed, N, want_probs=True, lib=lib)
+    if not np.abs(pr - laws[None]).max() < 1e-14:
+        return False, f"conditionals differ from the per-site laws by {np.abs(pr - laws[None]).max():.3e}"
+    cdf = np.cumsum(laws, axis=1)
+    for i in range(N):
+        want_lp = 0.0
+        for k in range(M):
+            u = oracle.uniform(seed, i, k)    # the generator is pinned on its own above
+            s = int(np.sum(cdf[k, :d - 1] < u * cdf[k, -1]))
+            if smp[i, k] != s:
+                return False, f"row {i} site {k}: outcome {smp[i, k]} != inverse-CDF draw {s}"
+            want_lp += math.log(laws[k, s])
+        if not abs(lp[i] - want_lp) < 1e-12:
+            return False, f"row {i}: logp {lp[i]!r} != {want_lp!r}"
+    return True, ""
+
+
+def pin_ghz(lib=None, N=3000, seed=5):
+    for M, d in ((8, 3), (16, 2), (5, 4)):
+        b, ts = gen.ghz_chain(M, d)
+        smp, lp = oracle.sample(b, ts, seed, N, lib=lib)
+        if not (smp == smp[:, :1]).all():
+            return False, f"GHZ(M={M},d={d}): outcomes not perfectly correlated"
+        if not np.abs(lp + math.log(d)).max() < 1e-12:
+            return False, f"GHZ(M={M},d={d}): logp != -log d"
+        f = np.bincount(smp[:, 0], minlength=d) / N
+        sig = math.sqrt((1 / d) * (1 - 1 / d) / N)
+        if not np.abs(f - 1 / d).max() < 5 * sig:
+            return False, f"GHZ first-site frequencies {f}"
+    return True, ""
+
+
+def pin_scale_invariance(lib=None, N=200, seed=11):
+    b, ts = _tiny()
+    scaled = [t * (1.7 if k % 2 else 0.6) for k, t in enumerate(ts)]
+    s0, l0, p0 = oracle.sample(b, ts, seed, N, want_probs=True, lib=lib)
+    s1, l1, p1 = oracle.sample(b, scaled, seed, N, want_probs=True, lib=lib)
+    if not (s0 == s1).all():
+        return False, "outcomes change when site tensors are scaled"
+    if not np.abs(l0 - l1).max() < 1e-11:
+        return False, f"logp changes by {np.abs(l0 - l1).max():.3e} when site tensors are scaled"
+    if not np.abs(p0 - p1).max() < 1e-12:
+        return False, "conditionals change when site tensors are scaled"
+    return True, ""
+
+
+def pin_long_chain(lib=None, N=8, seed=3):
+    b, ts, _ = gen.mps_tensors(3000, 4, 4, base_seed=100, skew=1.5)
+    smp, lp = oracle.sample(b, ts, seed, N, lib=lib)
+    for i in range(N):
+        if not math.isfinite(lp[i]):
+            return False, f"row {i}: logp {lp[i]!r} is not finite"
+        born = oracle.born_logprob(b, ts, smp[i], lib=lib)
+        if not abs(lp[i] - born) < 1e-8 * max(1.0, abs(born)):
+            return False, f"row {i}: logp {lp[i]!r} vs closed form {born!r}"
+    return True, ""
+
+
+FAST_PINS = [pin_philox_kat, pin_uniform_packing, pin_brute_force_normalised, pin_conditionals_vs_brute,
+             pin_logprob_vs_brute, pin_product_state, pin_ghz, pin_scale_invariance, pin_long_chain]
+
+
+def marginals_5sigma(samples: np.ndarray, bf: np.ndarray):
+    """Return the worst |f - p| / sigma over single-site and nearest-pair marginals."""
+    N, M = samples.shape
+    d = bf.shape[0]
+    worst = 0.0
+    where = ""
+    for k in range(M):
+        axes = tuple(a for a in range(M) if a != k)
+        p = bf.sum(axis=axes)
+        f = np.bincount(samples[:, k], minlength=d) / N
+        sig = np.sqrt(np.maximum(p * (1 - p), 1e-300) / N)
+        z = np.abs(f - p) / sig
+        z[(p == 0) & (f == 0)] = 0
+        if z.max() > worst:
+            worst, where = float(z.max()), f"site {k}"
+    for k in range(M - 1):
+        axes = tuple(a for a in range(M) if a not in (k, k + 1))
+        p = bf.sum(axis=axes).reshape(-1)
+        f = np.bincount(samples[:, k].astype(np.int64) * d + samples[:, k + 1], minlength=d * d) / N
+        sig = np.sqrt(np.maximum(p * (1 - p), 1e-300) / N)
+        z = np.abs(f - p) / sig
+        z[(p == 0) & (f == 0)] = 0
+        if z.max() > worst:
+            worst, where = float(z.max()), f"pair ({k},{k+1})"
+    return worst, where

@@ -1,0 +1,49 @@
+"""Plant plausible mistakes in copies of the oracle (on the CPU) and require that a pin catches each.
+
+This guards the pins themselves: an oracle with a dropped term, a wrong sign,
+a transposed index, a missing normalisation or a mis-keyed uniform must fail
+at least one of them.
+"""
+import os
+
+import pytest
+
+import oracle
+import oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
+
+MUTANTS = {
+    "drop_imag_cross_term": ("y[2 * c] += vr * ar - vi * ai;", "y[2 * c] += vr * ar;"),
+    "imag_sign_flip": ("y[2 * c + 1] += vr * ai + vi * ar;", "y[2 * c + 1] += vr * ai - vi * ar;"),
+    "transposed_site_index": ("const double *row = A + (size_t)2 * a * cols;",
+                              "const double *row = A + (size_t)2 * a * (cols == chi_l ? cols : chi_r);"),
+    "no_cumulative_sum": ("        acc += w[s];\n        C[s] = acc;", "        acc += w[s];\n        C[s] = w[s];"),
+    "threshold_not_scaled_by_Z": ("const double t = u * Z;", "const double t = u;"),
+    "logprob_without_Z": ("lp += log(w[s]) - log(Z);", "lp += log(w[s]);"),
+    "no_renormalisation": ("const double inv = 1.0 / sqrt(w[s]);", "const double inv = 1.0;"),
+    "uniform_wrong_site_key": ("orc_uniform(seed, n, (uint32_t)k, job)", "orc_uniform(seed, n, (uint32_t)(k + 1), job)"),
+    "philox_wrong_multiplier": ("#define ORC_PHILOX_M1 0xCD9E8D57u", "#define ORC_PHILOX_M1 0xCD9E8D59u"),
+    "uniform_drops_second_word": ("| (uint64_t)(x[1] >> 11);", "| 0u;"),
+    "select_previous_block": ("v[2 * b] = y[2 * (s * cr + b)] * inv;",
+                              "v[2 * b] = y[2 * (((s + 1) % d) * cr + b)] * inv;"),
+    "born_conjugates_one_factor": ("im += r[2 * a] * e[1] + r[2 * a + 1] * e[0];\n            }\n            t[2 * b] = re;",
+                                   "im += -r[2 * a] * e[1] + r[2 * a + 1] * e[0];\n            }\n            t[2 * b] = re;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(name, tmp_path):
+    find, repl = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(find) == 1, f"mutation site for {name} not unique/absent"
+    lib = oracle.load_variant(oracle.build_variant(src.replace(find, repl), str(tmp_path / f"{name}.so")))
+    failures = []
+    for pin in P.FAST_PINS:
+        try:
+            ok, detail = pin(lib=lib)
+        except Exception as e:  # a crash or a raised error also counts as caught
+            ok, detail = False, repr(e)
+        if not ok:
+            failures.append(pin.__name__)
+    assert failures, f"mutant {name} passed every pin"

@@ -1,0 +1,121 @@
+"""The oracle pinned to facts other than itself (CPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import oracle_pins as P
+
+
+@pytest.mark.parametrize("pin", P.FAST_PINS, ids=lambda f: f.__name__)
+def test_pin(pin):
+    ok, detail = pin()
+    assert ok, detail
+
+
+def test_uniform_range_and_uniformity():
+    n = 200_000
+    u = np.array([oracle.uniform(42, i, 7) for i in range(0, n)])
+    assert (u > 0).all() and (u < 1).all()
+    # 53-bit grid: u * 2^53 - 1/2 is an integer
+    g = u * float(1 << 53) - 0.5
+    assert np.all(g == np.floor(g))
+    # chi-square on 100 equiprobable bins (p-value > 1e-6 at 99 dof: stat < 190)
+    h = np.bincount(np.minimum((u * 100).astype(int), 99), minlength=100)
+    stat = ((h - n / 100) ** 2 / (n / 100)).sum()
+    assert stat < 190, stat
+    # the low bits carry entropy too (from the second output word)
+    low = (g.astype(np.uint64) & np.uint64(0xFF)).astype(int)
+    assert len(np.unique(low)) == 256
+
+
+def test_generator_right_canonical():
+    for (M, d, chi, skew) in ((12, 3, 16, None), (9, 4, 32, 1.5), (6, 6, 20, 1.5)):
+        b, ts, _ = gen.mps_tensors(M, d, chi, base_seed=21, skew=skew)
+        assert b[0] == 1 and b[-1] == 1
+        for k, A in enumerate(ts):
+            cl, dd, cr = A.shape
+            assert (cl, dd, cr) == (b[k], d, b[k + 1])
+            G = np.einsum("asb,csb->ac", A, A.conj())
+            assert np.abs(G - np.eye(cl)).max() < 1e-12
+
+
+def test_bond_profile():
+    assert gen.bond_dims(12, 3, 16) == [1, 3, 9, 16, 16, 16, 16, 16, 16, 16, 9, 3, 1]
+    b = gen.bond_dims(256, 4, 256)
+    assert b[:6] == [1, 4, 16, 64, 256, 256] and b[-5:] == [256, 64, 16, 4, 1]
+
+
+def test_skew_tilts_outcomes():
+    """The exp(-s/1.5) skew makes low outcomes dominate (GBS-like photon statistics)."""
+    b, ts, _ = gen.mps_tensors(40, 4, 16, base_seed=8, skew=1.5)
+    smp, _ = oracle.sample(b, ts, 1, 2000)
+    f = np.bincount(smp.reshape(-1), minlength=4) / smp.size
+    assert f[0] > f[1] > f[2] > f[3]
+
+
+def test_replay_follows_own_path():
+    b, ts = P._tiny()
+    smp, lp, pr = oracle.sample(b, ts, 42, 64, want_probs=True)
+    rows = np.arange(64)
+    r = oracle.replay(b, ts, 42, rows, smp)
+    assert (r["own"] == smp).all()
+    assert np.array_equal(r["probs"], pr)
+    assert np.array_equal(r["logprob"], lp)
+    assert (r["margin"] >= 0).all() and (r["margin"] <= 1).all()
+
+
+def test_replay_noncontiguous_rows_and_offset():
+    b, ts = P._tiny()
+    smp, lp = oracle.sample(b, ts, 42, 50, n0=1000)
+    rows = np.array([1003, 1004, 1020, 1049])
+    r = oracle.replay(b, ts, 42, rows, smp[rows - 1000])
+    assert (r["own"] == smp[rows - 1000]).all()
+    assert np.allclose(r["logprob"], lp[rows - 1000], rtol=0, atol=0)
+
+
+def test_replay_other_path_changes_own_draws():
+    """Forcing a different prefix changes the later conditionals (the chain has memory)."""
+    b, ts = P._tiny()
+    smp, _ = oracle.sample(b, ts, 42, 1)
+    forced = smp.copy()
+    forced[0, 2] = (forced[0, 2] + 1) % 3
+    r0 = oracle.replay(b, ts, 42, [0], smp)
+    r1 = oracle.replay(b, ts, 42, [0], forced)
+    assert np.abs(r0["probs"][0, 3] - r1["probs"][0, 3]).max() > 1e-6
+
+
+@pytest.mark.slow
+def test_marginals_within_5_sigma(tiny_chain, tiny_brute):
+    b, ts = tiny_chain
+    smp, _ = oracle.sample(b, ts, 2024, 100_000)
+    worst, where = P.marginals_5sigma(smp, tiny_brute)
+    assert worst < 5.0, (worst, where)
+
+
+def test_offset_rows_match():
+    """Row n's result depends only on (seed, n): sampling a sub-range reproduces it."""
+    b, ts = P._tiny()
+    s_all, l_all = oracle.sample(b, ts, 42, 300)
+    s_sub, l_sub = oracle.sample(b, ts, 42, 100, n0=150)
+    assert np.array_equal(s_all[150:250], s_sub)
+    assert np.array_equal(l_all[150:250], l_sub)
+
+
+def test_thread_count_independent():
+    b, ts = P._tiny()
+    s1, l1 = oracle.sample(b, ts, 42, 500, nthreads=1)
+    s2, l2 = oracle.sample(b, ts, 42, 500, nthreads=4)
+    assert np.array_equal(s1, s2) and np.array_equal(l1, l2)
+
+
+def test_pool_site_index():
+    b, ts, idx = gen.mps_tensors(40, 3, 9, base_seed=4, pool=4)
+    assert len(ts) < 40
+    full = [ts[j] for j in idx]
+    s1, l1 = oracle.sample(b, ts, 1, 50, site_index=idx)
+    s2, l2 = oracle.sample(b, full, 1, 50)
+    assert np.array_equal(s1, s2) and np.array_equal(l1, l2)
+    assert all(math.isfinite(x) for x in l1)
