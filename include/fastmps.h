@@ -1,0 +1,164 @@
+/*
+ * fastmps.h -- C ABI of the GB300 (sm_103a) MPS perfect-sampling library.
+ *
+ * What it computes (Sec. 2.2 "Parallel MPS Sampling", Fig. 1 workflow;
+ * Algorithm 2 "Measurement"; Sec. 3.3.1 per-sample scaling):
+ * N independent configurations s[n] = (s_0 .. s_{M-1}) are drawn from the Born
+ * distribution |A_0[s_0] A_1[s_1] ... A_{M-1}[s_{M-1}]|^2 of a right-canonical
+ * complex MPS with M sites, physical dimension d and bond dimensions
+ * b_0 = 1, b_1 .. b_{M-1}, b_M = 1.  Site k holds A_k[chi_l = b_k][d][chi_r =
+ * b_{k+1}].  For each sample n the left vector v (v_0 = [1]) is contracted with
+ * the site tensor, y_s = v A_k[:, s, :]; the unnormalised probabilities
+ * w_s = ||y_s||^2 are summed in s order into C_s with Z = C_{d-1}; the outcome
+ * is s* = #{s < d-1 : C_s < u Z} for the Philox4x32-10 uniform u = U(seed, n,
+ * k, job) in (0,1); log p(s[n]) accumulates log w_{s*} - log Z; and
+ * v <- y_{s*} / sqrt(w_{s*}).
+ *
+ * The uniform: key = (seed & 0xffffffff, seed >> 32), counter = (n & 0xffffffff,
+ * n >> 32, k, job); with Philox outputs x0, x1,
+ * u = (((uint64)x0 << 21 | x1 >> 11) + 0.5) * 2^-53.  Row n's result depends
+ * only on (site tensors, seed, n, job, precision), not on N, n0 or tiling
+ * choices other than through floating-point rounding.
+ *
+ * Conventions for every call
+ *  - Return 0 (FASTMPS_OK) on success or a negative FASTMPS_ERR_* code; the
+ *    message of the last failure is kept per handle (fastmps_last_error).
+ *  - No C++ exception crosses the ABI.  Calls on one handle are not
+ *    thread-safe; distinct handles are independent.
+ *  - Input arrays are host memory owned by the caller and only read during
+ *    the call.  Output arrays may be host or device memory (detected with
+ *    cudaPointerGetAttributes) and are owned by the caller.
+ *  - fastmps_sample* is synchronous: outputs are complete on return.
+ */
+#ifndef FASTMPS_H
+#define FASTMPS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes */
+#define FASTMPS_OK 0
+#define FASTMPS_ERR_INVALID_ARG (-1)   /* null pointer, negative size, out-of-range enum */
+#define FASTMPS_ERR_SHAPE (-2)         /* bond_dims disagree with loaded sites, d > 255, ... */
+#define FASTMPS_ERR_NOT_LOADED (-3)    /* a site (or pool entry) was never loaded */
+#define FASTMPS_ERR_OOM (-4)           /* device or pinned-host allocation failed */
+#define FASTMPS_ERR_CUDA (-5)          /* a CUDA runtime/driver call failed */
+#define FASTMPS_ERR_TIMEOUT (-6)       /* a bounded device-side wait gave up */
+#define FASTMPS_ERR_UNSUPPORTED (-7)   /* not available on this device/build */
+#define FASTMPS_ERR_NUMERIC (-8)       /* Z = sum_s w_s was not a positive finite number */
+
+/* Arithmetic of the per-site contraction (Sec. 3.3, adaptive mixed precision). */
+#define FASTMPS_FP32 0    /* complex64 storage, FP32 SIMT FMA (no tensor cores) */
+#define FASTMPS_BF16X2 1  /* site tensors BF16; v split hi+lo BF16; 2 tensor-core products */
+#define FASTMPS_BF16X3 2  /* site tensors hi+lo BF16; v hi+lo; 3 tensor-core products */
+
+/* Where site tensors live between uses (Sec. 3.1: I/O overlapped by a double buffer). */
+#define FASTMPS_RESIDENT_HBM 0    /* repacked once at load time, kept in device memory */
+#define FASTMPS_HOST_STREAM 1     /* kept in pinned host memory (BF16), copied per site into
+                                     one of two device slots on a copy stream, overlapped
+                                     with the previous site's compute */
+
+/* Element type of tensors passed to fastmps_load_site / fastmps_load_pool */
+#define FASTMPS_C64 0   /* interleaved complex float  (re, im) */
+#define FASTMPS_C128 1  /* interleaved complex double (re, im) */
+
+typedef struct fastmps_options {
+    int precision;          /* FASTMPS_FP32 | FASTMPS_BF16X2 | FASTMPS_BF16X3 */
+    int residency;          /* FASTMPS_RESIDENT_HBM | FASTMPS_HOST_STREAM (BF16 modes only) */
+    int64_t max_microbatch; /* rows per contraction launch; 0 = chosen from free memory */
+    int autotune;           /* 1: time the candidate tile shapes once per new shape */
+    void *stream;           /* cudaStream_t to run on; NULL = a stream owned by the handle */
+} fastmps_options;
+
+typedef struct fastmps_ctx *fastmps_handle;
+
+/* Per-call statistics of the last fastmps_sample* call on a handle. */
+typedef struct fastmps_stats {
+    double ms_total;        /* wall time of the call (host clock) */
+    double ms_contract;     /* device time in contraction kernels (CUDA events) */
+    double ms_measure;      /* device time in the measurement kernels */
+    int64_t launches;       /* kernels launched by the call */
+    int64_t contract_launches;
+    double flops_algorithmic; /* 8 * N * sum_k chi_l d chi_r */
+    double flops_issued;    /* algorithmic x the number of split products (BF16 modes) */
+    int64_t h2d_bytes;      /* host->device bytes copied during the call */
+    int64_t d2h_bytes;      /* device->host bytes copied during the call */
+} fastmps_stats;
+
+/* Fill *opt with the defaults: FP32, resident, automatic micro-batch, no autotune, own stream. */
+void fastmps_default_options(fastmps_options *opt);
+
+/*
+ * Create a handle on CUDA device `device`.  opt may be NULL (defaults).
+ * Fails with FASTMPS_ERR_UNSUPPORTED if the device is not compute capability
+ * 10.3 (the library is built for sm_103a only).  *out receives the handle
+ * (NULL on failure).
+ */
+int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt);
+
+/* Release every resource of the handle.  NULL is accepted; a handle must not be used afterwards. */
+void fastmps_destroy(fastmps_handle h);
+
+/*
+ * Message of the last failure on h (empty string if none).  With h == NULL,
+ * the message of the last failed fastmps_create in this process.
+ * The pointer stays valid until the next call on the same handle.
+ */
+const char *fastmps_last_error(fastmps_handle h);
+
+/*
+ * Load site k: A is host memory, shape [chi_l][d][chi_r] row-major,
+ * interleaved complex of type dtype.  The tensor is copied and repacked into
+ * the handle's arithmetic format (complex64, or BF16 planes of the real
+ * stacked operand); the caller keeps ownership of A.  Loading k again
+ * replaces the site.  In FASTMPS_HOST_STREAM residency the BF16 copy stays in
+ * pinned host memory.  Requirements: 0 <= k < 65536, chi_l, chi_r >= 1,
+ * 2 <= d <= 255, d * chi_r >= chi_l (an isometry must fit).
+ */
+int fastmps_load_site(fastmps_handle h, int k, int chi_l, int d, int chi_r, const void *A, int dtype);
+
+/*
+ * Pool extension for chains that reuse tensors (e.g. a pool of 16 interior
+ * isometries shared by thousands of sites): load pool entry j (same layout
+ * and rules as fastmps_load_site), then map site k to it.  A mapped site uses
+ * the pool entry until it is mapped again or loaded with fastmps_load_site.
+ */
+int fastmps_load_pool(fastmps_handle h, int j, int chi_l, int d, int chi_r, const void *A, int dtype);
+int fastmps_map_site(fastmps_handle h, int k, int j);
+
+/*
+ * Draw N samples, rows n = 0 .. N-1.
+ *   bond_dims   host array of M+1 ints with bond_dims[0] = bond_dims[M] = 1;
+ *               site k must be loaded with shape (bond_dims[k], d, bond_dims[k+1]).
+ *   out_samples N*M bytes, row n = sample n (out_samples[n*M + k] = s_k), or NULL.
+ *   out_logprob N doubles, log p(s[n]) = sum_k log(w_{s_k} / Z_k), or NULL.
+ * N = 0 is valid and does nothing.
+ */
+int fastmps_sample(fastmps_handle h, int M, int d, const int *bond_dims, int64_t N, uint64_t seed,
+                   uint8_t *out_samples, double *out_logprob);
+
+/*
+ * As fastmps_sample for rows n = n0 .. n0+N-1 (output row i is sample n0+i)
+ * and Philox counter word `job`.  trace_rows > 0 with trace_probs != NULL
+ * records the normalised conditionals w_s / Z of the first trace_rows rows at
+ * every site: trace_probs[(k * trace_rows + i) * d + s] (doubles, host or
+ * device memory), for parity checks.
+ */
+int fastmps_sample_ex(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N,
+                      uint64_t seed, uint32_t job, uint8_t *out_samples, double *out_logprob,
+                      int64_t trace_rows, double *trace_probs);
+
+/* Statistics of the last fastmps_sample* call. */
+int fastmps_get_stats(fastmps_handle h, fastmps_stats *out);
+
+/* Library version string (static storage). */
+const char *fastmps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTMPS_H */

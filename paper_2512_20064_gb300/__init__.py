@@ -1,0 +1,275 @@
+"""Python binding of ``libfastmps.so``: GB300 (sm_103a) perfect sampling from a right-canonical MPS.
+
+The binding only marshals arguments for the C ABI declared in
+``include/fastmps.h``; every step of the sampling runs in the library's CUDA
+kernels.  There is no CPU fallback: if the library is not built, or the
+device is not an sm_103a GPU, the calls raise.
+
+Low-level functions carry the C names (``fastmps_create``, ``fastmps_load_site``,
+``fastmps_sample``, ``fastmps_sample_ex``, ``fastmps_destroy`` ...); the
+:class:`Sampler` class wraps a handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB, build
+
+__all__ = [
+    "FastMPSError", "Sampler", "load_library", "build", "PRECISIONS", "RESIDENCIES",
+    "fastmps_create", "fastmps_destroy", "fastmps_last_error", "fastmps_load_site", "fastmps_load_pool",
+    "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_get_stats", "fastmps_version",
+    "fastmps_default_options",
+]
+
+OK = 0
+ERR_NAMES = {-1: "INVALID_ARG", -2: "SHAPE", -3: "NOT_LOADED", -4: "OOM", -5: "CUDA", -6: "TIMEOUT",
+             -7: "UNSUPPORTED", -8: "NUMERIC"}
+PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16x3": 2}
+RESIDENCIES = {"hbm": 0, "host_stream": 1}
+C64, C128 = 0, 1
+
+
+class fastmps_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("residency", ctypes.c_int), ("max_microbatch", ctypes.c_int64),
+                ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class fastmps_stats(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_contract", ctypes.c_double), ("ms_measure", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("contract_launches", ctypes.c_int64),
+                ("flops_algorithmic", ctypes.c_double), ("flops_issued", ctypes.c_double),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+
+class FastMPSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"fastmps error {code} ({ERR_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load the shared library (building it with nvcc first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB
+        if path is None and build_if_missing:
+            build()
+        if not os.path.exists(p):
+            raise ImportError(f"libfastmps.so not found at {p}; run paper_2512_20064_gb300.build.build()")
+        lib = ctypes.CDLL(p)
+        H = ctypes.c_void_p
+        P = ctypes.POINTER
+        lib.fastmps_default_options.argtypes = [P(fastmps_options)]
+        lib.fastmps_default_options.restype = None
+        lib.fastmps_create.argtypes = [P(H), ctypes.c_int, P(fastmps_options)]
+        lib.fastmps_create.restype = ctypes.c_int
+        lib.fastmps_destroy.argtypes = [H]
+        lib.fastmps_destroy.restype = None
+        lib.fastmps_last_error.argtypes = [H]
+        lib.fastmps_last_error.restype = ctypes.c_char_p
+        for name in ("fastmps_load_site", "fastmps_load_pool"):
+            f = getattr(lib, name)
+            f.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+            f.restype = ctypes.c_int
+        lib.fastmps_map_site.argtypes = [H, ctypes.c_int, ctypes.c_int]
+        lib.fastmps_map_site.restype = ctypes.c_int
+        lib.fastmps_sample.argtypes = [H, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
+                                       ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p]
+        lib.fastmps_sample.restype = ctypes.c_int
+        lib.fastmps_sample_ex.argtypes = [H, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        lib.fastmps_sample_ex.restype = ctypes.c_int
+        lib.fastmps_get_stats.argtypes = [H, P(fastmps_stats)]
+        lib.fastmps_get_stats.restype = ctypes.c_int
+        lib.fastmps_version.argtypes = []
+        lib.fastmps_version.restype = ctypes.c_char_p
+        if path is None:
+            _lib = lib
+        return lib
+
+
+# ---------------------------------------------------------------------------
+# Low-level functions with the C names (argument marshalling only).
+# ---------------------------------------------------------------------------
+
+def _check(lib, h, rc):
+    if rc != OK:
+        msg = lib.fastmps_last_error(h)
+        raise FastMPSError(rc, msg.decode() if msg else "")
+
+
+def fastmps_version() -> str:
+    return load_library().fastmps_version().decode()
+
+
+def fastmps_default_options() -> fastmps_options:
+    o = fastmps_options()
+    load_library().fastmps_default_options(ctypes.byref(o))
+    return o
+
+
+def fastmps_create(device: int = 0, options: fastmps_options | None = None) -> ctypes.c_void_p:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    rc = lib.fastmps_create(ctypes.byref(h), device, ctypes.byref(options) if options is not None else None)
+    _check(lib, None, rc)
+    return h
+
+
+def fastmps_destroy(h) -> None:
+    load_library().fastmps_destroy(h)
+
+
+def fastmps_last_error(h) -> str:
+    m = load_library().fastmps_last_error(h)
+    return m.decode() if m else ""
+
+
+def _tensor_arg(A):
+    A = np.asarray(A)
+    if A.ndim != 3:
+        raise ValueError("site tensor must have shape (chi_l, d, chi_r)")
+    if A.dtype == np.complex64:
+        dt = C64
+    elif A.dtype == np.complex128:
+        dt = C128
+    else:
+        A = A.astype(np.complex128)
+        dt = C128
+    A = np.ascontiguousarray(A)
+    return A, dt
+
+
+def fastmps_load_site(h, k: int, A) -> None:
+    lib = load_library()
+    A, dt = _tensor_arg(A)
+    cl, d, cr = A.shape
+    _check(lib, h, lib.fastmps_load_site(h, k, cl, d, cr, A.ctypes.data, dt))
+
+
+def fastmps_load_pool(h, j: int, A) -> None:
+    lib = load_library()
+    A, dt = _tensor_arg(A)
+    cl, d, cr = A.shape
+    _check(lib, h, lib.fastmps_load_pool(h, j, cl, d, cr, A.ctypes.data, dt))
+
+
+def fastmps_map_site(h, k: int, j: int) -> None:
+    lib = load_library()
+    _check(lib, h, lib.fastmps_map_site(h, k, j))
+
+
+def _ptr(x):
+    """Raw address of a numpy array or a torch tensor (host or device); None stays NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("output arrays must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("output tensors must be contiguous")
+        return x.data_ptr()
+    raise TypeError("outputs must be numpy arrays or torch tensors")
+
+
+def fastmps_sample_ex(h, M: int, d: int, bonds, n0: int, N: int, seed: int, job: int, out_samples, out_logprob,
+                      trace_rows: int = 0, trace_probs=None) -> None:
+    lib = load_library()
+    b = (ctypes.c_int * (M + 1))(*[int(x) for x in bonds])
+    _check(lib, h, lib.fastmps_sample_ex(h, M, d, b, n0, N, seed, job, _ptr(out_samples), _ptr(out_logprob),
+                                         trace_rows, _ptr(trace_probs)))
+
+
+def fastmps_sample(h, M: int, d: int, bonds, N: int, seed: int, out_samples, out_logprob) -> None:
+    lib = load_library()
+    b = (ctypes.c_int * (M + 1))(*[int(x) for x in bonds])
+    _check(lib, h, lib.fastmps_sample(h, M, d, b, N, seed, _ptr(out_samples), _ptr(out_logprob)))
+
+
+def fastmps_get_stats(h) -> dict:
+    lib = load_library()
+    s = fastmps_stats()
+    _check(lib, h, lib.fastmps_get_stats(h, ctypes.byref(s)))
+    return {f: getattr(s, f) for f, _ in fastmps_stats._fields_}
+
+
+class Sampler:
+    """A handle of the library: load site tensors once, then sample many times."""
+
+    def __init__(self, device: int = 0, precision: str = "fp32", residency: str = "hbm", max_microbatch: int = 0,
+                 stream=None):
+        o = fastmps_default_options()
+        o.precision = PRECISIONS[precision]
+        o.residency = RESIDENCIES[residency]
+        o.max_microbatch = int(max_microbatch)
+        if stream is not None:
+            o.stream = int(stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+        self.precision = precision
+        self.residency = residency
+        self.h = fastmps_create(device, o)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            fastmps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def load_site(self, k: int, A):
+        fastmps_load_site(self.h, k, A)
+
+    def load_chain(self, tensors, site_index=None):
+        """Load every site; with ``site_index`` the tensors form a pool and site k maps to ``site_index[k]``."""
+        if site_index is None:
+            for k, A in enumerate(tensors):
+                fastmps_load_site(self.h, k, A)
+        else:
+            for j, A in enumerate(tensors):
+                fastmps_load_pool(self.h, j, A)
+            for k, j in enumerate(site_index):
+                fastmps_map_site(self.h, k, j)
+
+    def sample(self, bonds, d: int, N: int, seed: int, n0: int = 0, job: int = 0, out_samples=None,
+               out_logprob=None, trace_rows: int = 0):
+        """Draw rows ``n0 .. n0+N-1``.  Returns ``(samples[N, M] uint8, logprob[N] float64[, trace[M, R, d]])``.
+
+        Outputs are numpy arrays unless ``out_samples`` / ``out_logprob`` are given
+        (numpy arrays or torch tensors, host or CUDA).
+        """
+        M = len(bonds) - 1
+        if out_samples is None:
+            out_samples = np.empty((N, M), np.uint8)
+        if out_logprob is None:
+            out_logprob = np.empty(N, np.float64)
+        trace = np.empty((M, trace_rows, d), np.float64) if trace_rows > 0 else None
+        fastmps_sample_ex(self.h, M, d, bonds, n0, N, seed, job, out_samples, out_logprob, trace_rows, trace)
+        if trace is not None:
+            return out_samples, out_logprob, trace
+        return out_samples, out_logprob
+
+    def stats(self) -> dict:
+        return fastmps_get_stats(self.h)

@@ -1,0 +1,713 @@
+// C ABI and host engine of the sampling library (see include/fastmps.h).
+//
+// Engine per call (Sec. 3.1 data-parallel scheme on one device): all N rows
+// of the left operand stay resident in device memory (the macro-batch);
+// for each site k the rows are processed in micro-batches: one contraction
+// launch writes the FP32 scratch Y and per-tile sums of squares, one
+// measurement launch draws the outcome and writes the next left operand.  In
+// host-streaming residency the BF16 site tensor of site k+1 is copied from
+// pinned host memory into one of two device slots on a copy stream while site
+// k computes (Sec. 3.1 double buffer; Sec. 3.3.2 16-bit storage).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/fastmps.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace fastmps;
+
+namespace {
+
+std::string g_create_error;
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+inline int64_t roundup(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+// A device or pinned-host buffer that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    bool host = false;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) {
+            if (host) cudaFreeHost(p);
+            else cudaFree(p);
+        }
+        p = nullptr;
+        bytes = 0;
+    }
+    bool ensure(size_t want) {
+        if (want <= bytes) return true;
+        release();
+        if (want == 0) return true;
+        cudaError_t e = host ? cudaHostAlloc(&p, want, cudaHostAllocDefault) : cudaMalloc(&p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        bytes = want;
+        return true;
+    }
+    template <class T>
+    T *as() const { return static_cast<T *>(p); }
+};
+
+struct Tensor {
+    SiteLayout L;
+    // resident operands (device)
+    DevBuf B_hi, B_lo, Bt;
+    CUtensorMap tmB[2];
+    // streamed operand (pinned host, compact BF16 [chi_l][d][chi_r] (re, im), hi block then lo block)
+    DevBuf host_compact;
+    int planes = 1;
+};
+
+}  // namespace
+
+struct fastmps_ctx {
+    int device = 0;
+    fastmps_options opt{};
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string last_error;
+    std::map<int, std::unique_ptr<Tensor>> site_tensor;  // private tensor of site k
+    std::map<int, std::unique_ptr<Tensor>> pool_tensor;  // pool entry j
+    std::map<int, int> site_pool;                        // site k -> pool entry j
+    // work buffers (grow only)
+    DevBuf V[2][2];  // [ping-pong][plane]  BF16 planes, or V[x][0] FP32
+    DevBuf Y, P, logp, O, Dout, Dlogp, trace, err;
+    DevBuf staging;  // device copy of a tensor being loaded
+    DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
+    cudaEvent_t copy_done[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
+    fastmps_stats stats{};
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace {
+
+int fail(fastmps_handle h, int code, const std::string &msg) {
+    if (h) h->last_error = msg;
+    return code;
+}
+
+int cuda_fail(fastmps_handle h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(h, e == cudaErrorMemoryAllocation ? FASTMPS_ERR_OOM : FASTMPS_ERR_CUDA, m);
+}
+
+bool is_bf16(const fastmps_handle h) { return h->opt.precision == FASTMPS_BF16X2 || h->opt.precision == FASTMPS_BF16X3; }
+
+SiteLayout make_layout(int precision, int chi_l, int d, int chi_r) {
+    SiteLayout L;
+    L.chi_l = chi_l;
+    L.d = d;
+    L.chi_r = chi_r;
+    L.K_pad = (int)roundup(2 * (int64_t)chi_l, 64);
+    if (precision == FASTMPS_FP32) {
+        L.bn = 128;
+    } else {
+        L.bn = (int)std::min<int64_t>(256, roundup(2 * (int64_t)chi_r, 32));
+    }
+    L.Cs = (int)roundup(2 * (int64_t)chi_r, L.bn);
+    L.ncols = d * L.Cs;
+    L.tiles_per_s = L.Cs / L.bn;
+    return L;
+}
+
+bool encode_2d_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                    uint32_t box_inner, uint32_t box_outer) {
+    EncodeTiledFn fn = get_encode_fn();
+    if (!fn) return false;
+    cuuint64_t gdim[2] = {inner, outer};
+    cuuint64_t gstride[1] = {ld_elems * 2};
+    cuuint32_t box[2] = {box_inner, box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), gdim, gstride, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Host round-to-nearest-even float -> bfloat16 bits (finite inputs).
+inline uint16_t host_bf16_bits(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7FFFu + lsb;
+    return (uint16_t)(u >> 16);
+}
+inline float host_bf16_float(uint16_t b) {
+    uint32_t u = (uint32_t)b << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+int check_shape_args(fastmps_handle h, int chi_l, int d, int chi_r, const void *A, int dtype) {
+    if (!A) return fail(h, FASTMPS_ERR_INVALID_ARG, "tensor pointer is NULL");
+    if (dtype != FASTMPS_C64 && dtype != FASTMPS_C128) return fail(h, FASTMPS_ERR_INVALID_ARG, "unknown dtype");
+    if (chi_l < 1 || chi_r < 1 || d < 2 || d > 255)
+        return fail(h, FASTMPS_ERR_SHAPE, "need chi_l >= 1, chi_r >= 1, 2 <= d <= 255");
+    if ((int64_t)d * chi_r < chi_l) return fail(h, FASTMPS_ERR_SHAPE, "d * chi_r < chi_l: not an isometry shape");
+    if ((int64_t)chi_l > (1 << 20) || (int64_t)chi_r > (1 << 20))
+        return fail(h, FASTMPS_ERR_SHAPE, "bond dimension above 2^20");
+    return FASTMPS_OK;
+}
+
+// Copy and repack one tensor into t.
+int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const void *A, int dtype) {
+    int rc = check_shape_args(h, chi_l, d, chi_r, A, dtype);
+    if (rc) return rc;
+    t.L = make_layout(h->opt.precision, chi_l, d, chi_r);
+    const int64_t nelem = (int64_t)chi_l * d * chi_r;
+    const size_t src_bytes = (size_t)nelem * (dtype == FASTMPS_C128 ? 16 : 8);
+    cudaError_t e;
+    if (h->opt.residency == FASTMPS_HOST_STREAM) {
+        // compact BF16 copy in pinned host memory
+        t.planes = h->opt.precision == FASTMPS_BF16X3 ? 2 : 1;
+        t.host_compact.host = true;
+        if (!t.host_compact.ensure((size_t)nelem * 2 * 2 * t.planes))
+            return fail(h, FASTMPS_ERR_OOM, "pinned host allocation for a streamed tensor failed");
+        uint16_t *dst = t.host_compact.as<uint16_t>();
+        const int64_t n2 = nelem * 2;
+        for (int64_t i = 0; i < n2; ++i) {
+            float x = dtype == FASTMPS_C128 ? (float)static_cast<const double *>(A)[i]
+                                            : static_cast<const float *>(A)[i];
+            uint16_t hb = host_bf16_bits(x);
+            dst[i] = hb;
+            if (t.planes > 1) dst[n2 + i] = host_bf16_bits(x - host_bf16_float(hb));
+        }
+        return FASTMPS_OK;
+    }
+    if (!h->staging.ensure(src_bytes)) return fail(h, FASTMPS_ERR_OOM, "staging allocation failed");
+    e = cudaMemcpyAsync(h->staging.p, A, src_bytes, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy of site tensor");
+    const size_t op_elems = (size_t)t.L.ncols * t.L.K_pad;
+    if (is_bf16(h)) {
+        if (!t.B_hi.ensure(op_elems * 2)) return fail(h, FASTMPS_ERR_OOM, "site operand allocation failed");
+        __nv_bfloat16 *lo = nullptr;
+        if (h->opt.precision == FASTMPS_BF16X3) {
+            if (!t.B_lo.ensure(op_elems * 2)) return fail(h, FASTMPS_ERR_OOM, "site operand allocation failed");
+            lo = t.B_lo.as<__nv_bfloat16>();
+        }
+        launch_repack_bf16(h->staging.p, dtype == FASTMPS_C128, t.L, t.B_hi.as<__nv_bfloat16>(), lo, h->stream);
+        if (!encode_2d_bf16(&t.tmB[0], t.B_hi.p, t.L.K_pad, t.L.ncols, t.L.K_pad, 64, t.L.bn))
+            return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+        if (lo && !encode_2d_bf16(&t.tmB[1], t.B_lo.p, t.L.K_pad, t.L.ncols, t.L.K_pad, 64, t.L.bn))
+            return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+        if (!lo) t.tmB[1] = t.tmB[0];
+    } else {
+        if (!t.Bt.ensure(op_elems * 4)) return fail(h, FASTMPS_ERR_OOM, "site operand allocation failed");
+        launch_repack_f32(h->staging.p, dtype == FASTMPS_C128, t.L, t.Bt.as<float>(), h->stream);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "repack launch");
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "repack");
+    return FASTMPS_OK;
+}
+
+Tensor *site_tensor_of(fastmps_handle h, int k) {
+    auto it = h->site_pool.find(k);
+    if (it != h->site_pool.end()) {
+        auto p = h->pool_tensor.find(it->second);
+        return p == h->pool_tensor.end() ? nullptr : p->second.get();
+    }
+    auto s = h->site_tensor.find(k);
+    return s == h->site_tensor.end() ? nullptr : s->second.get();
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct EventTimer {
+    fastmps_handle h;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> contract, measure;
+    size_t used = 0;
+    explicit EventTimer(fastmps_handle hh) : h(hh) {}
+    cudaEvent_t get() {
+        if (used == h->ev_pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            h->ev_pool.push_back(e);
+        }
+        return h->ev_pool[used++];
+    }
+    double total(const std::vector<std::pair<cudaEvent_t, cudaEvent_t>> &v) {
+        double s = 0;
+        for (auto &p : v) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, p.first, p.second);
+            s += ms;
+        }
+        return s;
+    }
+};
+
+int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int64_t N, uint64_t seed, uint32_t job,
+               uint8_t *out_samples, double *out_logprob, int64_t trace_rows, double *trace_probs) {
+    auto t_start = std::chrono::steady_clock::now();
+    h->stats = fastmps_stats{};
+    if (M < 1 || !bonds || N < 0 || n0 < 0) return fail(h, FASTMPS_ERR_INVALID_ARG, "need M >= 1, bonds, N >= 0, n0 >= 0");
+    if (d < 2 || d > 255) return fail(h, FASTMPS_ERR_SHAPE, "need 2 <= d <= 255");
+    if (bonds[0] != 1 || bonds[M] != 1) return fail(h, FASTMPS_ERR_SHAPE, "bond_dims[0] and bond_dims[M] must be 1");
+    if (trace_rows < 0 || (trace_rows > 0 && !trace_probs))
+        return fail(h, FASTMPS_ERR_INVALID_ARG, "trace_rows > 0 needs trace_probs");
+    std::vector<Tensor *> ts(M);
+    int ldV = 64;
+    int ncols_max = 0, ldP_max = 0;
+    double flops = 0;
+    for (int k = 0; k < M; ++k) {
+        Tensor *t = site_tensor_of(h, k);
+        if (!t) return fail(h, FASTMPS_ERR_NOT_LOADED, "site " + std::to_string(k) + " is not loaded");
+        if (t->L.chi_l != bonds[k] || t->L.d != d || t->L.chi_r != bonds[k + 1])
+            return fail(h, FASTMPS_ERR_SHAPE, "site " + std::to_string(k) + " was loaded with shape (" +
+                                                  std::to_string(t->L.chi_l) + ", " + std::to_string(t->L.d) + ", " +
+                                                  std::to_string(t->L.chi_r) + ") but bond_dims/d say (" +
+                                                  std::to_string(bonds[k]) + ", " + std::to_string(d) + ", " +
+                                                  std::to_string(bonds[k + 1]) + ")");
+        ts[k] = t;
+        ldV = std::max(ldV, t->L.K_pad);
+        ncols_max = std::max(ncols_max, t->L.ncols);
+        ldP_max = std::max(ldP_max, t->L.ncols / t->L.bn);
+        flops += 8.0 * bonds[k] * d * bonds[k + 1];
+    }
+    const int prods = h->opt.precision == FASTMPS_BF16X3 ? 3 : (h->opt.precision == FASTMPS_BF16X2 ? 2 : 1);
+    h->stats.flops_algorithmic = flops * (double)N;
+    h->stats.flops_issued = flops * (double)N * prods;
+    if (N == 0) return FASTMPS_OK;
+    const bool stream_mode = h->opt.residency == FASTMPS_HOST_STREAM;
+    const bool bf16 = is_bf16(h);
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+
+    // ---- plan ---------------------------------------------------------------
+    const int64_t N_pad = roundup(N, 128);
+    int64_t N2;
+    if (h->opt.max_microbatch > 0) {
+        N2 = std::max<int64_t>(128, h->opt.max_microbatch / 128 * 128);
+    } else {
+        const int64_t budget = (int64_t)2 << 30;  // bytes of FP32 scratch per micro-batch
+        N2 = std::max<int64_t>(128, budget / ((int64_t)ncols_max * 4) / 128 * 128);
+    }
+    N2 = std::min(N2, N_pad);
+
+    // ---- buffers -------------------------------------------------------------
+    const int planes = bf16 ? 2 : 1;
+    const size_t elem = bf16 ? 2 : 4;
+    for (int x = 0; x < 2; ++x)
+        for (int p = 0; p < planes; ++p)
+            if (!h->V[x][p].ensure((size_t)N_pad * ldV * elem))
+                return fail(h, FASTMPS_ERR_OOM, "left-operand allocation failed");
+    if (!h->Y.ensure((size_t)N2 * ncols_max * 4) || !h->P.ensure((size_t)N2 * ldP_max * 4) ||
+        !h->logp.ensure((size_t)N_pad * 8) || !h->O.ensure((size_t)M * N_pad) || !h->err.ensure(sizeof(int)))
+        return fail(h, FASTMPS_ERR_OOM, "work-buffer allocation failed");
+    const bool samples_dev = is_device_ptr(out_samples);
+    const bool logp_dev = is_device_ptr(out_logprob);
+    const bool trace_dev = is_device_ptr(trace_probs);
+    if (out_samples && !samples_dev && !h->Dout.ensure((size_t)N * M))
+        return fail(h, FASTMPS_ERR_OOM, "output staging allocation failed");
+    double *trace_buf = nullptr;
+    if (trace_rows > 0) {
+        trace_rows = std::min(trace_rows, N);
+        if (trace_dev) trace_buf = trace_probs;
+        else {
+            if (!h->trace.ensure((size_t)M * trace_rows * d * 8)) return fail(h, FASTMPS_ERR_OOM, "trace allocation failed");
+            trace_buf = h->trace.as<double>();
+        }
+    }
+    if (stream_mode) {
+        size_t cmax = 0, opmax = 0;
+        for (int k = 0; k < M; ++k) {
+            cmax = std::max(cmax, ts[k]->host_compact.bytes);
+            opmax = std::max(opmax, (size_t)ts[k]->L.ncols * ts[k]->L.K_pad * 2);
+        }
+        if (!h->slot_compact[0].ensure(cmax) || !h->slot_compact[1].ensure(cmax) || !h->slot_hi.ensure(opmax) ||
+            (h->opt.precision == FASTMPS_BF16X3 && !h->slot_lo.ensure(opmax)))
+            return fail(h, FASTMPS_ERR_OOM, "streaming slot allocation failed");
+    }
+
+    int *d_err = h->err.as<int>();
+    e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    cudaMemsetAsync(h->logp.p, 0, (size_t)N_pad * 8, st);
+    if (bf16)
+        launch_init_left_bf16(h->V[0][0].as<__nv_bfloat16>(), h->V[0][1].as<__nv_bfloat16>(), N_pad, ldV, st);
+    else
+        launch_init_left_f32(h->V[0][0].as<float>(), N_pad, ldV, st);
+    h->stats.launches += 1;
+
+    EventTimer timer(h);
+    const bool timing = true;
+
+    // streaming: prefetch site 0
+    auto issue_copy = [&](int k) -> cudaError_t {
+        const int slot = k & 1;
+        cudaError_t ee = cudaStreamWaitEvent(h->copy_stream, h->slot_free[slot], 0);
+        if (ee != cudaSuccess) return ee;
+        ee = cudaMemcpyAsync(h->slot_compact[slot].p, ts[k]->host_compact.p, ts[k]->host_compact.bytes,
+                             cudaMemcpyHostToDevice, h->copy_stream);
+        if (ee != cudaSuccess) return ee;
+        h->stats.h2d_bytes += (int64_t)ts[k]->host_compact.bytes;
+        return cudaEventRecord(h->copy_done[slot], h->copy_stream);
+    };
+    if (stream_mode) {
+        // the copy stream must not run ahead of work already queued on the compute stream
+        cudaEvent_t ev0 = timer.get();
+        cudaEventRecord(ev0, st);
+        cudaStreamWaitEvent(h->copy_stream, ev0, 0);
+        e = issue_copy(0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "site copy");
+    }
+
+    for (int k = 0; k < M; ++k) {
+        Tensor *t = ts[k];
+        const SiteLayout &L = t->L;
+        const int cur = k & 1, nxt = cur ^ 1;
+        const int K_next = k + 1 < M ? ts[k + 1]->L.K_pad : 64;
+        TcArgs ta;
+        if (bf16) {
+            const __nv_bfloat16 *Bh = t->B_hi.as<__nv_bfloat16>();
+            const __nv_bfloat16 *Bl = t->B_lo.as<__nv_bfloat16>();
+            if (stream_mode) {
+                if (k + 1 < M) {
+                    e = issue_copy(k + 1);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "site copy");
+                }
+                cudaStreamWaitEvent(st, h->copy_done[cur], 0);
+                __nv_bfloat16 *lo = h->opt.precision == FASTMPS_BF16X3 ? h->slot_lo.as<__nv_bfloat16>() : nullptr;
+                launch_expand_bf16(h->slot_compact[cur].as<__nv_bfloat16>(), t->planes, L,
+                                   h->slot_hi.as<__nv_bfloat16>(), lo, st);
+                h->stats.launches += 1;
+                cudaEventRecord(h->slot_free[cur], st);
+                Bh = h->slot_hi.as<__nv_bfloat16>();
+                Bl = lo;
+                if (!encode_2d_bf16(&ta.tmB[0], Bh, L.K_pad, L.ncols, L.K_pad, 64, L.bn) ||
+                    (Bl && !encode_2d_bf16(&ta.tmB[1], Bl, L.K_pad, L.ncols, L.K_pad, 64, L.bn)))
+                    return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+                if (!Bl) ta.tmB[1] = ta.tmB[0];
+            } else {
+                ta.tmB[0] = t->tmB[0];
+                ta.tmB[1] = t->tmB[1];
+            }
+            ta.a_planes = 2;
+            ta.b_planes = h->opt.precision == FASTMPS_BF16X3 ? 2 : 1;
+            if (!encode_2d_bf16(&ta.tmA[0], h->V[cur][0].p, L.K_pad, N_pad, ldV, 64, 128) ||
+                !encode_2d_bf16(&ta.tmA[1], h->V[cur][1].p, L.K_pad, N_pad, ldV, 64, 128))
+                return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+        }
+        for (int64_t r0 = 0; r0 < N; r0 += N2) {
+            const int64_t rows = std::min<int64_t>(N2, N - r0);
+            const int64_t rows_pad = roundup(rows, 128);
+            ContractOut co;
+            co.Y = h->Y.as<float>();
+            co.ldY = L.ncols;
+            co.P = h->P.as<float>();
+            co.ldP = L.ncols / L.bn;
+            co.rows_valid = (int)rows;
+            cudaEvent_t c0 = nullptr, c1 = nullptr, m1 = nullptr;
+            if (timing) {
+                c0 = timer.get();
+                cudaEventRecord(c0, st);
+            }
+            if (bf16) {
+                ta.row0 = r0;
+                ta.rows_pad = (int)rows_pad;
+                e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "contraction launch");
+            } else {
+                launch_contract_f32(h->V[cur][0].as<float>(), ldV, r0, rows_pad, t->Bt.as<float>(), L, co, st);
+            }
+            h->stats.launches += 1;
+            h->stats.contract_launches += 1;
+            if (timing) {
+                c1 = timer.get();
+                cudaEventRecord(c1, st);
+            }
+            MeasureArgs ma;
+            ma.Y = co.Y;
+            ma.ldY = co.ldY;
+            ma.P = co.P;
+            ma.ldP = co.ldP;
+            ma.d = d;
+            ma.chi_r = L.chi_r;
+            ma.Cs = L.Cs;
+            ma.tiles_per_s = L.tiles_per_s;
+            ma.rows = (int)rows;
+            ma.seed = seed;
+            ma.n_base = (uint64_t)(n0 + r0);
+            ma.k = (uint32_t)k;
+            ma.job = job;
+            ma.row0 = r0;
+            ma.ld_next = ldV;
+            ma.K_next = K_next;
+            ma.V32 = bf16 ? nullptr : h->V[nxt][0].as<float>();
+            ma.Vhi = bf16 ? h->V[nxt][0].as<__nv_bfloat16>() : nullptr;
+            ma.Vlo = bf16 ? h->V[nxt][1].as<__nv_bfloat16>() : nullptr;
+            ma.outcomes = h->O.as<uint8_t>() + (int64_t)k * N_pad + r0;
+            ma.logp = h->logp.as<double>();
+            ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
+            ma.trace_rows = (int)trace_rows;
+            ma.err = d_err;
+            launch_measure(ma, st);
+            h->stats.launches += 1;
+            if (timing) {
+                m1 = timer.get();
+                cudaEventRecord(m1, st);
+                timer.contract.push_back({c0, c1});
+                timer.measure.push_back({c1, m1});
+            }
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+        }
+    }
+
+    // ---- outputs -------------------------------------------------------------
+    if (out_samples) {
+        uint8_t *dst = samples_dev ? out_samples : h->Dout.as<uint8_t>();
+        launch_transpose_outcomes(h->O.as<uint8_t>(), N_pad, N, M, dst, st);
+        h->stats.launches += 1;
+        if (!samples_dev) {
+            e = cudaMemcpyAsync(out_samples, dst, (size_t)N * M, cudaMemcpyDeviceToHost, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy of samples");
+            h->stats.d2h_bytes += (int64_t)N * M;
+        }
+    }
+    if (out_logprob) {
+        e = cudaMemcpyAsync(out_logprob, h->logp.p, (size_t)N * 8,
+                            logp_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of log-probabilities");
+        if (!logp_dev) h->stats.d2h_bytes += N * 8;
+    }
+    if (trace_buf && !trace_dev) {
+        e = cudaMemcpyAsync(trace_probs, trace_buf, (size_t)M * trace_rows * d * 8, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of trace");
+    }
+    int herr = 0;
+    e = cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy of error word");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sampling");
+    if (timing) {
+        h->stats.ms_contract = timer.total(timer.contract);
+        h->stats.ms_measure = timer.total(timer.measure);
+    }
+    h->stats.ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (herr == kDevNumeric)
+        return fail(h, FASTMPS_ERR_NUMERIC, "a sample's probabilities summed to zero or a non-finite value");
+    if (herr != 0)
+        return fail(h, FASTMPS_ERR_TIMEOUT,
+                    "a bounded device wait in the contraction kernel gave up (code " + std::to_string(herr) + ")");
+    return FASTMPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void fastmps_default_options(fastmps_options *opt) {
+    if (!opt) return;
+    opt->precision = FASTMPS_FP32;
+    opt->residency = FASTMPS_RESIDENT_HBM;
+    opt->max_microbatch = 0;
+    opt->autotune = 0;
+    opt->stream = nullptr;
+}
+
+int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) {
+    if (!out) {
+        g_create_error = "out is NULL";
+        return FASTMPS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    fastmps_options o;
+    fastmps_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_BF16X3) {
+        g_create_error = "unknown precision";
+        return FASTMPS_ERR_INVALID_ARG;
+    }
+    if (o.residency != FASTMPS_RESIDENT_HBM && o.residency != FASTMPS_HOST_STREAM) {
+        g_create_error = "unknown residency";
+        return FASTMPS_ERR_INVALID_ARG;
+    }
+    if (o.residency == FASTMPS_HOST_STREAM && o.precision == FASTMPS_FP32) {
+        g_create_error = "host streaming keeps BF16 tensors: use a BF16 precision";
+        return FASTMPS_ERR_UNSUPPORTED;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        g_create_error = "no such CUDA device";
+        return FASTMPS_ERR_CUDA;
+    }
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, device);
+    if (!(prop.major == 10 && prop.minor == 3)) {
+        g_create_error = std::string("device ") + prop.name + " is sm_" + std::to_string(prop.major) +
+                         std::to_string(prop.minor) + "; this library is built for sm_103a only";
+        return FASTMPS_ERR_UNSUPPORTED;
+    }
+    if (o.precision != FASTMPS_FP32 && (!tc_max_smem_ok(device) || !get_encode_fn())) {
+        g_create_error = "tensor-core path needs 227 KB shared memory and cuTensorMapEncodeTiled";
+        return FASTMPS_ERR_UNSUPPORTED;
+    }
+    fastmps_ctx *h = new (std::nothrow) fastmps_ctx();
+    if (!h) {
+        g_create_error = "out of host memory";
+        return FASTMPS_ERR_OOM;
+    }
+    h->device = device;
+    h->opt = o;
+    h->num_sms = prop.multiProcessorCount;
+    cudaSetDevice(device);
+    if (o.stream) {
+        h->stream = static_cast<cudaStream_t>(o.stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete h;
+            g_create_error = "stream creation failed";
+            return FASTMPS_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventCreateWithFlags(&h->copy_done[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&h->slot_free[i], cudaEventDisableTiming);
+    }
+    h->staging.host = false;
+    *out = h;
+    return FASTMPS_OK;
+}
+
+void fastmps_destroy(fastmps_handle h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i) {
+        if (h->copy_done[i]) cudaEventDestroy(h->copy_done[i]);
+        if (h->slot_free[i]) cudaEventDestroy(h->slot_free[i]);
+    }
+    if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char *fastmps_last_error(fastmps_handle h) {
+    if (!h) return g_create_error.c_str();
+    return h->last_error.c_str();
+}
+
+int fastmps_load_site(fastmps_handle h, int k, int chi_l, int d, int chi_r, const void *A, int dtype) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    if (k < 0 || k >= 65536) return fail(h, FASTMPS_ERR_INVALID_ARG, "site index out of range");
+    cudaSetDevice(h->device);
+    std::unique_ptr<Tensor> t(new (std::nothrow) Tensor());
+    if (!t) return fail(h, FASTMPS_ERR_OOM, "out of host memory");
+    int rc = load_tensor(h, *t, chi_l, d, chi_r, A, dtype);
+    if (rc) return rc;
+    h->site_tensor[k] = std::move(t);
+    h->site_pool.erase(k);
+    return FASTMPS_OK;
+}
+
+int fastmps_load_pool(fastmps_handle h, int j, int chi_l, int d, int chi_r, const void *A, int dtype) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    if (j < 0 || j >= 65536) return fail(h, FASTMPS_ERR_INVALID_ARG, "pool index out of range");
+    cudaSetDevice(h->device);
+    std::unique_ptr<Tensor> t(new (std::nothrow) Tensor());
+    if (!t) return fail(h, FASTMPS_ERR_OOM, "out of host memory");
+    int rc = load_tensor(h, *t, chi_l, d, chi_r, A, dtype);
+    if (rc) return rc;
+    h->pool_tensor[j] = std::move(t);
+    return FASTMPS_OK;
+}
+
+int fastmps_map_site(fastmps_handle h, int k, int j) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    if (k < 0 || k >= 65536) return fail(h, FASTMPS_ERR_INVALID_ARG, "site index out of range");
+    if (h->pool_tensor.find(j) == h->pool_tensor.end())
+        return fail(h, FASTMPS_ERR_NOT_LOADED, "pool entry " + std::to_string(j) + " is not loaded");
+    h->site_pool[k] = j;
+    h->site_tensor.erase(k);
+    return FASTMPS_OK;
+}
+
+int fastmps_sample_ex(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N, uint64_t seed,
+                      uint32_t job, uint8_t *out_samples, double *out_logprob, int64_t trace_rows,
+                      double *trace_probs) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    try {
+        return run_sample(h, M, d, bond_dims, n0, N, seed, job, out_samples, out_logprob, trace_rows, trace_probs);
+    } catch (const std::bad_alloc &) {
+        return fail(h, FASTMPS_ERR_OOM, "out of host memory");
+    } catch (...) {
+        return fail(h, FASTMPS_ERR_CUDA, "unexpected host exception");
+    }
+}
+
+int fastmps_sample(fastmps_handle h, int M, int d, const int *bond_dims, int64_t N, uint64_t seed,
+                   uint8_t *out_samples, double *out_logprob) {
+    return fastmps_sample_ex(h, M, d, bond_dims, 0, N, seed, 0, out_samples, out_logprob, 0, nullptr);
+}
+
+int fastmps_get_stats(fastmps_handle h, fastmps_stats *out) {
+    if (!h || !out) return FASTMPS_ERR_INVALID_ARG;
+    *out = h->stats;
+    return FASTMPS_OK;
+}
+
+const char *fastmps_version(void) { return "fastmps-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,371 @@
+// Site-tensor repacking, FP32 SIMT contraction, measurement (Algorithm 2) and
+// output transposition kernels.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace fastmps {
+
+// ---------------------------------------------------------------------------
+// Stacked real operand of the complex contraction.
+//
+// With v = vr + i vi and A = Ar + i Ai, y = v A has
+//   Re y =  vr Ar - vi Ai,   Im y = vr Ai + vi Ar,
+// so with the left row [vr | vi] (length 2 chi_l) the output column
+// (s, p = 0, b) takes the operand column [Ar[:, s, b] ; -Ai[:, s, b]] and the
+// column (s, p = 1, b) takes [Ai[:, s, b] ; Ar[:, s, b]].  That is four real
+// products per complex multiply-add, 8 chi_l d chi_r flops per sample.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float load_part(const void *src, int is_f64, int64_t cidx, int part) {
+    if (is_f64) return (float)(static_cast<const double *>(src)[2 * cidx + part]);
+    return static_cast<const float *>(src)[2 * cidx + part];
+}
+
+// Returns the operand value at output column c and reduction index kappa and
+// sets *zero when the position is padding.  (re_part, sign) say which part of
+// A[a, s, b] it is: value = sign * (re_part ? Re : Im) A[a, s, b].
+struct StackedPos {
+    int64_t cidx;  // complex index a*d*chi_r + s*chi_r + b
+    int re_part;   // 1: real part, 0: imaginary part
+    float sign;
+    bool zero;
+};
+
+__device__ __forceinline__ StackedPos stacked_pos(int c, int kappa, int chi_l, int d, int chi_r, int Cs) {
+    StackedPos q;
+    const int s = c / Cs;
+    const int r = c - s * Cs;
+    q.zero = (r >= 2 * chi_r) || (kappa >= 2 * chi_l) || (s >= d);
+    if (q.zero) {
+        q.cidx = 0;
+        q.re_part = 1;
+        q.sign = 0.f;
+        return q;
+    }
+    const int p = r >= chi_r;
+    const int b = r - p * chi_r;
+    const int second = kappa >= chi_l;
+    const int a = second ? kappa - chi_l : kappa;
+    q.cidx = ((int64_t)a * d + s) * chi_r + b;
+    if (p == 0) {  // real output column: [Ar ; -Ai]
+        q.re_part = second ? 0 : 1;
+        q.sign = second ? -1.f : 1.f;
+    } else {       // imaginary output column: [Ai ; Ar]
+        q.re_part = second ? 1 : 0;
+        q.sign = 1.f;
+    }
+    return q;
+}
+
+__global__ void repack_bf16_kernel(const void *__restrict__ src, int is_f64, int chi_l, int d, int chi_r, int Cs,
+                                   int ncols, int K_pad, __nv_bfloat16 *__restrict__ B_hi,
+                                   __nv_bfloat16 *__restrict__ B_lo) {
+    const int64_t total = (int64_t)ncols * K_pad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / K_pad);
+        const int kappa = (int)(i - (int64_t)c * K_pad);
+        const StackedPos q = stacked_pos(c, kappa, chi_l, d, chi_r, Cs);
+        float x = 0.f;
+        if (!q.zero) x = q.sign * load_part(src, is_f64, q.cidx, q.re_part ? 0 : 1);
+        __nv_bfloat16 hi, lo;
+        split_bf16(x, hi, lo);
+        B_hi[i] = hi;
+        if (B_lo) B_lo[i] = lo;
+    }
+}
+
+__global__ void expand_bf16_kernel(const __nv_bfloat16 *__restrict__ compact, int planes, int chi_l, int d,
+                                   int chi_r, int Cs, int ncols, int K_pad, __nv_bfloat16 *__restrict__ B_hi,
+                                   __nv_bfloat16 *__restrict__ B_lo) {
+    const int64_t total = (int64_t)ncols * K_pad;
+    const int64_t plane = (int64_t)chi_l * d * chi_r * 2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / K_pad);
+        const int kappa = (int)(i - (int64_t)c * K_pad);
+        const StackedPos q = stacked_pos(c, kappa, chi_l, d, chi_r, Cs);
+        __nv_bfloat16 hi = __float2bfloat16_rn(0.f), lo = hi;
+        if (!q.zero) {
+            const int64_t e = 2 * q.cidx + (q.re_part ? 0 : 1);
+            hi = compact[e];
+            if (q.sign < 0.f) hi = __hneg(hi);
+            if (planes > 1) {
+                lo = compact[plane + e];
+                if (q.sign < 0.f) lo = __hneg(lo);
+            }
+        }
+        B_hi[i] = hi;
+        if (B_lo) B_lo[i] = lo;
+    }
+}
+
+__global__ void repack_f32_kernel(const void *__restrict__ src, int is_f64, int chi_l, int d, int chi_r, int Cs,
+                                  int ncols, int K_pad, float *__restrict__ Bt) {
+    const int64_t total = (int64_t)ncols * K_pad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int kappa = (int)(i / ncols);
+        const int c = (int)(i - (int64_t)kappa * ncols);
+        const StackedPos q = stacked_pos(c, kappa, chi_l, d, chi_r, Cs);
+        float x = 0.f;
+        if (!q.zero) x = q.sign * load_part(src, is_f64, q.cidx, q.re_part ? 0 : 1);
+        Bt[i] = x;
+    }
+}
+
+static int grid_for(int64_t total, int block) {
+    int64_t g = (total + block - 1) / block;
+    if (g > 152 * 32) g = 152 * 32;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+void launch_repack_bf16(const void *src, int is_f64, const SiteLayout &L, __nv_bfloat16 *B_hi, __nv_bfloat16 *B_lo,
+                        cudaStream_t st) {
+    const int64_t total = (int64_t)L.ncols * L.K_pad;
+    repack_bf16_kernel<<<grid_for(total, 256), 256, 0, st>>>(src, is_f64, L.chi_l, L.d, L.chi_r, L.Cs, L.ncols,
+                                                              L.K_pad, B_hi, B_lo);
+}
+
+void launch_expand_bf16(const __nv_bfloat16 *compact, int planes, const SiteLayout &L, __nv_bfloat16 *B_hi,
+                        __nv_bfloat16 *B_lo, cudaStream_t st) {
+    const int64_t total = (int64_t)L.ncols * L.K_pad;
+    expand_bf16_kernel<<<grid_for(total, 256), 256, 0, st>>>(compact, planes, L.chi_l, L.d, L.chi_r, L.Cs, L.ncols,
+                                                              L.K_pad, B_hi, B_lo);
+}
+
+void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *Bt, cudaStream_t st) {
+    const int64_t total = (int64_t)L.ncols * L.K_pad;
+    repack_f32_kernel<<<grid_for(total, 256), 256, 0, st>>>(src, is_f64, L.chi_l, L.d, L.chi_r, L.Cs, L.ncols,
+                                                             L.K_pad, Bt);
+}
+
+// ---------------------------------------------------------------------------
+// Left boundary v_0 = [1]: row = [1, 0, ..., 0] (real part 1, imaginary 0).
+// ---------------------------------------------------------------------------
+__global__ void init_left_bf16_kernel(__nv_bfloat16 *V_hi, __nv_bfloat16 *V_lo, int64_t rows, int ld) {
+    const int64_t total = rows * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const bool one = (i % ld) == 0;
+        V_hi[i] = __float2bfloat16_rn(one ? 1.f : 0.f);
+        if (V_lo) V_lo[i] = __float2bfloat16_rn(0.f);
+    }
+}
+
+__global__ void init_left_f32_kernel(float *V, int64_t rows, int ld) {
+    const int64_t total = rows * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        V[i] = (i % ld) == 0 ? 1.f : 0.f;
+}
+
+void launch_init_left_bf16(__nv_bfloat16 *V_hi, __nv_bfloat16 *V_lo, int64_t rows, int ld, cudaStream_t st) {
+    init_left_bf16_kernel<<<grid_for(rows * ld, 256), 256, 0, st>>>(V_hi, V_lo, rows, ld);
+}
+
+void launch_init_left_f32(float *V, int64_t rows, int ld, cudaStream_t st) {
+    init_left_f32_kernel<<<grid_for(rows * ld, 256), 256, 0, st>>>(V, rows, ld);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 SIMT contraction (the plain path): Y = V Bt over a 128 x 128 tile per
+// block, 8 x 8 outputs per thread, K staged 8 at a time in double-buffered
+// shared memory.  Epilogue: store the tile to the FP32 scratch and one sum of
+// squares per row (the tile lies inside one outcome block s).
+// ---------------------------------------------------------------------------
+constexpr int F32_BM = 128, F32_BN = 128, F32_BK = 8, F32_THREADS = 256;
+
+__global__ void __launch_bounds__(F32_THREADS, 2)
+contract_f32_kernel(const float *__restrict__ V, int64_t ldV, int64_t row0, const float *__restrict__ Bt, int ldB,
+                    int K, float *__restrict__ Y, int64_t ldY, float *__restrict__ P, int ldP, int rows_valid) {
+    __shared__ __align__(16) float As[2][F32_BK][F32_BM];
+    __shared__ __align__(16) float Bs[2][F32_BK][F32_BN];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * F32_BM;
+    const int n0 = blockIdx.x * F32_BN;
+    const float *Ag = V + (row0 + m0) * ldV;
+    const int a_row = tid >> 1, a_k = (tid & 1) * 4;
+    const int b_k = tid >> 5, b_n = (tid & 31) * 4;
+
+    float4 ra = *reinterpret_cast<const float4 *>(Ag + (int64_t)a_row * ldV + a_k);
+    float4 rb = *reinterpret_cast<const float4 *>(Bt + (int64_t)b_k * ldB + n0 + b_n);
+    As[0][a_k + 0][a_row] = ra.x;
+    As[0][a_k + 1][a_row] = ra.y;
+    As[0][a_k + 2][a_row] = ra.z;
+    As[0][a_k + 3][a_row] = ra.w;
+    *reinterpret_cast<float4 *>(&Bs[0][b_k][b_n]) = rb;
+    __syncthreads();
+
+    const int ty = tid >> 4, tx = tid & 15;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    const int nk = K / F32_BK;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) {
+            const int k0 = (kt + 1) * F32_BK;
+            ra = *reinterpret_cast<const float4 *>(Ag + (int64_t)a_row * ldV + k0 + a_k);
+            rb = *reinterpret_cast<const float4 *>(Bt + (int64_t)(k0 + b_k) * ldB + n0 + b_n);
+        }
+#pragma unroll
+        for (int kk = 0; kk < F32_BK; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[cur][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[cur][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[cur][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[cur][kk][64 + tx * 4]);
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (kt + 1 < nk) {
+            const int nxt = cur ^ 1;
+            As[nxt][a_k + 0][a_row] = ra.x;
+            As[nxt][a_k + 1][a_row] = ra.y;
+            As[nxt][a_k + 2][a_row] = ra.z;
+            As[nxt][a_k + 3][a_row] = ra.w;
+            *reinterpret_cast<float4 *>(&Bs[nxt][b_k][b_n]) = rb;
+        }
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        float ss = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ss = fmaf(acc[i][j], acc[i][j], ss);
+        ss += __shfl_xor_sync(0xffffffffu, ss, 1);
+        ss += __shfl_xor_sync(0xffffffffu, ss, 2);
+        ss += __shfl_xor_sync(0xffffffffu, ss, 4);
+        ss += __shfl_xor_sync(0xffffffffu, ss, 8);
+        if (r < rows_valid) {
+            float *yr = Y + (int64_t)r * ldY + n0;
+            *reinterpret_cast<float4 *>(yr + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            *reinterpret_cast<float4 *>(yr + 64 + tx * 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+            if (tx == 0) P[(int64_t)r * ldP + blockIdx.x] = ss;
+        }
+    }
+}
+
+void launch_contract_f32(const float *V, int64_t ldV, int64_t row0, int64_t rows_pad, const float *Bt,
+                         const SiteLayout &L, const ContractOut &o, cudaStream_t st) {
+    dim3 grid(L.ncols / F32_BN, (unsigned)(rows_pad / F32_BM));
+    contract_f32_kernel<<<grid, F32_THREADS, 0, st>>>(V, ldV, row0, Bt, L.ncols, L.K_pad, o.Y, o.ldY, o.P, o.ldP,
+                                                       o.rows_valid);
+}
+
+// ---------------------------------------------------------------------------
+// Measurement (Algorithm 2 with the exact per-sample rescaling of Sec. 3.3.1).
+// One warp per sample: combine the per-tile sums of squares of each outcome
+// block in FP64 (w_s), cumulative sum in s order, Philox uniform, outcome
+// s* = #{s < d-1 : C_s < u Z}, log-probability, then write the selected block
+// y_{s*} / sqrt(w_{s*}) as the next left row (FP32, or BF16 hi + lo).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+constexpr int MEASURE_THREADS = 256;
+
+__global__ void __launch_bounds__(MEASURE_THREADS) measure_kernel(const MeasureArgs a) {
+    extern __shared__ double sw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * (MEASURE_THREADS / 32) + warp;
+    if (row >= a.rows) return;
+    double *w = sw + warp * a.d;
+    const float *Prow = a.P + (int64_t)row * a.ldP;
+    for (int s = 0; s < a.d; ++s) {
+        double acc = 0.0;
+        for (int j = lane; j < a.tiles_per_s; j += 32) acc += (double)Prow[s * a.tiles_per_s + j];
+        acc = warp_sum_f64(acc);
+        if (lane == 0) w[s] = acc;
+    }
+    __syncwarp();
+    // cumulative sum in s order; Z is the last partial sum
+    double Z = 0.0;
+    for (int s = 0; s < a.d; ++s) Z += w[s];
+    const uint64_t n = a.n_base + (uint64_t)row;
+    const double u = sample_uniform(a.seed, n, a.k, a.job);
+    const double t = u * Z;
+    int sstar = 0;
+    double C = 0.0;
+    for (int s = 0; s < a.d - 1; ++s) {
+        C += w[s];
+        if (C < t) ++sstar;
+    }
+    const double ws = w[sstar];
+    const bool ok = (Z > 0.0) && isfinite(Z) && (ws > 0.0);
+    const int64_t grow = a.row0 + row;
+    if (lane == 0) {
+        a.outcomes[row] = (uint8_t)sstar;
+        if (ok) a.logp[grow] += log(ws) - log(Z);
+        else atomicExch(a.err, (int)kDevNumeric);
+    }
+    if (a.trace && grow < a.trace_rows) {
+        for (int s = lane; s < a.d; s += 32) a.trace[grow * a.d + s] = ok ? w[s] / Z : 0.0;
+    }
+    const float scale = ok ? (float)(1.0 / sqrt(ws)) : 0.f;
+    const float *ysrc = a.Y + (int64_t)row * a.ldY + (int64_t)sstar * a.Cs;
+    const int nreal = 2 * a.chi_r;
+    if (a.V32) {
+        float *dst = a.V32 + grow * a.ld_next;
+        for (int i = lane; i < a.K_next; i += 32) dst[i] = i < nreal ? ysrc[i] * scale : 0.f;
+    } else {
+        __nv_bfloat16 *dh = a.Vhi + grow * a.ld_next;
+        __nv_bfloat16 *dl = a.Vlo ? a.Vlo + grow * a.ld_next : nullptr;
+        for (int i = lane; i < a.K_next; i += 32) {
+            const float x = i < nreal ? ysrc[i] * scale : 0.f;
+            __nv_bfloat16 hi, lo;
+            split_bf16(x, hi, lo);
+            dh[i] = hi;
+            if (dl) dl[i] = lo;
+        }
+    }
+}
+
+void launch_measure(const MeasureArgs &a, cudaStream_t st) {
+    if (a.rows <= 0) return;
+    const int rows_per_block = MEASURE_THREADS / 32;
+    const int grid = (a.rows + rows_per_block - 1) / rows_per_block;
+    const size_t smem = sizeof(double) * (size_t)rows_per_block * a.d;
+    measure_kernel<<<grid, MEASURE_THREADS, smem, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Outcomes are produced site-major (coalesced writes per site); the caller
+// wants sample-major rows.  32 x 32 byte tiles through shared memory.
+// ---------------------------------------------------------------------------
+__global__ void transpose_u8_kernel(const uint8_t *__restrict__ O, int64_t ldO, int64_t N, int M,
+                                    uint8_t *__restrict__ out) {
+    __shared__ uint8_t t[32][33];
+    const int64_t n0 = (int64_t)blockIdx.x * 32;
+    const int k0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int k = k0 + j;
+        const int64_t n = n0 + threadIdx.x;
+        if (k < M && n < N) t[j][threadIdx.x] = O[(int64_t)k * ldO + n];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int64_t n = n0 + j;
+        const int k = k0 + threadIdx.x;
+        if (k < M && n < N) out[n * M + k] = t[threadIdx.x][j];
+    }
+}
+
+void launch_transpose_outcomes(const uint8_t *O, int64_t ldO, int64_t N, int M, uint8_t *out, cudaStream_t st) {
+    if (N <= 0 || M <= 0) return;
+    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32));
+    transpose_u8_kernel<<<grid, dim3(32, 8), 0, st>>>(O, ldO, N, M, out);
+}
+
+}  // namespace fastmps

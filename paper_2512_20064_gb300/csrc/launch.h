@@ -1,0 +1,96 @@
+// Host-side launchers of the library's kernels (internal; not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fastmps {
+
+// Column layout of the contraction output of one site.  Output column
+// c = s * Cs + p * chi_r + b holds the real (p = 0) or imaginary (p = 1) part
+// of y_s[b]; columns chi_r*2 .. Cs-1 of each block are zero padding, so a tile
+// of width bn never straddles two outcomes s.  K = 2*chi_l rows of the stacked
+// real operand, padded to K_pad (a multiple of 64).
+struct SiteLayout {
+    int chi_l = 0, d = 0, chi_r = 0;
+    int bn = 0;        // n-tile width of the contraction kernel
+    int Cs = 0;        // columns per outcome block (multiple of bn)
+    int ncols = 0;     // d * Cs
+    int K_pad = 0;     // roundup(2 chi_l, 64)
+    int tiles_per_s = 0;
+};
+
+// ---- repack of a complex site tensor (device staging copy) -----------------
+// src: interleaved complex [chi_l][d][chi_r], float (is_f64 = 0) or double.
+// Tensor-core operand: B[c][kappa] (K-major, ld = K_pad), BF16 hi (and lo).
+void launch_repack_bf16(const void *src, int is_f64, const SiteLayout &L, __nv_bfloat16 *B_hi,
+                        __nv_bfloat16 *B_lo, cudaStream_t st);
+// Same from a compact BF16 complex copy [chi_l][d][chi_r] of (re, im) pairs
+// (planes = 1: hi only; planes = 2: hi block followed by lo block).
+void launch_expand_bf16(const __nv_bfloat16 *compact, int planes, const SiteLayout &L, __nv_bfloat16 *B_hi,
+                        __nv_bfloat16 *B_lo, cudaStream_t st);
+// FP32 SIMT operand: Bt[kappa][c] (N-major, ld = ncols), float.
+void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *Bt, cudaStream_t st);
+
+// ---- left operand ----------------------------------------------------------
+// Set rows [0, rows) of V to the boundary vector v_0 = [1] (row = [1, 0, ... 0], ld elements).
+void launch_init_left_bf16(__nv_bfloat16 *V_hi, __nv_bfloat16 *V_lo, int64_t rows, int ld, cudaStream_t st);
+void launch_init_left_f32(float *V, int64_t rows, int ld, cudaStream_t st);
+
+// ---- contraction kernels ---------------------------------------------------
+struct ContractOut {
+    float *Y;          // [rows_pad][ldY] FP32 scratch
+    int64_t ldY;
+    float *P;          // [rows_pad][ldP] per-tile sums of squares
+    int ldP;
+    int rows_valid;    // rows of this micro-batch
+};
+
+// FP32 SIMT: Y = V[row0 : row0+rows_pad] (ld = ldV, K = L.K_pad) x Bt.
+void launch_contract_f32(const float *V, int64_t ldV, int64_t row0, int64_t rows_pad, const float *Bt,
+                         const SiteLayout &L, const ContractOut &o, cudaStream_t st);
+
+// tcgen05 BF16 split-precision contraction.  tmA[p] / tmB[p] are tensor maps
+// over the operand planes; a_planes in {1,2}, b_planes in {1,2}.
+struct TcArgs {
+    CUtensorMap tmA[2];
+    CUtensorMap tmB[2];
+    int a_planes, b_planes;
+    int64_t row0;     // first row of the micro-batch in the V planes
+    int rows_pad;     // multiple of 128
+};
+int tc_max_smem_ok(int device);
+cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int num_sms,
+                               int *d_err, cudaStream_t st);
+
+// ---- measurement (Algorithm 2) --------------------------------------------
+struct MeasureArgs {
+    const float *Y;
+    int64_t ldY;
+    const float *P;
+    int ldP;
+    int d, chi_r, Cs, tiles_per_s;
+    int rows;                 // rows of this micro-batch
+    uint64_t seed;
+    uint64_t n_base;          // sample index of row 0 of the micro-batch
+    uint32_t k, job;
+    // next left operand, rows offset row0 (all N rows live in the V buffer)
+    int64_t row0;
+    int ld_next;              // ld of the next V buffer (elements)
+    int K_next;               // entries of the next row that must be written (2 chi_r .. K_next-1 zeroed)
+    float *V32;               // FP32 path (or nullptr)
+    __nv_bfloat16 *Vhi, *Vlo; // BF16 paths (Vlo may be nullptr)
+    uint8_t *outcomes;        // [rows] outcome bytes of this site (site-major buffer slice)
+    double *logp;             // [rows] accumulated log-probability
+    double *trace;            // nullable: [trace_rows][d] normalised conditionals of this site
+    int trace_rows;
+    int *err;
+};
+void launch_measure(const MeasureArgs &a, cudaStream_t st);
+
+// out[n * M + k] = O[k * ldO + n] for n < N, k < M.
+void launch_transpose_outcomes(const uint8_t *O, int64_t ldO, int64_t N, int M, uint8_t *out, cudaStream_t st);
+
+}  // namespace fastmps

@@ -1,0 +1,62 @@
+"""Teacher-forced parity of a device run against the FP64 oracle.
+
+Given the device's outcomes for a set of rows, the oracle replays those rows
+along the device's outcome prefix and reports, at every (row, site), its own
+conditionals, the outcome its own uniform picks and that uniform's distance
+to the nearest interior CDF boundary.  The rules (identical uniforms on both
+sides):
+
+* conditionals: |p_dev(s) - p_orc(s)| <= tol for every traced (row, site, s);
+* outcomes: identical, except where the oracle's uniform lies within tol of a
+  CDF boundary (a "boundary draw"); mismatches must also be < 0.1 % of draws;
+* log-probability: |logp_dev - logp_orc| <= sum_k tol / p_orc(s_k) (first
+  order bound from the conditional tolerance), plus rounding slack.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle
+
+
+def check(bonds, tensors, seed, rows, dev_samples, dev_logprob, tol, dev_trace=None, trace_rows=0,
+          site_index=None, job=0, nthreads=0):
+    """rows: sample indices checked; dev_samples[i], dev_logprob[i] belong to rows[i].
+
+    dev_trace: [M, trace_rows, d] device conditionals of rows 0..trace_rows-1
+    (rows[i] < trace_rows are compared).  Returns a report dict; raises
+    AssertionError when a rule is broken.
+    """
+    rows = np.asarray(rows, np.int64)
+    forced = np.ascontiguousarray(dev_samples)
+    r = oracle.replay(bonds, tensors, seed, rows, forced, job=job, site_index=site_index, nthreads=nthreads)
+    M = forced.shape[1]
+    mism = r["own"] != forced
+    boundary = r["margin"] <= tol
+    bad_mism = mism & ~boundary
+    report = {
+        "rows": int(rows.size),
+        "draws": int(mism.size),
+        "mismatches": int(mism.sum()),
+        "mismatch_frac": float(mism.mean()),
+        "boundary_draws": int(boundary.sum()),
+        "mismatch_outside_band": int(bad_mism.sum()),
+    }
+    assert not bad_mism.any(), f"outcome mismatch outside the tolerance band: {report}"
+    assert report["mismatch_frac"] < 1e-3, f"too many boundary mismatches: {report}"
+    # log-probability bound
+    p_sel = np.take_along_axis(r["probs"], forced[:, :, None].astype(np.int64), axis=2)[:, :, 0]
+    bound = (tol / np.maximum(p_sel, 1e-300)).sum(axis=1) + 1e-9 * M
+    lp_err = np.abs(dev_logprob - r["logprob"])
+    report["logprob_max_err"] = float(lp_err.max())
+    report["logprob_max_err_over_bound"] = float((lp_err / bound).max())
+    assert (lp_err <= bound).all(), f"log-probability outside its bound: {report}"
+    if dev_trace is not None and trace_rows > 0:
+        sel = np.nonzero(rows < trace_rows)[0]
+        if sel.size:
+            dev = np.transpose(dev_trace[:, rows[sel], :], (1, 0, 2))  # [R, M, d]
+            err = np.abs(dev - r["probs"][sel])
+            report["prob_max_err"] = float(err.max())
+            report["prob_rows"] = int(sel.size)
+            assert err.max() <= tol, f"conditional probabilities differ by {err.max():.3e} > {tol}: {report}"
+    return report

@@ -1,0 +1,177 @@
+"""Device path vs the FP64 oracle through the C ABI (needs a GB300).
+
+Tolerances (conditional probabilities, absolute): 1e-5 for the FP32 path,
+1e-4 for the BF16 split-precision paths, whose oracle runs on the tensors the
+BF16 store represents.  Outcomes must be identical except at boundary draws.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+import parity
+from oracle import quant
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "bf16x2": 1e-4, "bf16x3": 1e-4}
+
+
+def oracle_tensors(tensors, precision):
+    if precision == "bf16x2":
+        return [quant.dequant_bf16(A, 1) for A in tensors]
+    if precision == "bf16x3":
+        return [quant.dequant_bf16(A, 2) for A in tensors]
+    return tensors
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2512_20064_gb300 as F
+
+    F.load_library()
+    return F
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = gen.WORKLOADS["tiny"]
+    b, ts, _ = gen.mps_tensors(w.M, w.d, w.chi, base_seed=w.base_seed, skew=w.skew)
+    return w, b, ts
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2", "bf16x3"])
+def test_tiny_full_parity(lib, tiny, precision):
+    """Tiny chain, N = 10^4, every row and every conditional checked."""
+    w, b, ts = tiny
+    with lib.Sampler(precision=precision) as s:
+        s.load_chain(ts)
+        smp, lp, tr = s.sample(b, w.d, w.N, w.sampler_seed, trace_rows=w.N)
+    rep = parity.check(b, oracle_tensors(ts, precision), w.sampler_seed, np.arange(w.N), smp, lp, TOL[precision],
+                       dev_trace=tr, trace_rows=w.N)
+    print(precision, rep)
+    assert rep["prob_rows"] == w.N
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2"])
+def test_microbatch_and_offsets_are_exact(lib, tiny, precision):
+    """Results depend only on (seed, n): micro-batch splits, ragged tails and n0 offsets reproduce them bitwise."""
+    w, b, ts = tiny
+    N = 1000
+    with lib.Sampler(precision=precision) as s:
+        s.load_chain(ts)
+        a_s, a_l = s.sample(b, w.d, N, 7)
+    with lib.Sampler(precision=precision, max_microbatch=256) as s:
+        s.load_chain(ts)
+        b_s, b_l = s.sample(b, w.d, N, 7)
+        c_s, c_l = s.sample(b, w.d, 100, 7, n0=333)
+        one_s, one_l = s.sample(b, w.d, 1, 7, n0=999)
+        z_s, z_l = s.sample(b, w.d, 0, 7)
+    assert np.array_equal(a_s, b_s) and np.array_equal(a_l, b_l)
+    assert np.array_equal(a_s[333:433], c_s) and np.array_equal(a_l[333:433], c_l)
+    assert np.array_equal(a_s[999:], one_s) and np.array_equal(a_l[999:], one_l)
+    assert z_s.shape == (0, w.M)
+
+
+def test_device_outputs_match_host_outputs(lib, tiny):
+    import torch
+
+    w, b, ts = tiny
+    with lib.Sampler(precision="fp32") as s:
+        s.load_chain(ts)
+        hs, hl = s.sample(b, w.d, 2000, 3)
+        ds = torch.empty((2000, w.M), dtype=torch.uint8, device="cuda")
+        dl = torch.empty(2000, dtype=torch.float64, device="cuda")
+        s.sample(b, w.d, 2000, 3, out_samples=ds, out_logprob=dl)
+    assert np.array_equal(hs, ds.cpu().numpy()) and np.array_equal(hl, dl.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2"])
+def test_special_cases(lib, precision):
+    """GHZ chain: perfectly correlated outcomes, log p = -log d; product state: the oracle's exact draws."""
+    for M, d in ((8, 3), (16, 2)):
+        b, ts = gen.ghz_chain(M, d)
+        with lib.Sampler(precision=precision) as s:
+            s.load_chain(ts)
+            smp, lp = s.sample(b, d, 5000, 11)
+        assert (smp == smp[:, :1]).all()
+        assert np.abs(lp + math.log(d)).max() < 1e-5
+    rng = np.random.Generator(np.random.PCG64(3))
+    laws = rng.random((20, 4)) ** 2
+    laws[4] = [0.5, 0.0, 0.0, 0.5]
+    laws /= laws.sum(axis=1, keepdims=True)
+    b, ts = gen.product_state(20, laws)
+    with lib.Sampler(precision=precision) as s:
+        s.load_chain(ts)
+        smp, lp = s.sample(b, 4, 4000, 9)
+    assert (smp[:, 4] % 3 == 0).all()  # zero-probability outcomes never drawn
+    rep = parity.check(b, oracle_tensors(ts, precision), 9, np.arange(4000), smp, lp, TOL[precision])
+    print(rep)
+
+
+def test_marginals_1e6(lib, tiny, tiny_brute):
+    """10^6 device samples of the tiny chain: single-site and nearest-pair marginals within 5 sigma."""
+    import oracle_pins
+
+    w, b, ts = tiny
+    with lib.Sampler(precision="fp32") as s:
+        s.load_chain(ts)
+        smp, _ = s.sample(b, w.d, 1_000_000, 2025)
+    worst, where = oracle_pins.marginals_5sigma(smp, tiny_brute)
+    print("worst z", worst, where)
+    assert worst < 5.0, (worst, where)
+
+
+def test_errors(lib, tiny):
+    F = lib
+    w, b, ts = tiny
+    with F.Sampler(precision="fp32") as s:
+        with pytest.raises(F.FastMPSError) as e:
+            s.sample(b, w.d, 10, 1)
+        assert e.value.code == -3  # not loaded
+        s.load_chain(ts)
+        bad = list(b)
+        bad[3] += 1
+        with pytest.raises(F.FastMPSError) as e:
+            s.sample(bad, w.d, 10, 1)
+        assert e.value.code == -2
+        with pytest.raises(F.FastMPSError) as e:
+            s.sample(b, 4, 10, 1)
+        assert e.value.code == -2
+        with pytest.raises(F.FastMPSError) as e:
+            s.load_site(0, np.zeros((1, 300, 1), np.complex64))
+        assert e.value.code == -2
+        with pytest.raises(F.FastMPSError) as e:
+            s.load_site(0, np.zeros((5, 2, 2), np.complex64))  # d*chi_r < chi_l
+        assert e.value.code == -2
+        with pytest.raises(F.FastMPSError) as e:
+            F.fastmps_map_site(s.h, 0, 99)
+        assert e.value.code == -3
+        with pytest.raises(F.FastMPSError) as e:
+            F.fastmps_sample_ex(s.h, w.M, w.d, b, 0, 10, 1, 0, None, None, 5, None)
+        assert e.value.code == -1
+        # the handle still works after errors
+        smp, lp = s.sample(b, w.d, 10, 1)
+        assert smp.shape == (10, w.M)
+    F.fastmps_destroy(None)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2", "bf16x3"])
+def test_plain_config_full_size_sampled_rows(lib, precision):
+    """M=256, d=4, chi=256, skewed, N=2^17 (the full plain workload, one call);
+    256 traced rows plus rows from the last micro-batch tail replayed by the oracle."""
+    w = gen.WORKLOADS["plain"]
+    b, ts, _ = gen.mps_tensors(w.M, w.d, w.chi, base_seed=w.base_seed, skew=w.skew, dtype=np.complex64)
+    with lib.Sampler(precision=precision) as s:
+        s.load_chain(ts)
+        smp, lp, tr = s.sample(b, w.d, w.N, w.sampler_seed, trace_rows=192)
+        st = s.stats()
+    rows = np.concatenate([np.arange(192), np.arange(w.N - 64, w.N)])
+    rep = parity.check(b, oracle_tensors(ts, precision), w.sampler_seed, rows, smp[rows], lp[rows], TOL[precision],
+                       dev_trace=tr, trace_rows=192)
+    print(precision, rep, st)
+    assert np.isfinite(lp).all()
+    # every row is a valid configuration
+    assert smp.max() < w.d
