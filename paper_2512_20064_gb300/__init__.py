@@ -17,7 +17,7 @@ import threading
 
 import numpy as np
 
-from .build import LIB, build
+from .native import LIB, build
 
 __all__ = [
     "FastMPSError", "Sampler", "load_library", "build", "PRECISIONS", "RESIDENCIES",
@@ -66,7 +66,7 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
         if path is None and build_if_missing:
             build()
         if not os.path.exists(p):
-            raise ImportError(f"libfastmps.so not found at {p}; run paper_2512_20064_gb300.build.build()")
+            raise ImportError(f"libfastmps.so not found at {p}; run paper_2512_20064_gb300.native.build()")
         lib = ctypes.CDLL(p)
         H = ctypes.c_void_p
         P = ctypes.POINTER
