@@ -25,8 +25,8 @@
  *    message of the last failure is kept per handle (fastmps_last_error).
  *  - No C++ exception crosses the ABI.  Calls on one handle are not
  *    thread-safe; distinct handles are independent.
- *  - Input arrays are host memory owned by the caller and only read during
- *    the call.  Output arrays may be host or device memory (detected with
+ *  - Input arrays are owned by the caller and only read during the call.
+ *    Output arrays may be host or device memory (detected with
  *    cudaPointerGetAttributes) and are owned by the caller.
  *  - fastmps_sample* is synchronous: outputs are complete on return.
  */
@@ -50,10 +50,17 @@ extern "C" {
 #define FASTMPS_ERR_UNSUPPORTED (-7)   /* not available on this device/build */
 #define FASTMPS_ERR_NUMERIC (-8)       /* Z = sum_s w_s was not a positive finite number */
 
-/* Arithmetic of the per-site contraction (Sec. 3.3, adaptive mixed precision). */
+/*
+ * Arithmetic of the per-site contraction (Sec. 3.3, adaptive mixed precision).
+ * BF16 modes keep the site tensor B and the left operand V as BF16 planes of
+ * successive rounding residuals (B = B0 [+ B1], V = V0 + V1 [+ V2]) and
+ * accumulate a list of plane products in FP32 on the tensor cores.
+ */
 #define FASTMPS_FP32 0    /* complex64 storage, FP32 SIMT FMA (no tensor cores) */
-#define FASTMPS_BF16X2 1  /* site tensors BF16; v split hi+lo BF16; 2 tensor-core products */
-#define FASTMPS_BF16X3 2  /* site tensors hi+lo BF16; v hi+lo; 3 tensor-core products */
+#define FASTMPS_BF16X2 1  /* V0 B0 + V1 B0: B in BF16, v to ~16 bits; 2 products */
+#define FASTMPS_BF16X3 2  /* V0 B0 + V1 B0 + V0 B1: B to ~16 bits, v to ~16 bits; 3 products */
+#define FASTMPS_BF16X3L 3 /* V0 B0 + V1 B0 + V2 B0: B in BF16, v to ~24 bits; 3 products */
+#define FASTMPS_BF16X4 4  /* V0 B0 + V1 B0 + V2 B0 + V0 B1: B ~16 bits, v ~24 bits; 4 products */
 
 /* Where site tensors live between uses (Sec. 3.1: I/O overlapped by a double buffer). */
 #define FASTMPS_RESIDENT_HBM 0    /* repacked once at load time, kept in device memory */
@@ -66,7 +73,7 @@ extern "C" {
 #define FASTMPS_C128 1  /* interleaved complex double (re, im) */
 
 typedef struct fastmps_options {
-    int precision;          /* FASTMPS_FP32 | FASTMPS_BF16X2 | FASTMPS_BF16X3 */
+    int precision;          /* FASTMPS_FP32 | FASTMPS_BF16X2 | _BF16X3 | _BF16X3L | _BF16X4 */
     int residency;          /* FASTMPS_RESIDENT_HBM | FASTMPS_HOST_STREAM (BF16 modes only) */
     int64_t max_microbatch; /* rows per contraction launch; 0 = chosen from free memory */
     int autotune;           /* 1: time the candidate tile shapes once per new shape */
@@ -110,8 +117,9 @@ void fastmps_destroy(fastmps_handle h);
 const char *fastmps_last_error(fastmps_handle h);
 
 /*
- * Load site k: A is host memory, shape [chi_l][d][chi_r] row-major,
- * interleaved complex of type dtype.  The tensor is copied and repacked into
+ * Load site k: A is host or device memory (detected with
+ * cudaPointerGetAttributes), shape [chi_l][d][chi_r] row-major, interleaved
+ * complex of type dtype.  The tensor is copied and repacked into
  * the handle's arithmetic format (complex64, or BF16 planes of the real
  * stacked operand); the caller keeps ownership of A.  Loading k again
  * replaces the site.  In FASTMPS_HOST_STREAM residency the BF16 copy stays in

@@ -67,6 +67,12 @@ def _bind(lib):
         ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
     lib.orc_sample.restype = ctypes.c_int
+    lib.orc_sample_segment.argtypes = [
+        ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p), ctypes.c_int, ctypes.c_uint64,
+        ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_int]
+    lib.orc_sample_segment.restype = ctypes.c_int
     lib.orc_born_logprob.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p),
                                      ctypes.c_void_p]
     lib.orc_born_logprob.restype = ctypes.c_double
@@ -94,21 +100,29 @@ def _load(lib=None):
 
 
 class _Chain:
-    """Keeps complex128 copies of the site tensors alive for one C call."""
+    """Keeps contiguous copies of the site tensors alive for one C call.
 
-    def __init__(self, bonds, tensors, site_index=None):
+    Tensors are passed as complex128, or as complex64 when every tensor is
+    complex64 (the oracle widens float entries to double exactly).
+    """
+
+    def __init__(self, bonds, tensors, site_index=None, sites=None):
         self.M = len(bonds) - 1
         self.bonds = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32))
         idx = list(range(self.M)) if site_index is None else list(site_index)
         if len(idx) != self.M:
             raise ValueError("site_index must have M entries")
+        sites = range(self.M) if sites is None else sites
+        used = sorted({idx[k] for k in sites})
+        self.f32 = all(np.asarray(tensors[j]).dtype == np.complex64 for j in used)
+        want = np.complex64 if self.f32 else np.complex128
         self.d = None
         conv = {}
-        arrs = []
-        for k in range(self.M):
+        ptrs = [None] * self.M
+        for k in sites:
             j = idx[k]
             if j not in conv:
-                conv[j] = np.ascontiguousarray(np.asarray(tensors[j], dtype=np.complex128))
+                conv[j] = np.ascontiguousarray(np.asarray(tensors[j], dtype=want))
             A = conv[j]
             if A.ndim != 3 or A.shape[0] != bonds[k] or A.shape[2] != bonds[k + 1]:
                 raise ValueError(f"site {k}: shape {A.shape} does not match bonds ({bonds[k]}, {bonds[k+1]})")
@@ -116,9 +130,9 @@ class _Chain:
                 self.d = A.shape[1]
             elif A.shape[1] != self.d:
                 raise ValueError("all sites must share d")
-            arrs.append(A)
-        self._keep = arrs
-        self.ptrs = (ctypes.c_void_p * self.M)(*[a.ctypes.data for a in arrs])
+            ptrs[k] = A.ctypes.data
+        self._keep = conv
+        self.ptrs = (ctypes.c_void_p * self.M)(*ptrs)
 
     def bond_ptr(self):
         return self.bonds.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
@@ -154,14 +168,32 @@ def sample(bonds, tensors, seed: int, N: int, n0: int = 0, job: int = 0, site_in
     smp = np.zeros((N, M), np.uint8)
     lp = np.zeros(N, np.float64)
     pr = np.zeros((N, M, d), np.float64) if want_probs else None
-    rc = lib.orc_sample(M, d, ch.bond_ptr(), ch.ptrs, seed, job, n0, N, _vp(smp), _vp(lp), _vp(pr),
-                        None, None, None, nthreads)
+    rc = lib.orc_sample_segment(M, d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, job, n0, N, 0, M, None, 0,
+                                _vp(smp), _vp(lp), _vp(pr), None, None, None, nthreads)
     if rc != 0:
-        raise RuntimeError(f"orc_sample failed ({rc})")
+        raise RuntimeError(f"orc_sample_segment failed ({rc})")
     return (smp, lp, pr) if want_probs else (smp, lp)
 
 
-def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=None, nthreads: int = 0, lib=None):
+def sample_prefix(bonds, tensors, seed: int, N: int, K: int, n0: int = 0, nthreads: int = 0, lib=None):
+    """Sample rows ``n0..n0+N-1`` over the first ``K`` sites only (used to time a bounded sample)."""
+    lib = _load(lib)
+    M = len(bonds) - 1
+    ch = _Chain(bonds, list(tensors) + [None] * (M - len(tensors)), sites=range(K))
+    ldv = max(bonds)
+    vstate = np.zeros((N, 2 * ldv), np.float64)
+    vstate[:, 0] = 1.0
+    smp = np.zeros((N, M), np.uint8)
+    lp = np.zeros(N, np.float64)
+    rc = lib.orc_sample_segment(M, ch.d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, 0, n0, N, 0, K, _vp(vstate),
+                                ldv, _vp(smp), _vp(lp), None, None, None, None, nthreads)
+    if rc != 0:
+        raise RuntimeError(f"orc_sample_segment failed ({rc})")
+    return smp[:, :K], lp
+
+
+def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=None, nthreads: int = 0, lib=None,
+           site_chunk: int | None = None):
     """Teacher-forced replay of rows ``rows`` (sample indices) along ``forced[R, M]``.
 
     Returns a dict with ``probs[R,M,d]`` (the oracle's conditionals along the
@@ -169,30 +201,51 @@ def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=Non
     each step), ``margin[R,M]`` (distance of that uniform to the nearest
     interior CDF boundary) and ``logprob[R]`` (sum of log conditionals of the
     forced outcomes).
+
+    ``tensors`` may be a list, or a callable ``tensors(k) -> A_k``; with
+    ``site_chunk`` the chain is replayed ``site_chunk`` sites at a time,
+    carrying the left vectors between segments, so only one chunk of tensors
+    needs to be in host memory.
     """
     lib = _load(lib)
-    ch = _Chain(bonds, tensors, site_index)
-    M, d = ch.M, ch.d
+    M = len(bonds) - 1
     rows = np.asarray(rows, dtype=np.int64)
     forced = np.ascontiguousarray(np.asarray(forced, dtype=np.uint8))
     R = rows.shape[0]
     assert forced.shape == (R, M)
-    probs = np.zeros((R, M, d), np.float64)
+    get = tensors if callable(tensors) else None
+    chunk = site_chunk or M
+    ldv = max(bonds)
+    vstate = np.zeros((R, 2 * ldv), np.float64)
+    vstate[:, 0] = 1.0
+    probs = None
     own = np.zeros((R, M), np.uint8)
     margin = np.zeros((R, M), np.float64)
     lp = np.zeros(R, np.float64)
-    # rows are arbitrary indices: run each contiguous run of indices as one call
-    i = 0
-    while i < R:
-        j = i + 1
-        while j < R and rows[j] == rows[j - 1] + 1:
-            j += 1
-        rc = lib.orc_sample(M, d, ch.bond_ptr(), ch.ptrs, seed, job, int(rows[i]), j - i, None,
-                            _vp(lp[i:j]), _vp(probs[i:j]), _vp(forced[i:j]), _vp(own[i:j]),
-                            _vp(margin[i:j]), nthreads)
-        if rc != 0:
-            raise RuntimeError(f"orc_sample (replay) failed ({rc})")
-        i = j
+    for k0 in range(0, M, chunk):
+        k1 = min(M, k0 + chunk)
+        if get is not None:
+            seg = [None] * M
+            for k in range(k0, k1):
+                seg[k] = get(k)
+            ch = _Chain(bonds, seg, sites=range(k0, k1))
+        else:
+            ch = _Chain(bonds, tensors, site_index, sites=range(k0, k1))
+        if probs is None:
+            probs = np.zeros((R, M, ch.d), np.float64)
+        # rows are arbitrary indices: run each contiguous run of indices as one call
+        i = 0
+        while i < R:
+            j = i + 1
+            while j < R and rows[j] == rows[j - 1] + 1:
+                j += 1
+            rc = lib.orc_sample_segment(M, ch.d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, job, int(rows[i]), j - i,
+                                        k0, k1, _vp(vstate[i:j]), ldv, None, _vp(lp[i:j]), _vp(probs[i:j]),
+                                        _vp(forced[i:j]), _vp(own[i:j]), _vp(margin[i:j]), nthreads)
+            if rc != 0:
+                raise RuntimeError(f"orc_sample_segment (replay) failed ({rc})")
+            i = j
+        del ch
     return {"probs": probs, "own": own, "margin": margin, "logprob": lp}
 
 

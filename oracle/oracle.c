@@ -85,8 +85,15 @@ double orc_uniform(uint64_t seed, uint64_t n, uint32_t k, uint32_t job)
 /* One site of one sample, complex double.                                   */
 /* ------------------------------------------------------------------------ */
 
-/* y[s*chi_r + b] (interleaved re, im) = sum_a v[a] A[a, s, b].  Plain loops. */
-static void orc_contract(const double *v, int chi_l, int d, int chi_r, const double *A, double *y)
+/* y[s*chi_r + b] (interleaved re, im) = sum_a v[a] A[a, s, b].  Plain loops.
+ * A holds interleaved complex doubles (a_is_f32 = 0) or floats (a_is_f32 = 1);
+ * float entries are widened exactly to double. */
+static inline double orc_elem(const void *A, int a_is_f32, size_t i)
+{
+    return a_is_f32 ? (double)((const float *)A)[i] : ((const double *)A)[i];
+}
+
+static void orc_contract(const double *v, int chi_l, int d, int chi_r, const void *A, int a_is_f32, double *y)
 {
     const int cols = d * chi_r;
     for (int c = 0; c < cols; ++c) {
@@ -95,9 +102,9 @@ static void orc_contract(const double *v, int chi_l, int d, int chi_r, const dou
     }
     for (int a = 0; a < chi_l; ++a) {
         const double vr = v[2 * a], vi = v[2 * a + 1];
-        const double *row = A + (size_t)2 * a * cols;
+        const size_t row = (size_t)2 * a * cols;
         for (int c = 0; c < cols; ++c) {
-            const double ar = row[2 * c], ai = row[2 * c + 1];
+            const double ar = orc_elem(A, a_is_f32, row + 2 * c), ai = orc_elem(A, a_is_f32, row + 2 * c + 1);
             y[2 * c] += vr * ar - vi * ai;
             y[2 * c + 1] += vr * ai + vi * ar;
         }
@@ -153,22 +160,35 @@ static int max_bond(int M, const int *bond)
 }
 
 /*
- * Sample rows n = n0 .. n0+N-1.  samples[i*M + k] = outcome of row n0+i at
- * site k; logprob[i] = sum_k log p(s_k | s_<k).  probs (nullable) receives
- * the normalised conditionals p(s | prefix) = w_s / Z as [i][k][s].
- * forced (nullable, [N][M]): teacher-forced replay; the row follows the given
- * outcomes instead of its own draws, while own_draw (nullable, [N][M]) still
- * records the outcome its own uniform would have picked and margin
- * (nullable, [N][M]) the distance min_s |u - C_s/Z| of that uniform to the
- * nearest interior CDF boundary.  Returns 0, or -1 on bad arguments.
+ * Sample rows n = n0 .. n0+N-1 over the sites k0 .. k1-1 of an M-site chain.
+ *
+ * Row i starts from the left vector vstate[i] (2*ldv doubles: re, im of
+ * bond[k0] entries) or, when vstate is NULL, from v_0 = [1] (then k0 must be
+ * 0); with vstate non-NULL the row's final left vector (bond[k1] entries) is
+ * written back there, so a chain can be sampled in segments.
+ * samples[i*M + k] = outcome of row n0+i at site k (columns k0..k1-1 written);
+ * logprob[i] += sum_k log p(s_k | s_<k) over the segment (set to 0 first by
+ * the caller or by orc_sample).  probs (nullable, [N][M][d]) receives the
+ * normalised conditionals p(s | prefix) = w_s / Z.  forced (nullable,
+ * [N][M]): teacher-forced replay; the row follows the given outcomes instead
+ * of its own draws, while own_draw (nullable, [N][M]) records the outcome its
+ * own uniform would have picked and margin (nullable, [N][M]) the distance
+ * min_s |u - C_s/Z| of that uniform to the nearest interior CDF boundary.
+ * A holds one pointer per site, interleaved complex doubles or, with
+ * a_is_f32, complex floats.  Returns 0, -1 on bad arguments, -2 on
+ * allocation failure.
  */
-int orc_sample(int M, int d, const int *bond, const double *const *A, uint64_t seed, uint32_t job,
-               int64_t n0, int64_t N, uint8_t *samples, double *logprob, double *probs,
-               const uint8_t *forced, uint8_t *own_draw, double *margin, int nthreads)
+int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int a_is_f32, uint64_t seed,
+                       uint32_t job, int64_t n0, int64_t N, int k0, int k1, double *vstate, int ldv,
+                       uint8_t *samples, double *logprob, double *probs, const uint8_t *forced,
+                       uint8_t *own_draw, double *margin, int nthreads)
 {
     if (M < 1 || d < 2 || d > 255 || N < 0 || !bond || !A) return -1;
+    if (k0 < 0 || k1 > M || k0 > k1) return -1;
+    if (!vstate && k0 != 0) return -1;
     if (bond[0] != 1 || bond[M] != 1) return -1;
     const int chi = max_bond(M, bond);
+    if (vstate && ldv < chi) return -1;
     int bad = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -185,12 +205,25 @@ int orc_sample(int M, int d, const int *bond, const double *const *A, uint64_t s
         for (int64_t i = 0; i < N; ++i) {
             if (bad) continue;
             const uint64_t n = (uint64_t)(n0 + i);
-            v[0] = 1.0;
-            v[1] = 0.0;
+            if (vstate) {
+                for (int b = 0; b < 2 * bond[k0]; ++b) v[b] = vstate[(size_t)i * 2 * ldv + b];
+            } else {
+                v[0] = 1.0;
+                v[1] = 0.0;
+            }
             double lp = 0.0;
-            for (int k = 0; k < M; ++k) {
+            int dead = 0;
+            for (int k = k0; k < k1; ++k) {
                 const int cl = bond[k], cr = bond[k + 1];
-                orc_contract(v, cl, d, cr, A[k], y);
+                if (dead) {
+                    if (samples) samples[i * M + k] = 0;
+                    if (own_draw) own_draw[i * M + k] = 0;
+                    if (margin) margin[i * M + k] = INFINITY;
+                    if (probs)
+                        for (int t = 0; t < d; ++t) probs[((size_t)i * M + k) * d + t] = NAN;
+                    continue;
+                }
+                orc_contract(v, cl, d, cr, A[k], a_is_f32, y);
                 orc_block_norms(y, d, cr, w);
                 const double u = orc_uniform(seed, n, (uint32_t)k, job);
                 double Z, mg;
@@ -200,20 +233,13 @@ int orc_sample(int M, int d, const int *bond, const double *const *A, uint64_t s
                 if (margin) margin[i * M + k] = mg;
                 if (probs)
                     for (int t = 0; t < d; ++t) probs[((size_t)i * M + k) * d + t] = w[t] / Z;
-                if (s < 0 || s >= d || !(w[s] > 0.0)) {
-                    /* a forced outcome of zero probability: the replay stops */
-                    lp = -INFINITY;
-                    if (samples) samples[i * M + k] = (uint8_t)s;
-                    for (int kk = k + 1; kk < M; ++kk) {
-                        if (samples) samples[i * M + kk] = 0;
-                        if (own_draw) own_draw[i * M + kk] = 0;
-                        if (margin) margin[i * M + kk] = INFINITY;
-                        if (probs)
-                            for (int t = 0; t < d; ++t) probs[((size_t)i * M + kk) * d + t] = NAN;
-                    }
-                    break;
-                }
                 if (samples) samples[i * M + k] = (uint8_t)s;
+                if (s < 0 || s >= d || !(w[s] > 0.0)) {
+                    /* a forced outcome of zero probability: the replay of this row stops */
+                    lp = -INFINITY;
+                    dead = 1;
+                    continue;
+                }
                 lp += log(w[s]) - log(Z);
                 const double inv = 1.0 / sqrt(w[s]);
                 for (int b = 0; b < cr; ++b) {
@@ -221,13 +247,26 @@ int orc_sample(int M, int d, const int *bond, const double *const *A, uint64_t s
                     v[2 * b + 1] = y[2 * (s * cr + b) + 1] * inv;
                 }
             }
-            if (logprob) logprob[i] = lp;
+            if (logprob) logprob[i] += lp;
+            if (vstate)
+                for (int b = 0; b < 2 * bond[k1]; ++b) vstate[(size_t)i * 2 * ldv + b] = dead ? NAN : v[b];
         }
         free(v);
         free(y);
         free(w);
     }
     return bad ? -2 : 0;
+}
+
+/* Whole chain from v_0 = [1]; logprob[i] is overwritten.  See orc_sample_segment. */
+int orc_sample(int M, int d, const int *bond, const double *const *A, uint64_t seed, uint32_t job,
+               int64_t n0, int64_t N, uint8_t *samples, double *logprob, double *probs,
+               const uint8_t *forced, uint8_t *own_draw, double *margin, int nthreads)
+{
+    if (logprob)
+        for (int64_t i = 0; i < N; ++i) logprob[i] = 0.0;
+    return orc_sample_segment(M, d, bond, (const void *const *)A, 0, seed, job, n0, N, 0, M, NULL, 0, samples,
+                              logprob, probs, forced, own_draw, margin, nthreads);
 }
 
 /* ------------------------------------------------------------------------ */

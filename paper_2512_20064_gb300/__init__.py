@@ -29,7 +29,7 @@ __all__ = [
 OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "SHAPE", -3: "NOT_LOADED", -4: "OOM", -5: "CUDA", -6: "TIMEOUT",
              -7: "UNSUPPORTED", -8: "NUMERIC"}
-PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16x3": 2}
+PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16x3": 2, "bf16x3l": 3, "bf16x4": 4}
 RESIDENCIES = {"hbm": 0, "host_stream": 1}
 C64, C128 = 0, 1
 
@@ -138,32 +138,38 @@ def fastmps_last_error(h) -> str:
 
 
 def _tensor_arg(A):
+    """(pointer, keep-alive object, dtype code, shape) of a site tensor: a numpy array or a torch tensor
+    (host or CUDA) of shape (chi_l, d, chi_r), complex64 or complex128."""
+    if hasattr(A, "data_ptr") and hasattr(A, "is_cuda"):
+        import torch
+
+        if A.dim() != 3:
+            raise ValueError("site tensor must have shape (chi_l, d, chi_r)")
+        if A.dtype not in (torch.complex64, torch.complex128):
+            A = A.to(torch.complex128)
+        A = A.contiguous()
+        return A.data_ptr(), A, (C64 if A.dtype == torch.complex64 else C128), tuple(A.shape)
     A = np.asarray(A)
     if A.ndim != 3:
         raise ValueError("site tensor must have shape (chi_l, d, chi_r)")
-    if A.dtype == np.complex64:
-        dt = C64
-    elif A.dtype == np.complex128:
-        dt = C128
-    else:
+    if A.dtype not in (np.complex64, np.complex128):
         A = A.astype(np.complex128)
-        dt = C128
     A = np.ascontiguousarray(A)
-    return A, dt
+    return A.ctypes.data, A, (C64 if A.dtype == np.complex64 else C128), A.shape
 
 
 def fastmps_load_site(h, k: int, A) -> None:
     lib = load_library()
-    A, dt = _tensor_arg(A)
-    cl, d, cr = A.shape
-    _check(lib, h, lib.fastmps_load_site(h, k, cl, d, cr, A.ctypes.data, dt))
+    ptr, keep, dt, (cl, d, cr) = _tensor_arg(A)
+    _check(lib, h, lib.fastmps_load_site(h, k, cl, d, cr, ptr, dt))
+    del keep
 
 
 def fastmps_load_pool(h, j: int, A) -> None:
     lib = load_library()
-    A, dt = _tensor_arg(A)
-    cl, d, cr = A.shape
-    _check(lib, h, lib.fastmps_load_pool(h, j, cl, d, cr, A.ctypes.data, dt))
+    ptr, keep, dt, (cl, d, cr) = _tensor_arg(A)
+    _check(lib, h, lib.fastmps_load_pool(h, j, cl, d, cr, ptr, dt))
+    del keep
 
 
 def fastmps_map_site(h, k: int, j: int) -> None:

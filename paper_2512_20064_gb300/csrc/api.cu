@@ -112,7 +112,7 @@ struct fastmps_ctx {
     std::map<int, std::unique_ptr<Tensor>> pool_tensor;  // pool entry j
     std::map<int, int> site_pool;                        // site k -> pool entry j
     // work buffers (grow only)
-    DevBuf V[2][2];  // [ping-pong][plane]  BF16 planes, or V[x][0] FP32
+    DevBuf V[2][3];  // [ping-pong][plane]  BF16 planes, or V[x][0] FP32
     DevBuf Y, P, logp, O, Dout, Dlogp, trace, err;
     DevBuf staging;  // device copy of a tensor being loaded
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
@@ -133,7 +133,23 @@ int cuda_fail(fastmps_handle h, cudaError_t e, const char *what) {
     return fail(h, e == cudaErrorMemoryAllocation ? FASTMPS_ERR_OOM : FASTMPS_ERR_CUDA, m);
 }
 
-bool is_bf16(const fastmps_handle h) { return h->opt.precision == FASTMPS_BF16X2 || h->opt.precision == FASTMPS_BF16X3; }
+bool is_bf16(const fastmps_handle h) { return h->opt.precision != FASTMPS_FP32; }
+
+// Planes of the split-precision operands and the products accumulated per precision mode.
+struct PrecisionPlan {
+    int a_planes, b_planes, nprod;
+    int pa[kMaxProducts], pb[kMaxProducts];
+};
+
+PrecisionPlan plan_of(int precision) {
+    switch (precision) {
+        case FASTMPS_BF16X2: return {2, 1, 2, {0, 1, 0, 0}, {0, 0, 0, 0}};
+        case FASTMPS_BF16X3: return {2, 2, 3, {0, 1, 0, 0}, {0, 0, 1, 0}};
+        case FASTMPS_BF16X3L: return {3, 1, 3, {0, 1, 2, 0}, {0, 0, 0, 0}};
+        case FASTMPS_BF16X4: return {3, 2, 4, {0, 1, 2, 0}, {0, 0, 0, 1}};
+        default: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
+    }
+}
 
 SiteLayout make_layout(int precision, int chi_l, int d, int chi_r) {
     SiteLayout L;
@@ -192,6 +208,16 @@ int check_shape_args(fastmps_handle h, int chi_l, int d, int chi_r, const void *
     return FASTMPS_OK;
 }
 
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 // Copy and repack one tensor into t.
 int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const void *A, int dtype) {
     int rc = check_shape_args(h, chi_l, d, chi_r, A, dtype);
@@ -200,9 +226,17 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
     const int64_t nelem = (int64_t)chi_l * d * chi_r;
     const size_t src_bytes = (size_t)nelem * (dtype == FASTMPS_C128 ? 16 : 8);
     cudaError_t e;
+    const bool a_on_device = is_device_ptr(A);
+    std::vector<uint8_t> host_copy;
+    if (a_on_device && h->opt.residency == FASTMPS_HOST_STREAM) {
+        host_copy.resize(src_bytes);
+        e = cudaMemcpy(host_copy.data(), A, src_bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of site tensor");
+        A = host_copy.data();
+    }
     if (h->opt.residency == FASTMPS_HOST_STREAM) {
         // compact BF16 copy in pinned host memory
-        t.planes = h->opt.precision == FASTMPS_BF16X3 ? 2 : 1;
+        t.planes = plan_of(h->opt.precision).b_planes;
         t.host_compact.host = true;
         if (!t.host_compact.ensure((size_t)nelem * 2 * 2 * t.planes))
             return fail(h, FASTMPS_ERR_OOM, "pinned host allocation for a streamed tensor failed");
@@ -218,13 +252,14 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
         return FASTMPS_OK;
     }
     if (!h->staging.ensure(src_bytes)) return fail(h, FASTMPS_ERR_OOM, "staging allocation failed");
-    e = cudaMemcpyAsync(h->staging.p, A, src_bytes, cudaMemcpyHostToDevice, h->stream);
+    e = cudaMemcpyAsync(h->staging.p, A, src_bytes, a_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "copy of site tensor");
     const size_t op_elems = (size_t)t.L.ncols * t.L.K_pad;
     if (is_bf16(h)) {
         if (!t.B_hi.ensure(op_elems * 2)) return fail(h, FASTMPS_ERR_OOM, "site operand allocation failed");
         __nv_bfloat16 *lo = nullptr;
-        if (h->opt.precision == FASTMPS_BF16X3) {
+        if (plan_of(h->opt.precision).b_planes > 1) {
             if (!t.B_lo.ensure(op_elems * 2)) return fail(h, FASTMPS_ERR_OOM, "site operand allocation failed");
             lo = t.B_lo.as<__nv_bfloat16>();
         }
@@ -253,16 +288,6 @@ Tensor *site_tensor_of(fastmps_handle h, int k) {
     }
     auto s = h->site_tensor.find(k);
     return s == h->site_tensor.end() ? nullptr : s->second.get();
-}
-
-bool is_device_ptr(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
 struct EventTimer {
@@ -317,7 +342,8 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         ldP_max = std::max(ldP_max, t->L.ncols / t->L.bn);
         flops += 8.0 * bonds[k] * d * bonds[k + 1];
     }
-    const int prods = h->opt.precision == FASTMPS_BF16X3 ? 3 : (h->opt.precision == FASTMPS_BF16X2 ? 2 : 1);
+    const PrecisionPlan plan = plan_of(h->opt.precision);
+    const int prods = plan.nprod;
     h->stats.flops_algorithmic = flops * (double)N;
     h->stats.flops_issued = flops * (double)N * prods;
     if (N == 0) return FASTMPS_OK;
@@ -338,7 +364,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     N2 = std::min(N2, N_pad);
 
     // ---- buffers -------------------------------------------------------------
-    const int planes = bf16 ? 2 : 1;
+    const int planes = bf16 ? plan.a_planes : 1;
     const size_t elem = bf16 ? 2 : 4;
     for (int x = 0; x < 2; ++x)
         for (int p = 0; p < planes; ++p)
@@ -368,7 +394,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             opmax = std::max(opmax, (size_t)ts[k]->L.ncols * ts[k]->L.K_pad * 2);
         }
         if (!h->slot_compact[0].ensure(cmax) || !h->slot_compact[1].ensure(cmax) || !h->slot_hi.ensure(opmax) ||
-            (h->opt.precision == FASTMPS_BF16X3 && !h->slot_lo.ensure(opmax)))
+            (plan.b_planes > 1 && !h->slot_lo.ensure(opmax)))
             return fail(h, FASTMPS_ERR_OOM, "streaming slot allocation failed");
     }
 
@@ -376,8 +402,11 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     cudaMemsetAsync(h->logp.p, 0, (size_t)N_pad * 8, st);
+    __nv_bfloat16 *Vp[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    for (int x = 0; x < 2; ++x)
+        for (int p = 0; p < planes && bf16; ++p) Vp[x][p] = h->V[x][p].as<__nv_bfloat16>();
     if (bf16)
-        launch_init_left_bf16(h->V[0][0].as<__nv_bfloat16>(), h->V[0][1].as<__nv_bfloat16>(), N_pad, ldV, st);
+        launch_init_left_bf16(Vp[0], planes, N_pad, ldV, st);
     else
         launch_init_left_f32(h->V[0][0].as<float>(), N_pad, ldV, st);
     h->stats.launches += 1;
@@ -420,7 +449,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                     if (e != cudaSuccess) return cuda_fail(h, e, "site copy");
                 }
                 cudaStreamWaitEvent(st, h->copy_done[cur], 0);
-                __nv_bfloat16 *lo = h->opt.precision == FASTMPS_BF16X3 ? h->slot_lo.as<__nv_bfloat16>() : nullptr;
+                __nv_bfloat16 *lo = plan.b_planes > 1 ? h->slot_lo.as<__nv_bfloat16>() : nullptr;
                 launch_expand_bf16(h->slot_compact[cur].as<__nv_bfloat16>(), t->planes, L,
                                    h->slot_hi.as<__nv_bfloat16>(), lo, st);
                 h->stats.launches += 1;
@@ -435,11 +464,18 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 ta.tmB[0] = t->tmB[0];
                 ta.tmB[1] = t->tmB[1];
             }
-            ta.a_planes = 2;
-            ta.b_planes = h->opt.precision == FASTMPS_BF16X3 ? 2 : 1;
-            if (!encode_2d_bf16(&ta.tmA[0], h->V[cur][0].p, L.K_pad, N_pad, ldV, 64, 128) ||
-                !encode_2d_bf16(&ta.tmA[1], h->V[cur][1].p, L.K_pad, N_pad, ldV, 64, 128))
-                return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+            ta.a_planes = plan.a_planes;
+            ta.b_planes = plan.b_planes;
+            ta.nprod = plan.nprod;
+            for (int q = 0; q < kMaxProducts; ++q) {
+                ta.prod_a[q] = plan.pa[q];
+                ta.prod_b[q] = plan.pb[q];
+            }
+            for (int p = 0; p < 3; ++p) {
+                const int src = p < plan.a_planes ? p : 0;
+                if (!encode_2d_bf16(&ta.tmA[p], h->V[cur][src].p, L.K_pad, N_pad, ldV, 64, 128))
+                    return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+            }
         }
         for (int64_t r0 = 0; r0 < N; r0 += N2) {
             const int64_t rows = std::min<int64_t>(N2, N - r0);
@@ -487,8 +523,8 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.ld_next = ldV;
             ma.K_next = K_next;
             ma.V32 = bf16 ? nullptr : h->V[nxt][0].as<float>();
-            ma.Vhi = bf16 ? h->V[nxt][0].as<__nv_bfloat16>() : nullptr;
-            ma.Vlo = bf16 ? h->V[nxt][1].as<__nv_bfloat16>() : nullptr;
+            for (int p = 0; p < 3; ++p) ma.Vp[p] = Vp[nxt][p];
+            ma.nplanes = planes;
             ma.outcomes = h->O.as<uint8_t>() + (int64_t)k * N_pad + r0;
             ma.logp = h->logp.as<double>();
             ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
@@ -569,7 +605,7 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
     fastmps_options o;
     fastmps_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_BF16X3) {
+    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_BF16X4) {
         g_create_error = "unknown precision";
         return FASTMPS_ERR_INVALID_ARG;
     }

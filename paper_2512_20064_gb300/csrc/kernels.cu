@@ -144,12 +144,14 @@ void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *
 // ---------------------------------------------------------------------------
 // Left boundary v_0 = [1]: row = [1, 0, ..., 0] (real part 1, imaginary 0).
 // ---------------------------------------------------------------------------
-__global__ void init_left_bf16_kernel(__nv_bfloat16 *V_hi, __nv_bfloat16 *V_lo, int64_t rows, int ld) {
+__global__ void init_left_bf16_kernel(__nv_bfloat16 *V0, __nv_bfloat16 *V1, __nv_bfloat16 *V2, int64_t rows,
+                                      int ld) {
     const int64_t total = rows * ld;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const bool one = (i % ld) == 0;
-        V_hi[i] = __float2bfloat16_rn(one ? 1.f : 0.f);
-        if (V_lo) V_lo[i] = __float2bfloat16_rn(0.f);
+        V0[i] = __float2bfloat16_rn(one ? 1.f : 0.f);
+        V1[i] = __float2bfloat16_rn(0.f);
+        if (V2) V2[i] = __float2bfloat16_rn(0.f);
     }
 }
 
@@ -159,8 +161,9 @@ __global__ void init_left_f32_kernel(float *V, int64_t rows, int ld) {
         V[i] = (i % ld) == 0 ? 1.f : 0.f;
 }
 
-void launch_init_left_bf16(__nv_bfloat16 *V_hi, __nv_bfloat16 *V_lo, int64_t rows, int ld, cudaStream_t st) {
-    init_left_bf16_kernel<<<grid_for(rows * ld, 256), 256, 0, st>>>(V_hi, V_lo, rows, ld);
+void launch_init_left_bf16(__nv_bfloat16 *const *Vp, int nplanes, int64_t rows, int ld, cudaStream_t st) {
+    init_left_bf16_kernel<<<grid_for(rows * ld, 256), 256, 0, st>>>(Vp[0], Vp[1], nplanes > 2 ? Vp[2] : nullptr,
+                                                                      rows, ld);
 }
 
 void launch_init_left_f32(float *V, int64_t rows, int ld, cudaStream_t st) {
@@ -263,80 +266,134 @@ void launch_contract_f32(const float *V, int64_t ldV, int64_t row0, int64_t rows
 
 // ---------------------------------------------------------------------------
 // Measurement (Algorithm 2 with the exact per-sample rescaling of Sec. 3.3.1).
-// One warp per sample: combine the per-tile sums of squares of each outcome
-// block in FP64 (w_s), cumulative sum in s order, Philox uniform, outcome
-// s* = #{s < d-1 : C_s < u Z}, log-probability, then write the selected block
-// y_{s*} / sqrt(w_{s*}) as the next left row (FP32, or BF16 hi + lo).
+// One warp per sample:
+//  1. w_s = sum of the FP32 per-tile sums of squares of outcome block s,
+//     accumulated in FP64 (lane s sums its block's tiles; wide blocks use a
+//     warp reduction);
+//  2. C_s = w_0 + ... + w_s in s order (FP64), Z = C_{d-1}, Philox uniform u,
+//     s* = #{s < d-1 : C_s < u Z}: the decision is taken in FP64 as in the
+//     oracle;
+//  3. log p accumulates log w_{s*} - log Z in FP64; each logarithm is taken in
+//     FP32 (w and Z are O(1) because the left vector is renormalised at every
+//     site, so the absolute error per site is ~1e-7);
+//  4. the selected block y_{s*} is scaled by 1/sqrt(w_{s*}) (FP32; the scale
+//     cancels in every later ratio w/Z) and written as the next left row:
+//     FP32, or BF16 planes hi (+ lo (+ lo2)) of successive residuals.
+// GB300's FP64 units are slow, so FP64 is kept to the O(d) operations of the
+// draw and the accumulation.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double warp_sum_f64(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 constexpr int MEASURE_THREADS = 256;
+constexpr int MEASURE_WARPS = MEASURE_THREADS / 32;
+
+__device__ __forceinline__ void write_planes(float x, int nplanes, __nv_bfloat16 &h0, __nv_bfloat16 &h1,
+                                             __nv_bfloat16 &h2) {
+    h0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h0);
+    h1 = __float2bfloat16_rn(r1);
+    if (nplanes > 2) h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+}
 
 __global__ void __launch_bounds__(MEASURE_THREADS) measure_kernel(const MeasureArgs a) {
     extern __shared__ double sw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * (MEASURE_THREADS / 32) + warp;
+    const int row = blockIdx.x * MEASURE_WARPS + warp;
     if (row >= a.rows) return;
     double *w = sw + warp * a.d;
     const float *Prow = a.P + (int64_t)row * a.ldP;
-    for (int s = 0; s < a.d; ++s) {
-        double acc = 0.0;
-        for (int j = lane; j < a.tiles_per_s; j += 32) acc += (double)Prow[s * a.tiles_per_s + j];
-        acc = warp_sum_f64(acc);
-        if (lane == 0) w[s] = acc;
+    const int T = a.tiles_per_s;
+    if (T <= 16) {
+        for (int s = lane; s < a.d; s += 32) {
+            double acc = 0.0;
+            for (int j = 0; j < T; ++j) acc += (double)Prow[s * T + j];
+            w[s] = acc;
+        }
+    } else {
+        for (int s = 0; s < a.d; ++s) {
+            double acc = 0.0;
+            for (int j = lane; j < T; j += 32) acc += (double)Prow[s * T + j];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) w[s] = acc;
+        }
     }
     __syncwarp();
-    // cumulative sum in s order; Z is the last partial sum
-    double Z = 0.0;
-    for (int s = 0; s < a.d; ++s) Z += w[s];
     const uint64_t n = a.n_base + (uint64_t)row;
     const double u = sample_uniform(a.seed, n, a.k, a.job);
+    // cumulative sum in s order; Z is its last value
+    double C = w[0];
+    int below = 0;  // number of s < d-1 with C_s < u Z, counted after Z is known
+    for (int s = 1; s < a.d; ++s) C += w[s];
+    const double Z = C;
     const double t = u * Z;
-    int sstar = 0;
-    double C = 0.0;
+    C = 0.0;
     for (int s = 0; s < a.d - 1; ++s) {
         C += w[s];
-        if (C < t) ++sstar;
+        below += (C < t) ? 1 : 0;
     }
+    const int sstar = below;
     const double ws = w[sstar];
     const bool ok = (Z > 0.0) && isfinite(Z) && (ws > 0.0);
     const int64_t grow = a.row0 + row;
     if (lane == 0) {
         a.outcomes[row] = (uint8_t)sstar;
-        if (ok) a.logp[grow] += log(ws) - log(Z);
+        if (ok) a.logp[grow] += (double)(logf((float)ws) - logf((float)Z));
         else atomicExch(a.err, (int)kDevNumeric);
     }
     if (a.trace && grow < a.trace_rows) {
         for (int s = lane; s < a.d; s += 32) a.trace[grow * a.d + s] = ok ? w[s] / Z : 0.0;
     }
-    const float scale = ok ? (float)(1.0 / sqrt(ws)) : 0.f;
+    const float scale = ok ? rsqrtf((float)ws) : 0.f;
     const float *ysrc = a.Y + (int64_t)row * a.ldY + (int64_t)sstar * a.Cs;
     const int nreal = 2 * a.chi_r;
     if (a.V32) {
         float *dst = a.V32 + grow * a.ld_next;
-        for (int i = lane; i < a.K_next; i += 32) dst[i] = i < nreal ? ysrc[i] * scale : 0.f;
+        if ((nreal & 3) == 0) {
+            for (int i = 4 * lane; i < a.K_next; i += 128) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < nreal) {
+                    v = *reinterpret_cast<const float4 *>(ysrc + i);
+                    v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+                }
+                *reinterpret_cast<float4 *>(dst + i) = v;
+            }
+        } else {
+            for (int i = lane; i < a.K_next; i += 32) dst[i] = i < nreal ? ysrc[i] * scale : 0.f;
+        }
+        return;
+    }
+    __nv_bfloat16 *d0 = a.Vp[0] + grow * a.ld_next;
+    __nv_bfloat16 *d1 = a.Vp[1] + grow * a.ld_next;
+    __nv_bfloat16 *d2 = a.nplanes > 2 ? a.Vp[2] + grow * a.ld_next : nullptr;
+    if ((nreal & 3) == 0) {
+        for (int i = 4 * lane; i < a.K_next; i += 128) {
+            float x[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < nreal) {
+                const float4 v = *reinterpret_cast<const float4 *>(ysrc + i);
+                x[0] = v.x * scale; x[1] = v.y * scale; x[2] = v.z * scale; x[3] = v.w * scale;
+            }
+            __align__(8) __nv_bfloat16 p0[4], p1[4], p2[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) write_planes(x[e], a.nplanes, p0[e], p1[e], p2[e]);
+            *reinterpret_cast<uint2 *>(d0 + i) = *reinterpret_cast<const uint2 *>(p0);
+            *reinterpret_cast<uint2 *>(d1 + i) = *reinterpret_cast<const uint2 *>(p1);
+            if (d2) *reinterpret_cast<uint2 *>(d2 + i) = *reinterpret_cast<const uint2 *>(p2);
+        }
     } else {
-        __nv_bfloat16 *dh = a.Vhi + grow * a.ld_next;
-        __nv_bfloat16 *dl = a.Vlo ? a.Vlo + grow * a.ld_next : nullptr;
         for (int i = lane; i < a.K_next; i += 32) {
             const float x = i < nreal ? ysrc[i] * scale : 0.f;
-            __nv_bfloat16 hi, lo;
-            split_bf16(x, hi, lo);
-            dh[i] = hi;
-            if (dl) dl[i] = lo;
+            __nv_bfloat16 h0, h1, h2;
+            write_planes(x, a.nplanes, h0, h1, h2);
+            d0[i] = h0;
+            d1[i] = h1;
+            if (d2) d2[i] = h2;
         }
     }
 }
 
 void launch_measure(const MeasureArgs &a, cudaStream_t st) {
     if (a.rows <= 0) return;
-    const int rows_per_block = MEASURE_THREADS / 32;
-    const int grid = (a.rows + rows_per_block - 1) / rows_per_block;
-    const size_t smem = sizeof(double) * (size_t)rows_per_block * a.d;
+    const int grid = (a.rows + MEASURE_WARPS - 1) / MEASURE_WARPS;
+    const size_t smem = sizeof(double) * (size_t)MEASURE_WARPS * a.d;
     measure_kernel<<<grid, MEASURE_THREADS, smem, st>>>(a);
 }
 

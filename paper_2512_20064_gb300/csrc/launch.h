@@ -36,7 +36,7 @@ void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *
 
 // ---- left operand ----------------------------------------------------------
 // Set rows [0, rows) of V to the boundary vector v_0 = [1] (row = [1, 0, ... 0], ld elements).
-void launch_init_left_bf16(__nv_bfloat16 *V_hi, __nv_bfloat16 *V_lo, int64_t rows, int ld, cudaStream_t st);
+void launch_init_left_bf16(__nv_bfloat16 *const *Vp, int nplanes, int64_t rows, int ld, cudaStream_t st);
 void launch_init_left_f32(float *V, int64_t rows, int ld, cudaStream_t st);
 
 // ---- contraction kernels ---------------------------------------------------
@@ -53,11 +53,15 @@ void launch_contract_f32(const float *V, int64_t ldV, int64_t row0, int64_t rows
                          const SiteLayout &L, const ContractOut &o, cudaStream_t st);
 
 // tcgen05 BF16 split-precision contraction.  tmA[p] / tmB[p] are tensor maps
-// over the operand planes; a_planes in {1,2}, b_planes in {1,2}.
+// over the operand planes (a_planes in {1,2,3}, b_planes in {1,2}); the
+// products accumulated are (prod_a[q], prod_b[q]) for q < nprod.
+constexpr int kMaxProducts = 4;
 struct TcArgs {
-    CUtensorMap tmA[2];
+    CUtensorMap tmA[3];
     CUtensorMap tmB[2];
     int a_planes, b_planes;
+    int nprod;
+    int prod_a[kMaxProducts], prod_b[kMaxProducts];
     int64_t row0;     // first row of the micro-batch in the V planes
     int rows_pad;     // multiple of 128
 };
@@ -81,7 +85,8 @@ struct MeasureArgs {
     int ld_next;              // ld of the next V buffer (elements)
     int K_next;               // entries of the next row that must be written (2 chi_r .. K_next-1 zeroed)
     float *V32;               // FP32 path (or nullptr)
-    __nv_bfloat16 *Vhi, *Vlo; // BF16 paths (Vlo may be nullptr)
+    __nv_bfloat16 *Vp[3];     // BF16 paths: planes of successive residuals
+    int nplanes;              // 2 or 3
     uint8_t *outcomes;        // [rows] outcome bytes of this site (site-major buffer slice)
     double *logp;             // [rows] accumulated log-probability
     double *trace;            // nullable: [trace_rows][d] normalised conditionals of this site

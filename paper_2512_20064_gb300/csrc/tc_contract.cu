@@ -1,12 +1,13 @@
 // tcgen05 split-precision contraction of the left vectors with one site tensor.
 //
 // Y[row, c] = sum_kappa V[row, kappa] B[c, kappa] over the stacked real
-// operands (K = 2 chi_l, padded to a multiple of 64), with V = V_hi (+ V_lo)
-// and B = B_hi (+ B_lo) held as BF16 planes and every product accumulated in
-// FP32 in tensor memory:
-//   1 product : V_hi B_hi
-//   2 products: V_hi B_hi + V_lo B_hi               (BF16x2)
-//   3 products: V_hi B_hi + V_lo B_hi + V_hi B_lo   (BF16x3)
+// operands (K = 2 chi_l, padded to a multiple of 64), with V = V_0 + V_1 (+ V_2)
+// and B = B_0 (+ B_1) held as BF16 planes of successive rounding residuals
+// and a list of plane products accumulated in FP32 in tensor memory, e.g.
+//   BF16x2 : V_0 B_0 + V_1 B_0
+//   BF16x3 : V_0 B_0 + V_1 B_0 + V_0 B_1
+//   BF16x3L: V_0 B_0 + V_1 B_0 + V_2 B_0
+//   BF16x4 : V_0 B_0 + V_1 B_0 + V_2 B_0 + V_0 B_1
 //
 // Persistent kernel, one CTA per SM, 192 threads:
 //   warp 0 : TMA producer (one thread) -- 128 x 64 tiles of each V plane and
@@ -43,6 +44,7 @@ constexpr int kSmemLimit = 232448;           // 227 KB opt-in per block
 struct TcParams {
     int num_m_tiles, num_n_tiles, num_k_blocks, bn;
     int a_planes, b_planes, stages, nprod;
+    uint32_t prod_code;  // product q uses A plane (code >> 4q) & 3 and B plane (code >> (4q+2)) & 3
     uint32_t stage_bytes, b_plane_bytes;
     int row0;
     uint32_t idesc;
@@ -70,8 +72,8 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity) 
 
 __global__ void __launch_bounds__(kThreads, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
-                   const __grid_constant__ CUtensorMap tmB0, const __grid_constant__ CUtensorMap tmB1,
-                   const TcParams p) {
+                   const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
+                   const __grid_constant__ CUtensorMap tmB1, const TcParams p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -102,6 +104,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     if (warp == 0 && lane == 0) {
         prefetch_tmap(&tmA0);
         if (p.a_planes > 1) prefetch_tmap(&tmA1);
+        if (p.a_planes > 2) prefetch_tmap(&tmA2);
         prefetch_tmap(&tmB0);
         if (p.b_planes > 1) prefetch_tmap(&tmB1);
     }
@@ -139,6 +142,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                     const int x = kb * kBK;
                     tma_load_2d(sbase, &tmA0, &full[stage], x, y_a);
                     if (p.a_planes > 1) tma_load_2d(sbase + kATileBytes, &tmA1, &full[stage], x, y_a);
+                    if (p.a_planes > 2) tma_load_2d(sbase + 2 * kATileBytes, &tmA2, &full[stage], x, y_a);
                     uint8_t *bbase = sbase + (size_t)p.a_planes * kATileBytes;
                     tma_load_2d(bbase, &tmB0, &full[stage], x, y_b);
                     if (p.b_planes > 1) tma_load_2d(bbase + p.b_plane_bytes, &tmB1, &full[stage], x, y_b);
@@ -184,9 +188,10 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                     const uint32_t sa = smem_u32(smem + (size_t)stage * p.stage_bytes);
                     const uint32_t sb = sa + (uint32_t)p.a_planes * kATileBytes;
                     for (int q = 0; q < p.nprod; ++q) {
-                        // q = 0: V_hi B_hi, q = 1: V_lo B_hi, q = 2: V_hi B_lo
-                        const uint32_t a_addr = sa + (q == 1 ? kATileBytes : 0u);
-                        const uint32_t b_addr = sb + (q == 2 ? p.b_plane_bytes : 0u);
+                        const uint32_t pa = (p.prod_code >> (4 * q)) & 3u;
+                        const uint32_t pb = (p.prod_code >> (4 * q + 2)) & 3u;
+                        const uint32_t a_addr = sa + pa * kATileBytes;
+                        const uint32_t b_addr = sb + pb * p.b_plane_bytes;
                         const uint64_t ad = sw128_kmajor_desc(a_addr);
                         const uint64_t bd = sw128_kmajor_desc(b_addr);
 #pragma unroll
@@ -287,7 +292,16 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     p.bn = L.bn;
     p.a_planes = a.a_planes;
     p.b_planes = a.b_planes;
-    p.nprod = a.a_planes == 1 ? 1 : (a.b_planes == 1 ? 2 : 3);
+    if (a.nprod < 1 || a.nprod > kMaxProducts || a.a_planes < 1 || a.a_planes > 3 || a.b_planes < 1 ||
+        a.b_planes > 2)
+        return cudaErrorInvalidValue;
+    p.nprod = a.nprod;
+    p.prod_code = 0;
+    for (int q = 0; q < a.nprod; ++q) {
+        if (a.prod_a[q] < 0 || a.prod_a[q] >= a.a_planes || a.prod_b[q] < 0 || a.prod_b[q] >= a.b_planes)
+            return cudaErrorInvalidValue;
+        p.prod_code |= ((uint32_t)a.prod_a[q] | ((uint32_t)a.prod_b[q] << 2)) << (4 * q);
+    }
     p.b_plane_bytes = (uint32_t)L.bn * kBK * 2;
     p.stage_bytes = (uint32_t)a.a_planes * kATileBytes + (uint32_t)a.b_planes * p.b_plane_bytes;
     p.stages = stages_for(p.stage_bytes);
@@ -301,16 +315,13 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     p.rows_valid = o.rows_valid;
     p.err = d_err;
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 256;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = cudaFuncSetAttribute(tc_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e != cudaSuccess) return e;
     const int total = p.num_m_tiles * p.num_n_tiles;
     const int grid = total < num_sms ? total : num_sms;
     if (grid <= 0) return cudaSuccess;
-    tc_contract_kernel<<<grid, kThreads, smem, st>>>(a.tmA[0], a.tmA[a.a_planes > 1 ? 1 : 0], a.tmB[0],
+    tc_contract_kernel<<<grid, kThreads, smem, st>>>(a.tmA[0], a.tmA[a.a_planes > 1 ? 1 : 0],
+                                                     a.tmA[a.a_planes > 2 ? 2 : 0], a.tmB[0],
                                                      a.tmB[a.b_planes > 1 ? 1 : 0], p);
     return cudaGetLastError();
 }

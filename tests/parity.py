@@ -20,7 +20,7 @@ import oracle
 
 
 def check(bonds, tensors, seed, rows, dev_samples, dev_logprob, tol, dev_trace=None, trace_rows=0,
-          site_index=None, job=0, nthreads=0):
+          site_index=None, job=0, nthreads=0, site_chunk=None):
     """rows: sample indices checked; dev_samples[i], dev_logprob[i] belong to rows[i].
 
     dev_trace: [M, trace_rows, d] device conditionals of rows 0..trace_rows-1
@@ -29,7 +29,8 @@ def check(bonds, tensors, seed, rows, dev_samples, dev_logprob, tol, dev_trace=N
     """
     rows = np.asarray(rows, np.int64)
     forced = np.ascontiguousarray(dev_samples)
-    r = oracle.replay(bonds, tensors, seed, rows, forced, job=job, site_index=site_index, nthreads=nthreads)
+    r = oracle.replay(bonds, tensors, seed, rows, forced, job=job, site_index=site_index, nthreads=nthreads,
+                      site_chunk=site_chunk)
     M = forced.shape[1]
     mism = r["own"] != forced
     boundary = r["margin"] <= tol

@@ -16,13 +16,14 @@ from oracle import quant
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "bf16x2": 1e-4, "bf16x3": 1e-4}
+TOL = {"fp32": 1e-5, "bf16x2": 1e-4, "bf16x3": 1e-4, "bf16x3l": 1e-4, "bf16x4": 1e-4}
 
 
 def oracle_tensors(tensors, precision):
-    if precision == "bf16x2":
+    """The tensors a device store of each precision represents (what the oracle is run on)."""
+    if precision in ("bf16x2", "bf16x3l"):
         return [quant.dequant_bf16(A, 1) for A in tensors]
-    if precision == "bf16x3":
+    if precision in ("bf16x3", "bf16x4"):
         return [quant.dequant_bf16(A, 2) for A in tensors]
     return tensors
 
@@ -42,7 +43,7 @@ def tiny():
     return w, b, ts
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x2", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4"])
 def test_tiny_full_parity(lib, tiny, precision):
     """Tiny chain, N = 10^4, every row and every conditional checked."""
     w, b, ts = tiny
@@ -158,7 +159,7 @@ def test_errors(lib, tiny):
     F.fastmps_destroy(None)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16x2", "bf16x3"])
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4"])
 def test_plain_config_full_size_sampled_rows(lib, precision):
     """M=256, d=4, chi=256, skewed, N=2^17 (the full plain workload, one call);
     256 traced rows plus rows from the last micro-batch tail replayed by the oracle."""

@@ -16,8 +16,8 @@ SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 MUTANTS = {
     "drop_imag_cross_term": ("y[2 * c] += vr * ar - vi * ai;", "y[2 * c] += vr * ar;"),
     "imag_sign_flip": ("y[2 * c + 1] += vr * ai + vi * ar;", "y[2 * c + 1] += vr * ai - vi * ar;"),
-    "transposed_site_index": ("const double *row = A + (size_t)2 * a * cols;",
-                              "const double *row = A + (size_t)2 * a * (cols == chi_l ? cols : chi_r);"),
+    "transposed_site_index": ("const size_t row = (size_t)2 * a * cols;",
+                              "const size_t row = (size_t)2 * a * (cols == chi_l ? cols : chi_r);"),
     "no_cumulative_sum": ("        acc += w[s];\n        C[s] = acc;", "        acc += w[s];\n        C[s] = w[s];"),
     "threshold_not_scaled_by_Z": ("const double t = u * Z;", "const double t = u;"),
     "logprob_without_Z": ("lp += log(w[s]) - log(Z);", "lp += log(w[s]);"),

@@ -119,3 +119,27 @@ def test_pool_site_index():
     s2, l2 = oracle.sample(b, full, 1, 50)
     assert np.array_equal(s1, s2) and np.array_equal(l1, l2)
     assert all(math.isfinite(x) for x in l1)
+
+
+def test_segmented_replay_equals_whole_chain():
+    """Replaying 5 sites at a time with carried left vectors gives the whole-chain result bitwise."""
+    b, ts = P._tiny()
+    smp, lp, pr = oracle.sample(b, ts, 42, 40, want_probs=True)
+    r1 = oracle.replay(b, ts, 42, np.arange(40), smp)
+    r2 = oracle.replay(b, lambda k: ts[k], 42, np.arange(40), smp, site_chunk=5)
+    for key in ("probs", "own", "margin"):
+        assert np.array_equal(r1[key], r2[key]), key
+    assert np.allclose(r1["logprob"], r2["logprob"], rtol=0, atol=1e-13)
+    assert np.array_equal(r1["probs"], pr)
+
+
+def test_prefix_sampling_and_complex64_inputs():
+    b, ts = P._tiny()
+    smp, lp = oracle.sample(b, ts, 42, 30)
+    s5, _ = oracle.sample_prefix(b, ts[:5], 42, 30, 5)
+    assert np.array_equal(s5, smp[:, :5])
+    t64 = [t.astype(np.complex64) for t in ts]
+    widened = [t.astype(np.complex128) for t in t64]
+    a, la = oracle.sample(b, t64, 42, 30)
+    c, lc = oracle.sample(b, widened, 42, 30)
+    assert np.array_equal(a, c) and np.array_equal(la, lc)
