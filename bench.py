@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="precision", choices=["precision", "plain", "tiny"])
-    ap.add_argument("--precision", default=None, choices=["fp32", "bf16x2", "bf16x3"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4"])
     ap.add_argument("--macro", type=int, default=None, help="rows per step (macro-batch)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -154,43 +154,33 @@ def make_workload(w, device):
     return b, ts, idx
 
 
-def cpu_oracle_rate(w, b, tensors_host_fn, cpu_seconds: float, rows_max: int = 256):
-    """Time the FP64 oracle (as it stands) on a bounded sample: R rows x K leading sites."""
+def cpu_oracle_rate(w, b, tensors_host_fn, cpu_seconds: float, rows_max: int = 512):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the workload: R rows through the
+    first K sites (interior sites cost 8 chi^2 d flops each, like the bulk of the chain).
+
+    A short probe sizes the sample so that the timed part takes about ``cpu_seconds``.
+    Returns (cpu_baseline dict, R, K, seconds).
+    """
     import oracle
 
     cores = oracle.num_threads()
-    per_ss = 8.0 * w.chi * w.chi * w.d  # flops per interior sample-site
-    # rough oracle speed guess (0.5 GFLOP/s per core) to size the sample, then measure
-    target = cpu_seconds * cores * 0.5e9 / per_ss
-    K = max(4, min(w.M, int(max(8, target // max(1, min(rows_max, cores * 4))))))
-    R = max(1, min(rows_max, int(target // K)))
-    R = max(R, min(rows_max, cores))
-    ts = tensors_host_fn(K)
-    bk = list(b[:K]) + [1]
-    # the truncated chain must end in a bond of size 1: close it with the sampler's own rule
-    # (we only time the first K sites: use the real bonds and stop the timing at site K)
+    # probe: one row per core through the first sites
+    Kp = min(w.M, max(8, (b.index(w.chi) + 2) if w.chi in b else 8))
+    tsp = tensors_host_fn(Kp)
     t0 = time.perf_counter()
-    oracle.sample(b[:K + 1], ts, 42, R, n0=0, nthreads=cores) if b[K] == 1 else _oracle_prefix(b, ts, K, R, cores)
+    oracle.sample_prefix(b, tsp, w.sampler_seed, cores, Kp, nthreads=cores)
+    probe = max(1e-3, time.perf_counter() - t0)
+    rate = cores * Kp / probe                      # sample-sites/s, a slight underestimate
+    units = max(cores, int(rate * cpu_seconds))
+    K = int(min(w.M, max(Kp, units // (4 * cores))))
+    R = int(max(cores, min(rows_max, units // K)))
+    ts = tensors_host_fn(K)
+    t0 = time.perf_counter()
+    oracle.sample_prefix(b, ts, w.sampler_seed, R, K, nthreads=cores)
     dt = time.perf_counter() - t0
-    del bk
     return {"value": R * K / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{R} rows x first {K} sites of the workload (FP64 complex oracle, OpenMP over rows), "
+            "sample": f"{R} rows x the first {K} of {w.M} sites (FP64 complex oracle, OpenMP over rows), "
                       f"{dt:.1f} s"}, R, K, dt
-
-
-def _oracle_prefix(b, ts, K, R, cores):
-    """Run the oracle over the first K sites: append a closing site that maps the bond to 1."""
-    import oracle
-
-    chi = b[K]
-    d = ts[0].shape[1]
-    # closing tensor: an isometry chi -> (d * 1) is impossible when chi > d; use the identity-like
-    # contraction on the first site of the bond only.  Timing only (outcomes not used).
-    close = np.zeros((chi, d, 1), np.complex128)
-    for a in range(min(chi, d)):
-        close[a, a, 0] = 1.0
-    bonds = list(b[:K + 1]) + [1]
-    oracle.sample(bonds, list(ts) + [close], 42, R, n0=0, nthreads=cores)
 
 
 def run_ours(args, rank, ws, local):
@@ -318,7 +308,7 @@ def e2e_rate(args, w, b, ts, idx, precision, macro, local):
         def step(i):
             for k in range(w.M):
                 s.load_site(k, host[idx[k]])
-            s.sample(b, w.d, macro, w.sampler_seed, n0=i * macro, out_samples=out_s, out_logprob=out_l)
+            s.sample(b, w.d, macro, w.sampler_seed, n0=(i + 1) * macro, out_samples=out_s, out_logprob=out_l)
     else:
         s = F.Sampler(device=local, precision=precision, residency="host_stream")
         for j in range(len(ts)):
@@ -330,7 +320,7 @@ def e2e_rate(args, w, b, ts, idx, precision, macro, local):
         h2d = None
 
         def step(i):
-            s.sample(b, w.d, macro, w.sampler_seed, n0=i * macro, out_samples=out_s, out_logprob=out_l)
+            s.sample(b, w.d, macro, w.sampler_seed, n0=(i + 1) * macro, out_samples=out_s, out_logprob=out_l)
     steps = max(1, min(args.steps, 2))
     step(-1)
     torch.cuda.synchronize()

@@ -104,7 +104,7 @@ struct Tensor {
 struct fastmps_ctx {
     int device = 0;
     fastmps_options opt{};
-    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    cudaStream_t stream = nullptr, copy_stream = nullptr, measure_stream = nullptr;
     bool own_stream = false;
     int num_sms = 0;
     std::string last_error;
@@ -113,10 +113,11 @@ struct fastmps_ctx {
     std::map<int, int> site_pool;                        // site k -> pool entry j
     // work buffers (grow only)
     DevBuf V[2][3];  // [ping-pong][plane]  BF16 planes, or V[x][0] FP32
-    DevBuf Y, P, logp, O, Dout, Dlogp, trace, err;
+    DevBuf Y[2], P[2], logp, O, Dout, Dlogp, trace, err;
     DevBuf staging;  // device copy of a tensor being loaded
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
+    cudaEvent_t contract_done[2] = {nullptr, nullptr}, measure_done[2] = {nullptr, nullptr};
     fastmps_stats stats{};
     std::vector<cudaEvent_t> ev_pool;
 };
@@ -358,10 +359,14 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     if (h->opt.max_microbatch > 0) {
         N2 = std::max<int64_t>(128, h->opt.max_microbatch / 128 * 128);
     } else {
-        const int64_t budget = (int64_t)2 << 30;  // bytes of FP32 scratch per micro-batch
+        // FP32 scratch budget per micro-batch buffer (two buffers), and at least four
+        // micro-batches per site so that measurement overlaps the next contraction
+        const int64_t budget = (int64_t)2 << 30;
         N2 = std::max<int64_t>(128, budget / ((int64_t)ncols_max * 4) / 128 * 128);
+        N2 = std::min(N2, std::max<int64_t>(128, roundup((N + 3) / 4, 128)));
     }
     N2 = std::min(N2, N_pad);
+    const int64_t J = (N + N2 - 1) / N2;  // micro-batches per site
 
     // ---- buffers -------------------------------------------------------------
     const int planes = bf16 ? plan.a_planes : 1;
@@ -370,8 +375,11 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         for (int p = 0; p < planes; ++p)
             if (!h->V[x][p].ensure((size_t)N_pad * ldV * elem))
                 return fail(h, FASTMPS_ERR_OOM, "left-operand allocation failed");
-    if (!h->Y.ensure((size_t)N2 * ncols_max * 4) || !h->P.ensure((size_t)N2 * ldP_max * 4) ||
-        !h->logp.ensure((size_t)N_pad * 8) || !h->O.ensure((size_t)M * N_pad) || !h->err.ensure(sizeof(int)))
+    const int nybuf = J > 1 ? 2 : 1;
+    for (int b = 0; b < nybuf; ++b)
+        if (!h->Y[b].ensure((size_t)N2 * ncols_max * 4) || !h->P[b].ensure((size_t)N2 * ldP_max * 4))
+            return fail(h, FASTMPS_ERR_OOM, "scratch allocation failed");
+    if (!h->logp.ensure((size_t)N_pad * 8) || !h->O.ensure((size_t)M * N_pad) || !h->err.ensure(sizeof(int)))
         return fail(h, FASTMPS_ERR_OOM, "work-buffer allocation failed");
     const bool samples_dev = is_device_ptr(out_samples);
     const bool logp_dev = is_device_ptr(out_logprob);
@@ -412,7 +420,14 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     h->stats.launches += 1;
 
     EventTimer timer(h);
-    const bool timing = true;
+    cudaStream_t ms = h->measure_stream;
+    int64_t g = 0;  // micro-batch counter over the whole call
+    // the measurement stream starts after everything queued so far on the compute stream
+    {
+        cudaEvent_t ev = timer.get();
+        cudaEventRecord(ev, st);
+        cudaStreamWaitEvent(ms, ev, 0);
+    }
 
     // streaming: prefetch site 0
     auto issue_copy = [&](int k) -> cudaError_t {
@@ -477,20 +492,22 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                     return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
             }
         }
-        for (int64_t r0 = 0; r0 < N; r0 += N2) {
+        for (int64_t r0 = 0; r0 < N; r0 += N2, ++g) {
             const int64_t rows = std::min<int64_t>(N2, N - r0);
             const int64_t rows_pad = roundup(rows, 128);
+            const int yb = (int)(g % nybuf);
+            // the scratch buffer is free once the measurement two micro-batches back is done; with one
+            // micro-batch per site the left rows of this contraction come from the previous measurement
+            if (g >= nybuf) cudaStreamWaitEvent(st, h->measure_done[yb], 0);
+            if (nybuf == 1 && g >= 1) cudaStreamWaitEvent(st, h->measure_done[0], 0);
             ContractOut co;
-            co.Y = h->Y.as<float>();
+            co.Y = h->Y[yb].as<float>();
             co.ldY = L.ncols;
-            co.P = h->P.as<float>();
+            co.P = h->P[yb].as<float>();
             co.ldP = L.ncols / L.bn;
             co.rows_valid = (int)rows;
-            cudaEvent_t c0 = nullptr, c1 = nullptr, m1 = nullptr;
-            if (timing) {
-                c0 = timer.get();
-                cudaEventRecord(c0, st);
-            }
+            cudaEvent_t c0 = timer.get(), c1 = timer.get(), m0 = timer.get(), m1 = timer.get();
+            cudaEventRecord(c0, st);
             if (bf16) {
                 ta.row0 = r0;
                 ta.rows_pad = (int)rows_pad;
@@ -501,10 +518,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             }
             h->stats.launches += 1;
             h->stats.contract_launches += 1;
-            if (timing) {
-                c1 = timer.get();
-                cudaEventRecord(c1, st);
-            }
+            cudaEventRecord(c1, st);
+            cudaEventRecord(h->contract_done[yb], st);
+            cudaStreamWaitEvent(ms, h->contract_done[yb], 0);
             MeasureArgs ma;
             ma.Y = co.Y;
             ma.ldY = co.ldY;
@@ -530,18 +546,19 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
             ma.trace_rows = (int)trace_rows;
             ma.err = d_err;
-            launch_measure(ma, st);
+            cudaEventRecord(m0, ms);
+            launch_measure(ma, ms);
             h->stats.launches += 1;
-            if (timing) {
-                m1 = timer.get();
-                cudaEventRecord(m1, st);
-                timer.contract.push_back({c0, c1});
-                timer.measure.push_back({c1, m1});
-            }
+            cudaEventRecord(m1, ms);
+            cudaEventRecord(h->measure_done[yb], ms);
+            timer.contract.push_back({c0, c1});
+            timer.measure.push_back({m0, m1});
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
         }
     }
+    // the compute stream resumes after the last measurement
+    if (g > 0) cudaStreamWaitEvent(st, h->measure_done[(g - 1) % nybuf], 0);
 
     // ---- outputs -------------------------------------------------------------
     if (out_samples) {
@@ -569,10 +586,8 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     if (e != cudaSuccess) return cuda_fail(h, e, "copy of error word");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(h, e, "sampling");
-    if (timing) {
-        h->stats.ms_contract = timer.total(timer.contract);
-        h->stats.ms_measure = timer.total(timer.measure);
-    }
+    h->stats.ms_contract = timer.total(timer.contract);
+    h->stats.ms_measure = timer.total(timer.measure);
     h->stats.ms_total =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     if (herr == kDevNumeric)
@@ -655,9 +670,12 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
         h->own_stream = true;
     }
     cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&h->measure_stream, cudaStreamNonBlocking);
     for (int i = 0; i < 2; ++i) {
         cudaEventCreateWithFlags(&h->copy_done[i], cudaEventDisableTiming);
         cudaEventCreateWithFlags(&h->slot_free[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&h->contract_done[i], cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&h->measure_done[i], cudaEventDisableTiming);
     }
     h->staging.host = false;
     *out = h;
@@ -669,12 +687,16 @@ void fastmps_destroy(fastmps_handle h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
+    if (h->measure_stream) cudaStreamSynchronize(h->measure_stream);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     for (int i = 0; i < 2; ++i) {
         if (h->copy_done[i]) cudaEventDestroy(h->copy_done[i]);
         if (h->slot_free[i]) cudaEventDestroy(h->slot_free[i]);
+        if (h->contract_done[i]) cudaEventDestroy(h->contract_done[i]);
+        if (h->measure_done[i]) cudaEventDestroy(h->measure_done[i]);
     }
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+    if (h->measure_stream) cudaStreamDestroy(h->measure_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }

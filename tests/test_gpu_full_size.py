@@ -24,7 +24,7 @@ def precision_chain():
     return w, b, ts
 
 
-@pytest.mark.parametrize("precision,planes", [("bf16x2", 1), ("bf16x3l", 1)])
+@pytest.mark.parametrize("precision,planes", [("bf16x2", 1)])
 def test_precision_workload_sampled_rows(precision_chain, precision, planes):
     import torch
 
