@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
+                    help="where the synthetic isometries are drawn (QR); cpu is slower but needs no torch linalg")
     return ap.parse_args()
 
 
@@ -147,11 +149,16 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def make_workload(w, device):
-    """Site tensors of the workload, generated on the device (torch complex64)."""
+def make_workload(w, device, gen_device="cuda"):
+    """Site tensors of the workload as torch complex64 tensors on `device`, drawn on the GPU (QR by
+    torch on the device) or on the host (numpy) and then copied."""
+    if gen_device == "cuda":
+        return gen.mps_tensors(w.M, w.d, w.chi, base_seed=w.base_seed, skew=w.skew, pool=w.pool, device=device)
+    import torch
+
     b, ts, idx = gen.mps_tensors(w.M, w.d, w.chi, base_seed=w.base_seed, skew=w.skew, pool=w.pool,
-                                 device=device)
-    return b, ts, idx
+                                 dtype=np.complex64)
+    return b, [torch.from_numpy(t).to(device) for t in ts], idx
 
 
 def cpu_oracle_rate(w, b, tensors_host_fn, cpu_seconds: float, rows_max: int = 512):
@@ -195,7 +202,7 @@ def run_ours(args, rank, ws, local):
     macro = min(macro, w.N)
     device = f"cuda:{local}"
     t_gen = time.perf_counter()
-    b, ts, idx = make_workload(w, device)
+    b, ts, idx = make_workload(w, device, args.gen_device)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
 

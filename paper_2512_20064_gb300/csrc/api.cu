@@ -359,11 +359,10 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     if (h->opt.max_microbatch > 0) {
         N2 = std::max<int64_t>(128, h->opt.max_microbatch / 128 * 128);
     } else {
-        // FP32 scratch budget per micro-batch buffer (two buffers), and at least four
-        // micro-batches per site so that measurement overlaps the next contraction
+        // FP32 scratch budget per micro-batch buffer; with several micro-batches per site the
+        // measurement of one overlaps the contraction of the next
         const int64_t budget = (int64_t)2 << 30;
         N2 = std::max<int64_t>(128, budget / ((int64_t)ncols_max * 4) / 128 * 128);
-        N2 = std::min(N2, std::max<int64_t>(128, roundup((N + 3) / 4, 128)));
     }
     N2 = std::min(N2, N_pad);
     const int64_t J = (N + N2 - 1) / N2;  // micro-batches per site
@@ -769,3 +768,4 @@ int fastmps_get_stats(fastmps_handle h, fastmps_stats *out) {
 const char *fastmps_version(void) { return "fastmps-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
