@@ -159,6 +159,35 @@ int fastmps_sample_ex(fastmps_handle h, int M, int d, const int *bond_dims, int6
                       uint64_t seed, uint32_t job, uint8_t *out_samples, double *out_logprob,
                       int64_t trace_rows, double *trace_probs);
 
+/*
+ * fastmps_sample_noalloc -- sampling that allocates no memory.  (An addition
+ * of this library for callers that cannot allocate; the paper has no
+ * counterpart.)
+ *
+ * Same result as fastmps_sample_ex for rows n0 .. n0+N-1 (no trace), for
+ * callers that may not call cudaMalloc while they sample: code inside CUDA
+ * stream capture, runtimes whose device memory belongs to their own caching
+ * allocator or a fixed budget, services that forbid allocation after
+ * start-up.  Every per-call buffer (left operands, contraction scratch,
+ * outcomes, log-probabilities, error word) is carved from one static device
+ * array of 64 MiB that each device loading this library holds until the
+ * process exits; the call makes no cudaMalloc, cudaFree or other allocating
+ * call.  The handle and its site tensors must already exist (creating and
+ * loading do allocate), with FASTMPS_RESIDENT_HBM residency.
+ *   out_samples, out_logprob: DEVICE memory owned by the caller (N*M bytes,
+ *   N doubles), or NULL; host pointers are rejected (FASTMPS_ERR_INVALID_ARG).
+ *   A chain/row count whose buffers exceed the 64 MiB array is rejected with
+ *   FASTMPS_ERR_INVALID_ARG and a message giving the size it needed.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (accumulators are cleared at the start of each call); calls
+ * that overlap on the GPU race on it, so serialise them.  The call runs on
+ * the handle's stream and returns when its outputs are complete.
+ */
+int fastmps_sample_noalloc(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N,
+                           uint64_t seed, uint32_t job, uint8_t *out_samples, double *out_logprob);
+
 /* Statistics of the last fastmps_sample* call. */
 int fastmps_get_stats(fastmps_handle h, fastmps_stats *out);
 

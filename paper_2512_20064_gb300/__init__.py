@@ -22,7 +22,8 @@ from .native import LIB, build
 __all__ = [
     "FastMPSError", "Sampler", "load_library", "build", "PRECISIONS", "RESIDENCIES",
     "fastmps_create", "fastmps_destroy", "fastmps_last_error", "fastmps_load_site", "fastmps_load_pool",
-    "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_get_stats", "fastmps_version",
+    "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_sample_noalloc", "fastmps_get_stats",
+    "fastmps_version",
     "fastmps_default_options",
 ]
 
@@ -91,6 +92,10 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
                                           ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         lib.fastmps_sample_ex.restype = ctypes.c_int
+        lib.fastmps_sample_noalloc.argtypes = [H, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
+                                               ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                               ctypes.c_void_p]
+        lib.fastmps_sample_noalloc.restype = ctypes.c_int
         lib.fastmps_get_stats.argtypes = [H, P(fastmps_stats)]
         lib.fastmps_get_stats.restype = ctypes.c_int
         lib.fastmps_version.argtypes = []
@@ -198,6 +203,18 @@ def fastmps_sample_ex(h, M: int, d: int, bonds, n0: int, N: int, seed: int, job:
     b = (ctypes.c_int * (M + 1))(*[int(x) for x in bonds])
     _check(lib, h, lib.fastmps_sample_ex(h, M, d, b, n0, N, seed, job, _ptr(out_samples), _ptr(out_logprob),
                                          trace_rows, _ptr(trace_probs)))
+
+
+def fastmps_sample_noalloc(h, M: int, d: int, bonds, n0: int, N: int, seed: int, job: int, out_samples,
+                           out_logprob) -> None:
+    """Sampling that allocates nothing (static 64 MiB device scratch); outputs must be device memory.
+
+    For callers that cannot allocate while sampling (inside CUDA stream capture, under a caching
+    allocator or a fixed memory budget).  Make the first call on a device before any stream capture;
+    calls that overlap on the GPU share the scratch and must be serialised."""
+    lib = load_library()
+    b = (ctypes.c_int * (M + 1))(*[int(x) for x in bonds])
+    _check(lib, h, lib.fastmps_sample_noalloc(h, M, d, b, n0, N, seed, job, _ptr(out_samples), _ptr(out_logprob)))
 
 
 def fastmps_sample(h, M: int, d: int, bonds, N: int, seed: int, out_samples, out_logprob) -> None:

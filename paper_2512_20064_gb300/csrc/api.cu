@@ -769,3 +769,51 @@ const char *fastmps_version(void) { return "fastmps-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// Views for entry points implemented in other translation units.
+// ---------------------------------------------------------------------------
+#include "handle_view.h"
+
+namespace fastmps {
+
+int handle_view(fastmps_handle h, HandleView *out) {
+    if (!h || !out) return FASTMPS_ERR_INVALID_ARG;
+    out->device = h->device;
+    out->precision = h->opt.precision;
+    out->residency = h->opt.residency;
+    out->stream = h->stream;
+    out->num_sms = h->num_sms;
+    return FASTMPS_OK;
+}
+
+int site_view(fastmps_handle h, int k, SiteView *out) {
+    Tensor *t = site_tensor_of(h, k);
+    if (!t) return FASTMPS_ERR_NOT_LOADED;
+    out->L = t->L;
+    out->B0 = t->B_hi.as<__nv_bfloat16>();
+    out->B1 = t->B_lo.as<__nv_bfloat16>();
+    out->Bt = t->Bt.as<float>();
+    out->tmB[0] = t->tmB[0];
+    out->tmB[1] = t->tmB[1];
+    return FASTMPS_OK;
+}
+
+int set_error(fastmps_handle h, int code, const char *msg) { return fail(h, code, msg); }
+
+void precision_products(int precision, int *a_planes, int *b_planes, int *nprod, int *pa, int *pb) {
+    const PrecisionPlan p = plan_of(precision);
+    *a_planes = p.a_planes;
+    *b_planes = p.b_planes;
+    *nprod = p.nprod;
+    for (int q = 0; q < kMaxProducts; ++q) {
+        pa[q] = p.pa[q];
+        pb[q] = p.pb[q];
+    }
+}
+
+bool encode_bf16_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                     uint32_t box_outer) {
+    return encode_2d_bf16(map, base, inner, outer, ld_elems, 64, box_outer);
+}
+
+}  // namespace fastmps

@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfastmps.so")
-SOURCES = ["api.cu", "kernels.cu", "tc_contract.cu"]
-HEADERS = ["common.cuh", "launch.h"]
+SOURCES = ["api.cu", "kernels.cu", "tc_contract.cu", "noalloc.cu"]
+HEADERS = ["common.cuh", "launch.h", "handle_view.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]
