@@ -78,6 +78,8 @@ typedef struct fastmps_options {
     int64_t max_microbatch; /* rows per contraction launch; 0 = chosen from free memory */
     int autotune;           /* 1: time the candidate tile shapes once per new shape */
     void *stream;           /* cudaStream_t to run on; NULL = a stream owned by the handle */
+    int fused_measure;      /* BF16 modes: 1 (default) = measure inside the contraction kernel,
+                               0 = separate measurement kernel on a second stream */
 } fastmps_options;
 
 typedef struct fastmps_ctx *fastmps_handle;
@@ -95,7 +97,8 @@ typedef struct fastmps_stats {
     int64_t d2h_bytes;      /* device->host bytes copied during the call */
 } fastmps_stats;
 
-/* Fill *opt with the defaults: FP32, resident, automatic micro-batch, no autotune, own stream. */
+/* Fill *opt with the defaults: FP32, resident, automatic micro-batch, no autotune, own stream,
+ * fused measurement. */
 void fastmps_default_options(fastmps_options *opt);
 
 /*

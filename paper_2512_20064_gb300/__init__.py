@@ -37,7 +37,7 @@ C64, C128 = 0, 1
 
 class fastmps_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("residency", ctypes.c_int), ("max_microbatch", ctypes.c_int64),
-                ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p), ("fused_measure", ctypes.c_int)]
 
 
 class fastmps_stats(ctypes.Structure):
@@ -234,8 +234,9 @@ class Sampler:
     """A handle of the library: load site tensors once, then sample many times."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", residency: str = "hbm", max_microbatch: int = 0,
-                 stream=None):
+                 stream=None, fused_measure: bool = True):
         o = fastmps_default_options()
+        o.fused_measure = int(bool(fused_measure))
         o.precision = PRECISIONS[precision]
         o.residency = RESIDENCIES[residency]
         o.max_microbatch = int(max_microbatch)

@@ -113,7 +113,7 @@ struct fastmps_ctx {
     std::map<int, int> site_pool;                        // site k -> pool entry j
     // work buffers (grow only)
     DevBuf V[2][3];  // [ping-pong][plane]  BF16 planes, or V[x][0] FP32
-    DevBuf Y[2], P[2], logp, O, Dout, Dlogp, trace, err;
+    DevBuf Y[2], P[2], logp, O, Dout, Dlogp, trace, err, tile_cnt;
     DevBuf staging;  // device copy of a tensor being loaded
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
@@ -374,7 +374,11 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         for (int p = 0; p < planes; ++p)
             if (!h->V[x][p].ensure((size_t)N_pad * ldV * elem))
                 return fail(h, FASTMPS_ERR_OOM, "left-operand allocation failed");
-    const int nybuf = J > 1 ? 2 : 1;
+    // BF16 modes measure inside the contraction kernel (no second launch, one scratch buffer)
+    const bool fused = bf16 && h->opt.fused_measure;
+    const int nybuf = (J > 1 && !fused) ? 2 : 1;
+    if (fused && !h->tile_cnt.ensure((size_t)(N2 / 128) * sizeof(int)))
+        return fail(h, FASTMPS_ERR_OOM, "tile-counter allocation failed");
     for (int b = 0; b < nybuf; ++b)
         if (!h->Y[b].ensure((size_t)N2 * ncols_max * 4) || !h->P[b].ensure((size_t)N2 * ldP_max * 4))
             return fail(h, FASTMPS_ERR_OOM, "scratch allocation failed");
@@ -406,6 +410,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     }
 
     int *d_err = h->err.as<int>();
+    if (fused) cudaMemsetAsync(h->tile_cnt.p, 0, (size_t)(N2 / 128) * sizeof(int), st);
     e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     cudaMemsetAsync(h->logp.p, 0, (size_t)N_pad * 8, st);
@@ -497,29 +502,14 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             const int yb = (int)(g % nybuf);
             // the scratch buffer is free once the measurement two micro-batches back is done; with one
             // micro-batch per site the left rows of this contraction come from the previous measurement
-            if (g >= nybuf) cudaStreamWaitEvent(st, h->measure_done[yb], 0);
-            if (nybuf == 1 && g >= 1) cudaStreamWaitEvent(st, h->measure_done[0], 0);
+            if (!fused && g >= nybuf) cudaStreamWaitEvent(st, h->measure_done[yb], 0);
+            if (!fused && nybuf == 1 && g >= 1) cudaStreamWaitEvent(st, h->measure_done[0], 0);
             ContractOut co;
             co.Y = h->Y[yb].as<float>();
             co.ldY = L.ncols;
             co.P = h->P[yb].as<float>();
             co.ldP = L.ncols / L.bn;
             co.rows_valid = (int)rows;
-            cudaEvent_t c0 = timer.get(), c1 = timer.get(), m0 = timer.get(), m1 = timer.get();
-            cudaEventRecord(c0, st);
-            if (bf16) {
-                ta.row0 = r0;
-                ta.rows_pad = (int)rows_pad;
-                e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st);
-                if (e != cudaSuccess) return cuda_fail(h, e, "contraction launch");
-            } else {
-                launch_contract_f32(h->V[cur][0].as<float>(), ldV, r0, rows_pad, t->Bt.as<float>(), L, co, st);
-            }
-            h->stats.launches += 1;
-            h->stats.contract_launches += 1;
-            cudaEventRecord(c1, st);
-            cudaEventRecord(h->contract_done[yb], st);
-            cudaStreamWaitEvent(ms, h->contract_done[yb], 0);
             MeasureArgs ma;
             ma.Y = co.Y;
             ma.ldY = co.ldY;
@@ -545,19 +535,38 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
             ma.trace_rows = (int)trace_rows;
             ma.err = d_err;
-            cudaEventRecord(m0, ms);
-            launch_measure(ma, ms);
+            cudaEvent_t c0 = timer.get(), c1 = timer.get();
+            cudaEventRecord(c0, st);
+            if (bf16) {
+                ta.row0 = r0;
+                ta.rows_pad = (int)rows_pad;
+                e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st, fused ? &ma : nullptr,
+                                       fused ? h->tile_cnt.as<int>() : nullptr);
+                if (e != cudaSuccess) return cuda_fail(h, e, "contraction launch");
+            } else {
+                launch_contract_f32(h->V[cur][0].as<float>(), ldV, r0, rows_pad, t->Bt.as<float>(), L, co, st);
+            }
             h->stats.launches += 1;
-            cudaEventRecord(m1, ms);
-            cudaEventRecord(h->measure_done[yb], ms);
+            h->stats.contract_launches += 1;
+            cudaEventRecord(c1, st);
             timer.contract.push_back({c0, c1});
-            timer.measure.push_back({m0, m1});
+            if (!fused) {
+                cudaEvent_t m0 = timer.get(), m1 = timer.get();
+                cudaEventRecord(h->contract_done[yb], st);
+                cudaStreamWaitEvent(ms, h->contract_done[yb], 0);
+                cudaEventRecord(m0, ms);
+                launch_measure(ma, ms);
+                h->stats.launches += 1;
+                cudaEventRecord(m1, ms);
+                cudaEventRecord(h->measure_done[yb], ms);
+                timer.measure.push_back({m0, m1});
+            }
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
         }
     }
     // the compute stream resumes after the last measurement
-    if (g > 0) cudaStreamWaitEvent(st, h->measure_done[(g - 1) % nybuf], 0);
+    if (g > 0 && !fused) cudaStreamWaitEvent(st, h->measure_done[(g - 1) % nybuf], 0);
 
     // ---- outputs -------------------------------------------------------------
     if (out_samples) {
@@ -608,6 +617,7 @@ void fastmps_default_options(fastmps_options *opt) {
     opt->max_microbatch = 0;
     opt->autotune = 0;
     opt->stream = nullptr;
+    opt->fused_measure = 1;
 }
 
 int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) {

@@ -17,6 +17,7 @@ enum DeviceError : int {
     kDevTimeoutProducer = 1,
     kDevTimeoutMma = 2,
     kDevTimeoutEpilogue = 3,
+    kDevTimeoutMeasure = 4,
     kDevNumeric = 16,
 };
 
@@ -126,6 +127,11 @@ __device__ __forceinline__ void tma_load_2d(void *smem_dst, const CUtensorMap *m
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
         ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Drop a 128-byte line from L2 without writing it back (its contents become undefined).
+__device__ __forceinline__ void discard_l2_line(const void *p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(p)) : "memory");
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {

@@ -66,8 +66,12 @@ struct TcArgs {
     int rows_pad;     // multiple of 128
 };
 int tc_max_smem_ok(int device);
+struct MeasureArgs;
+// fused != nullptr: the measurement of each m-tile runs inside the contraction
+// kernel (tile_cnt: one zeroed int per m-tile, left zeroed on return).
 cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int num_sms,
-                               int *d_err, cudaStream_t st);
+                               int *d_err, cudaStream_t st, const MeasureArgs *fused = nullptr,
+                               int *tile_cnt = nullptr);
 
 // ---- measurement (Algorithm 2) --------------------------------------------
 struct MeasureArgs {

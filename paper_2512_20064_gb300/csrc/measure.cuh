@@ -1,0 +1,139 @@
+// Measurement step shared by the stand-alone measurement kernel and the
+// measurement warps fused into the tcgen05 contraction (device code, internal).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace fastmps {
+
+// ---------------------------------------------------------------------------
+// Measurement (Algorithm 2 with the exact per-sample rescaling of Sec. 3.3.1).
+// Phase 1, one thread per sample (measure_draw):
+//  * w_s = sum of the FP32 per-tile sums of squares of outcome block s,
+//    accumulated in FP64;
+//  * C_s = w_0 + ... + w_s in s order (FP64), Z = C_{d-1}, Philox uniform u,
+//    s* = #{s < d-1 : C_s < u Z}: the decision is taken in FP64 as in the
+//    oracle;
+//  * log p accumulates log w_{s*} - log Z in FP64; each logarithm is taken in
+//    FP32 (w and Z are O(1) because the left vector is renormalised at every
+//    site, so the absolute error per site is ~1e-7).
+// Phase 2, a warp per sample (measure_write_row): the selected block y_{s*} is scaled
+// by 1/sqrt(w_{s*}) (FP32; the scale cancels in every later ratio w/Z) and
+// written as the next left row -- FP32, or BF16 planes of successive
+// residuals -- with coalesced 16-byte loads.
+// GB300's FP64 pipes are narrow, so FP64 is kept to the O(d) per-sample
+// operations of the draw and the accumulation, one sample per lane.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void write_planes(float x, int nplanes, __nv_bfloat16 &h0, __nv_bfloat16 &h1,
+                                             __nv_bfloat16 &h2) {
+    h0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h0);
+    h1 = __float2bfloat16_rn(r1);
+    h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+    if (nplanes < 3) h2 = __float2bfloat16_rn(0.f);
+}
+
+__device__ __forceinline__ void measure_write_row(const MeasureArgs &a, int lane, const float *ysrc, float scale,
+                                                  int64_t grow) {
+    const int nreal = 2 * a.chi_r;
+    if (a.V32) {
+        float *dst = a.V32 + grow * a.ld_next;
+        if ((nreal & 3) == 0) {
+            for (int i = 4 * lane; i < a.K_next; i += 128) {
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (i < nreal) {
+                    v = __ldcg(reinterpret_cast<const float4 *>(ysrc + i));
+                    v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+                }
+                *reinterpret_cast<float4 *>(dst + i) = v;
+            }
+        } else {
+            for (int i = lane; i < a.K_next; i += 32) dst[i] = i < nreal ? ysrc[i] * scale : 0.f;
+        }
+        return;
+    }
+    __nv_bfloat16 *d0 = a.Vp[0] + grow * a.ld_next;
+    __nv_bfloat16 *d1 = a.Vp[1] + grow * a.ld_next;
+    __nv_bfloat16 *d2 = a.nplanes > 2 ? a.Vp[2] + grow * a.ld_next : nullptr;
+    if ((nreal & 3) == 0) {
+        for (int i = 4 * lane; i < a.K_next; i += 128) {
+            float x[4] = {0.f, 0.f, 0.f, 0.f};
+            if (i < nreal) {
+                const float4 v = __ldcg(reinterpret_cast<const float4 *>(ysrc + i));
+                x[0] = v.x * scale; x[1] = v.y * scale; x[2] = v.z * scale; x[3] = v.w * scale;
+            }
+            __align__(8) __nv_bfloat16 p0[4], p1[4], p2[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) write_planes(x[e], a.nplanes, p0[e], p1[e], p2[e]);
+            *reinterpret_cast<uint2 *>(d0 + i) = *reinterpret_cast<const uint2 *>(p0);
+            *reinterpret_cast<uint2 *>(d1 + i) = *reinterpret_cast<const uint2 *>(p1);
+            if (d2) *reinterpret_cast<uint2 *>(d2 + i) = *reinterpret_cast<const uint2 *>(p2);
+        }
+    } else {
+        for (int i = lane; i < a.K_next; i += 32) {
+            const float x = i < nreal ? ysrc[i] * scale : 0.f;
+            __nv_bfloat16 h0, h1, h2;
+            write_planes(x, a.nplanes, h0, h1, h2);
+            d0[i] = h0;
+            d1[i] = h1;
+            if (d2) d2[i] = h2;
+        }
+    }
+}
+
+// Phase 1 for sample `row` of the micro-batch (row < a.rows): draw, outcome,
+// log-probability, optional trace.  Returns the outcome and sets *scale to
+// 1/sqrt(w_{s*}).  P is read through L2 (it may have been written by other
+// thread blocks of the same kernel).
+__device__ __forceinline__ int measure_draw(const MeasureArgs &a, int row, float *scale_out) {
+    int sstar = 0;
+    float scale = 0.f;
+    {
+        const float *Prow = a.P + (int64_t)row * a.ldP;
+        const int T = a.tiles_per_s;
+        // pass 1: Z = w_0 + ... + w_{d-1} in s order
+        double Z = 0.0;
+        for (int s = 0; s < a.d; ++s) {
+            double acc = 0.0;
+            for (int j = 0; j < T; ++j) acc += (double)__ldcg(Prow + s * T + j);
+            Z += acc;
+        }
+        const uint64_t n = a.n_base + (uint64_t)row;
+        const double t = sample_uniform(a.seed, n, a.k, a.job) * Z;
+        // pass 2: the same partial sums again; s* is the first s < d-1 with C_s >= t (else d-1),
+        // which equals #{s < d-1 : C_s < t} because C is non-decreasing
+        double C = 0.0, ws = 0.0;
+        sstar = a.d - 1;
+        for (int s = 0; s < a.d; ++s) {
+            double acc = 0.0;
+            for (int j = 0; j < T; ++j) acc += (double)__ldcg(Prow + s * T + j);
+            C += acc;
+            if (s == a.d - 1 || C >= t) {
+                sstar = s;
+                ws = acc;
+                break;
+            }
+        }
+        const bool ok = (Z > 0.0) && isfinite(Z) && (ws > 0.0);
+        const int64_t grow = a.row0 + row;
+        a.outcomes[row] = (uint8_t)sstar;
+        if (ok) a.logp[grow] += (double)(logf((float)ws) - logf((float)Z));
+        else atomicExch(a.err, (int)kDevNumeric);
+        if (a.trace && grow < a.trace_rows) {
+            for (int s = 0; s < a.d; ++s) {
+                double acc = 0.0;
+                for (int j = 0; j < T; ++j) acc += (double)__ldcg(Prow + s * T + j);
+                a.trace[grow * a.d + s] = ok ? acc / Z : 0.0;
+            }
+        }
+        scale = ok ? rsqrtf((float)ws) : 0.f;
+    }
+    *scale_out = scale;
+    return sstar;
+}
+
+}  // namespace fastmps

@@ -17,16 +17,29 @@
 //            store the FP32 tile to the scratch Y and the row's sum of squares
 //            over the tile (the tile lies in one outcome block s) to P.
 // Two accumulator buffers of 256 columns let the epilogue of tile i overlap
-// the main loop of tile i+1.  Every wait is bounded (common.cuh); on a
-// timeout the kernel records an error word, drains its own in-flight copies
-// and MMAs, frees tensor memory and returns.
+// the main loop of tile i+1.
+//
+// Fused variant (320 threads): warps 6-9 measure.  After storing a tile, the
+// epilogue publishes it (fence, then a per-m-tile counter in global memory);
+// the thread block that completes the last n-tile of an m-tile hands that
+// m-tile to its measurement warps through a shared-memory ring.  They combine
+// the per-tile sums of squares of the 128 rows (written by other blocks, read
+// through L2), draw the outcomes and write the renormalised selected blocks as
+// the next left rows (Algorithm 2) while the tensor cores continue with the
+// next tiles; the scratch rows are still hot in L2.
+//
+// Every wait is bounded (common.cuh); on a timeout the kernel records an
+// error word, drains its own in-flight copies and MMAs, frees tensor memory
+// and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "common.cuh"
 #include "launch.h"
+#include "measure.cuh"
 
 namespace fastmps {
 
@@ -34,7 +47,10 @@ namespace {
 
 constexpr int kBM = 128;
 constexpr int kBK = 64;                      // BF16 elements per k-block = one 128-byte swizzle row
-constexpr int kThreads = 192;
+constexpr int kThreads = 192;                // TMA + MMA + 4 epilogue warps
+constexpr int kThreadsFused = 320;           // + 4 measurement warps
+constexpr int kRing = 4;                     // m-tiles queued for the measurement warps
+constexpr int kBarrierBytes = 2048;          // mbarriers, ring, measurement staging
 constexpr uint32_t kTmemCols = 512;          // 2 accumulators x 256 columns
 constexpr uint32_t kAccStride = 256;
 constexpr uint32_t kATileBytes = kBM * kBK * 2;  // 16 KB
@@ -54,7 +70,32 @@ struct TcParams {
     int ldP;
     int rows_valid;
     int *err;
+    // fused measurement
+    int *tile_cnt;     // per m-tile count of finished n-tiles (zero at launch; reset by the measurer)
+    MeasureArgs m;
 };
+
+// Named barriers among a subset of warps.  The non-.aligned forms are used
+// because lanes of one warp may reach them at different times.
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Named barrier that also ORs a predicate over the participating threads: a
+// group decides together whether to leave a loop, so no thread is left
+// waiting at a later barrier for a thread that already left.
+__device__ __forceinline__ bool named_bar_any(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
 
 __device__ __forceinline__ void record_error(int *err, volatile int *abort_flag, int code) {
     *abort_flag = 1;
@@ -70,7 +111,8 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity) 
     return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 1)
+template <bool kFused>
+__global__ void __launch_bounds__(kFused ? kThreadsFused : kThreads, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
                    const __grid_constant__ CUtensorMap tmB1, const TcParams p) {
@@ -83,8 +125,13 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     uint64_t *tfull = empty + p.stages;
     uint64_t *tempty = tfull + 2;
     uint64_t *drain = tempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *mfull = drain + 1;     // [kRing] m-tile handed to the measurement warps
+    uint64_t *mempty = mfull + kRing;
+    int *mt_slot = reinterpret_cast<int *>(mempty + kRing);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mt_slot + kRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *m_sstar = reinterpret_cast<int *>(tmem_slot + 4);   // [128]
+    float *m_scale = reinterpret_cast<float *>(m_sstar + kBM);  // [128]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -98,6 +145,10 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
         mbar_init(&tempty[0], 128);
         mbar_init(&tempty[1], 128);
         mbar_init(drain, 1);
+        for (int r = 0; r < kRing; ++r) {
+            mbar_init(&mfull[r], 1);
+            mbar_init(&mempty[r], kBM);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -218,16 +269,19 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             }
         }
         __syncwarp();
-    } else {
+    } else if (warp < 6) {
         // ---------------- epilogue: warps 2..5 ----------------
         const int quad = warp & 3;  // tensor-memory lane quarter this warp may access
         int lt = 0;
+        int ring = 0;               // (fused) next ring slot and its phase, tracked by thread 64
+        uint32_t ring_phase = 0;
         for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++lt) {
             const int buf = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
             const int mt = tile / p.num_n_tiles;
             const int nt = tile - mt * p.num_n_tiles;
-            if (!mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag)) {
+            const bool ready = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag);
+            if (kFused ? named_bar_any(1, 128, !ready) : !ready) {
                 record_error(p.err, abort_flag, kDevTimeoutEpilogue);
                 break;
             }
@@ -257,6 +311,80 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             tc_fence_before();
             mbar_arrive(&tempty[buf]);
             if (valid) p.P[(int64_t)row * p.ldP + nt] = ss;
+            if (kFused) {
+                // publish this tile; the block that completes the m-tile measures it
+                __threadfence();
+                named_bar_sync(1, 128);
+                if (threadIdx.x == 64) {
+                    const int done = atomicAdd(&p.tile_cnt[mt], 1);
+                    if (done == p.num_n_tiles - 1) {
+                        __threadfence();
+                        if (!mbar_wait_bounded(&mempty[ring], ring_phase ^ 1u, abort_flag)) {
+                            record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                        } else {
+                            mt_slot[ring] = mt;
+                            mbar_arrive(&mfull[ring]);
+                            if (++ring == kRing) {
+                                ring = 0;
+                                ring_phase ^= 1u;
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (kFused && threadIdx.x == 64) {
+            // no more m-tiles from this block: stop the measurement warps
+            if (mbar_wait_bounded(&mempty[ring], ring_phase ^ 1u, abort_flag)) {
+                mt_slot[ring] = -1;
+                mbar_arrive(&mfull[ring]);
+            }
+        }
+    } else if (kFused) {
+        // ---------------- measurement: warps 6..9 ----------------
+        const int m = threadIdx.x - 192;  // 0..127: the row of the m-tile this thread draws
+        const int mw = m >> 5;
+        int ring = 0;
+        uint32_t ring_phase = 0;
+        while (true) {
+            const bool ready = mbar_wait_bounded(&mfull[ring], ring_phase, abort_flag);
+            if (named_bar_any(2, 128, !ready)) {
+                record_error(p.err, abort_flag, kDevTimeoutMeasure);
+                break;
+            }
+            const int mt = mt_slot[ring];
+            mbar_arrive(&mempty[ring]);
+            if (++ring == kRing) {
+                ring = 0;
+                ring_phase ^= 1u;
+            }
+            if (mt < 0) break;
+            __threadfence();
+            if (m == 0) p.tile_cnt[mt] = 0;
+            const int row = mt * kBM + m;
+            int sstar = 0;
+            float scale = 0.f;
+            if (row < p.rows_valid) sstar = measure_draw(p.m, row, &scale);
+            m_sstar[m] = sstar;
+            m_scale[m] = scale;
+            named_bar_sync(2, 128);
+            for (int j = 0; j < 32; ++j) {
+                const int r = mt * kBM + mw * 32 + j;
+                if (r >= p.rows_valid) break;
+                const int sj = m_sstar[mw * 32 + j];
+                const float *ysrc = p.Y + (int64_t)r * p.ldY + (int64_t)sj * p.m.Cs;
+                measure_write_row(p.m, lane, ysrc, m_scale[mw * 32 + j], p.m.row0 + r);
+            }
+            named_bar_sync(2, 128);
+            // the m-tile's scratch rows are not read again: drop them from L2 so that they are
+            // never written back to DRAM
+            const int rr = mt * kBM + m;
+            if (rr < p.rows_valid) {
+                const float *yr = p.Y + (int64_t)rr * p.ldY;
+                const int lines = (int)(p.ldY / 32);
+                for (int l = 0; l < lines; ++l) discard_l2_line(yr + 32 * l);
+            }
         }
     }
 
@@ -269,7 +397,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
 }
 
 int stages_for(uint32_t stage_bytes) {
-    const int fixed = 1024 /* alignment */ + 256 /* barriers */;
+    const int fixed = 1024 /* alignment */ + kBarrierBytes;
     int s = (kSmemLimit - fixed) / (int)stage_bytes;
     if (s > kMaxStages) s = kMaxStages;
     return s;
@@ -284,7 +412,7 @@ int tc_max_smem_ok(int device) {
 }
 
 cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int num_sms, int *d_err,
-                               cudaStream_t st) {
+                               cudaStream_t st, const MeasureArgs *fused, int *tile_cnt) {
     TcParams p;
     p.num_m_tiles = a.rows_pad / kBM;
     p.num_n_tiles = L.ncols / L.bn;
@@ -314,15 +442,29 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     p.ldP = o.ldP;
     p.rows_valid = o.rows_valid;
     p.err = d_err;
-    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + 256;
-    cudaError_t e = cudaFuncSetAttribute(tc_contract_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    if (e != cudaSuccess) return e;
+    p.tile_cnt = tile_cnt;
+    if (fused) {
+        if (!tile_cnt) return cudaErrorInvalidValue;
+        p.m = *fused;
+    } else {
+        memset(&p.m, 0, sizeof(p.m));
+    }
+    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kBarrierBytes;
     const int total = p.num_m_tiles * p.num_n_tiles;
     const int grid = total < num_sms ? total : num_sms;
     if (grid <= 0) return cudaSuccess;
-    tc_contract_kernel<<<grid, kThreads, smem, st>>>(a.tmA[0], a.tmA[a.a_planes > 1 ? 1 : 0],
-                                                     a.tmA[a.a_planes > 2 ? 2 : 0], a.tmB[0],
-                                                     a.tmB[a.b_planes > 1 ? 1 : 0], p);
+    const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
+    const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
+    cudaError_t e;
+    if (fused) {
+        e = cudaFuncSetAttribute(tc_contract_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+        if (e != cudaSuccess) return e;
+        tc_contract_kernel<true><<<grid, kThreadsFused, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
+    } else {
+        e = cudaFuncSetAttribute(tc_contract_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+        if (e != cudaSuccess) return e;
+        tc_contract_kernel<false><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
+    }
     return cudaGetLastError();
 }
 

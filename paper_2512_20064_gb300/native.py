@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfastmps.so")
 SOURCES = ["api.cu", "kernels.cu", "tc_contract.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "launch.h", "handle_view.h"]
+HEADERS = ["common.cuh", "launch.h", "handle_view.h", "measure.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]
