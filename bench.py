@@ -50,8 +50,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--separate-measure", action="store_true",
-                    help="BF16 modes: separate measurement kernel instead of the fused one")
+    ap.add_argument("--fused-measure", action="store_true",
+                    help="BF16 modes: measurement warps inside the contraction kernel")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="where the synthetic isometries are drawn (QR); cpu is slower but needs no torch linalg")
     return ap.parse_args()
@@ -209,7 +209,7 @@ def run_ours(args, rank, ws, local):
     t_gen = time.perf_counter() - t_gen
 
     stream = torch.cuda.Stream(device=local)
-    s = F.Sampler(device=local, precision=precision, stream=stream, fused_measure=not args.separate_measure)
+    s = F.Sampler(device=local, precision=precision, stream=stream, fused_measure=args.fused_measure)
     t_load = time.perf_counter()
     for k in range(w.M):
         A = ts[idx[k]]
@@ -282,7 +282,7 @@ def run_ours(args, rank, ws, local):
         "dtype": "bf16" if tensor else "f32", "data": "synthetic (seeded skewed Haar isometries, GBS-shaped)",
         "config": {"workload": w.note, "M": w.M, "d": w.d, "chi": w.chi, "N": w.N, "rows_per_step": macro,
                    "precision": precision, "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                   "measurement": "separate kernel" if args.separate_measure or precision == "fp32" else "fused",
+                   "measurement": "fused" if args.fused_measure and precision != "fp32" else "separate kernel",
                    "l2": "inputs larger than L2 (site tensors and left operand exceed 129 MB per step)"},
         "roofline": roof, "gpu_launches": launches, "clocks": clk,
         "setup_s": {"generate": t_gen, "load": t_load},

@@ -78,8 +78,9 @@ typedef struct fastmps_options {
     int64_t max_microbatch; /* rows per contraction launch; 0 = chosen from free memory */
     int autotune;           /* 1: time the candidate tile shapes once per new shape */
     void *stream;           /* cudaStream_t to run on; NULL = a stream owned by the handle */
-    int fused_measure;      /* BF16 modes: 1 (default) = measure inside the contraction kernel,
-                               0 = separate measurement kernel on a second stream */
+    int fused_measure;      /* BF16 modes: 0 (default) = separate measurement kernel, overlapped
+                               on a second stream when there are several micro-batches;
+                               1 = measurement warps inside the contraction kernel */
 } fastmps_options;
 
 typedef struct fastmps_ctx *fastmps_handle;
@@ -98,7 +99,7 @@ typedef struct fastmps_stats {
 } fastmps_stats;
 
 /* Fill *opt with the defaults: FP32, resident, automatic micro-batch, no autotune, own stream,
- * fused measurement. */
+ * separate measurement kernel. */
 void fastmps_default_options(fastmps_options *opt);
 
 /*

@@ -52,3 +52,42 @@ def dequant_bf16(A, planes: int = 1) -> np.ndarray:
 def complex64_of(A) -> np.ndarray:
     """The complex128 tensor that a complex64 store of ``A`` represents."""
     return np.asarray(A).astype(np.complex64).astype(np.complex128)
+
+
+# ---------------------------------------------------------------------------
+# FP8 E4M3 (the OCP "E4M3FN" format: 1 sign bit, 4 exponent bits with bias 7,
+# 3 mantissa bits, largest finite value 448, subnormals down to 2^-9, no
+# infinities), round to nearest, ties to even, saturating to +-448.
+# ---------------------------------------------------------------------------
+
+E4M3_MAX = 448.0
+
+
+def e4m3_round(x) -> np.ndarray:
+    """Round to the nearest E4M3 value (ties to even), saturating at +-448; float64 result."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(a)                      # a = m * 2^ex, m in [0.5, 1)
+    e = np.maximum(ex - 1, -6)               # exponent of the leading bit; -6 for subnormals
+    q = np.ldexp(1.0, (e - 3).astype(np.int64))  # spacing of representable values at that exponent
+    r = np.round(a / q) * q                  # numpy rounds halves to even
+    r = np.minimum(r, E4M3_MAX)
+    r[a == 0] = 0.0
+    return np.copysign(r, x)
+
+
+def e4m3_site_scale(A) -> float:
+    """Power-of-two scale of an FP8 site store: the largest 2^j with max|Re, Im| * 2^j <= 448."""
+    A = np.asarray(A)
+    m = float(max(np.abs(A.real).max(), np.abs(A.imag).max()))
+    if m == 0.0:
+        return 1.0
+    return float(2.0 ** np.floor(np.log2(E4M3_MAX / m)))
+
+
+def dequant_e4m3(A) -> np.ndarray:
+    """The complex128 tensor an FP8 E4M3 store with a per-site power-of-two scale represents."""
+    s = e4m3_site_scale(A)
+    re = np.asarray(A.real, dtype=np.float32).astype(np.float64)
+    im = np.asarray(A.imag, dtype=np.float32).astype(np.float64)
+    return (e4m3_round(re * s) + 1j * e4m3_round(im * s)) / s

@@ -234,7 +234,7 @@ class Sampler:
     """A handle of the library: load site tensors once, then sample many times."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", residency: str = "hbm", max_microbatch: int = 0,
-                 stream=None, fused_measure: bool = True):
+                 stream=None, fused_measure: bool = False):
         o = fastmps_default_options()
         o.fused_measure = int(bool(fused_measure))
         o.precision = PRECISIONS[precision]

@@ -113,7 +113,7 @@ struct fastmps_ctx {
     std::map<int, int> site_pool;                        // site k -> pool entry j
     // work buffers (grow only)
     DevBuf V[2][3];  // [ping-pong][plane]  BF16 planes, or V[x][0] FP32
-    DevBuf Y[2], P[2], logp, O, Dout, Dlogp, trace, err, tile_cnt;
+    DevBuf Y[2], P[2], logp, O, Dout, Dlogp, trace, err;
     DevBuf staging;  // device copy of a tensor being loaded
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
@@ -363,6 +363,10 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         // measurement of one overlaps the contraction of the next
         const int64_t budget = (int64_t)2 << 30;
         N2 = std::max<int64_t>(128, budget / ((int64_t)ncols_max * 4) / 128 * 128);
+        // the fused BF16 kernel gives each thread block whole m-tiles: use whole waves of
+        // (128 rows x SMs) so that every block gets the same number of m-tiles
+        const int64_t wave = (int64_t)128 * h->num_sms;
+        if (bf16 && h->opt.fused_measure && N2 >= wave && N_pad > N2) N2 = N2 / wave * wave;
     }
     N2 = std::min(N2, N_pad);
     const int64_t J = (N + N2 - 1) / N2;  // micro-batches per site
@@ -377,8 +381,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     // BF16 modes measure inside the contraction kernel (no second launch, one scratch buffer)
     const bool fused = bf16 && h->opt.fused_measure;
     const int nybuf = (J > 1 && !fused) ? 2 : 1;
-    if (fused && !h->tile_cnt.ensure((size_t)(N2 / 128) * sizeof(int)))
-        return fail(h, FASTMPS_ERR_OOM, "tile-counter allocation failed");
+
     for (int b = 0; b < nybuf; ++b)
         if (!h->Y[b].ensure((size_t)N2 * ncols_max * 4) || !h->P[b].ensure((size_t)N2 * ldP_max * 4))
             return fail(h, FASTMPS_ERR_OOM, "scratch allocation failed");
@@ -410,7 +413,6 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     }
 
     int *d_err = h->err.as<int>();
-    if (fused) cudaMemsetAsync(h->tile_cnt.p, 0, (size_t)(N2 / 128) * sizeof(int), st);
     e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     cudaMemsetAsync(h->logp.p, 0, (size_t)N_pad * 8, st);
@@ -540,8 +542,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             if (bf16) {
                 ta.row0 = r0;
                 ta.rows_pad = (int)rows_pad;
-                e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st, fused ? &ma : nullptr,
-                                       fused ? h->tile_cnt.as<int>() : nullptr);
+                e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st, fused ? &ma : nullptr);
                 if (e != cudaSuccess) return cuda_fail(h, e, "contraction launch");
             } else {
                 launch_contract_f32(h->V[cur][0].as<float>(), ldV, r0, rows_pad, t->Bt.as<float>(), L, co, st);
@@ -617,7 +618,7 @@ void fastmps_default_options(fastmps_options *opt) {
     opt->max_microbatch = 0;
     opt->autotune = 0;
     opt->stream = nullptr;
-    opt->fused_measure = 1;
+    opt->fused_measure = 0;
 }
 
 int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) {

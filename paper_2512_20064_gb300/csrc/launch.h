@@ -68,10 +68,9 @@ struct TcArgs {
 int tc_max_smem_ok(int device);
 struct MeasureArgs;
 // fused != nullptr: the measurement of each m-tile runs inside the contraction
-// kernel (tile_cnt: one zeroed int per m-tile, left zeroed on return).
+// kernel (one thread block per m-tile at a time; grid = min(m-tiles, SMs)).
 cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int num_sms,
-                               int *d_err, cudaStream_t st, const MeasureArgs *fused = nullptr,
-                               int *tile_cnt = nullptr);
+                               int *d_err, cudaStream_t st, const MeasureArgs *fused = nullptr);
 
 // ---- measurement (Algorithm 2) --------------------------------------------
 struct MeasureArgs {

@@ -43,13 +43,22 @@ __device__ __forceinline__ void measure_write_row(const MeasureArgs &a, int lane
     if (a.V32) {
         float *dst = a.V32 + grow * a.ld_next;
         if ((nreal & 3) == 0) {
-            for (int i = 4 * lane; i < a.K_next; i += 128) {
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (i < nreal) {
-                    v = __ldcg(reinterpret_cast<const float4 *>(ysrc + i));
-                    v.x *= scale; v.y *= scale; v.z *= scale; v.w *= scale;
+            constexpr int U = 4;
+            for (int base = 4 * lane; base < a.K_next; base += 128 * U) {
+                float4 v[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = base + 128 * u;
+                    v[u] = i < nreal ? __ldcg(reinterpret_cast<const float4 *>(ysrc + i))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                *reinterpret_cast<float4 *>(dst + i) = v;
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = base + 128 * u;
+                    if (i >= a.K_next) break;
+                    *reinterpret_cast<float4 *>(dst + i) =
+                        make_float4(v[u].x * scale, v[u].y * scale, v[u].z * scale, v[u].w * scale);
+                }
             }
         } else {
             for (int i = lane; i < a.K_next; i += 32) dst[i] = i < nreal ? ysrc[i] * scale : 0.f;
@@ -60,18 +69,27 @@ __device__ __forceinline__ void measure_write_row(const MeasureArgs &a, int lane
     __nv_bfloat16 *d1 = a.Vp[1] + grow * a.ld_next;
     __nv_bfloat16 *d2 = a.nplanes > 2 ? a.Vp[2] + grow * a.ld_next : nullptr;
     if ((nreal & 3) == 0) {
-        for (int i = 4 * lane; i < a.K_next; i += 128) {
-            float x[4] = {0.f, 0.f, 0.f, 0.f};
-            if (i < nreal) {
-                const float4 v = __ldcg(reinterpret_cast<const float4 *>(ysrc + i));
-                x[0] = v.x * scale; x[1] = v.y * scale; x[2] = v.z * scale; x[3] = v.w * scale;
-            }
-            __align__(8) __nv_bfloat16 p0[4], p1[4], p2[4];
+        // four 16-byte loads in flight per lane before any store
+        constexpr int U = 4;
+        for (int base = 4 * lane; base < a.K_next; base += 128 * U) {
+            float4 v[U];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) write_planes(x[e], a.nplanes, p0[e], p1[e], p2[e]);
-            *reinterpret_cast<uint2 *>(d0 + i) = *reinterpret_cast<const uint2 *>(p0);
-            *reinterpret_cast<uint2 *>(d1 + i) = *reinterpret_cast<const uint2 *>(p1);
-            if (d2) *reinterpret_cast<uint2 *>(d2 + i) = *reinterpret_cast<const uint2 *>(p2);
+            for (int u = 0; u < U; ++u) {
+                const int i = base + 128 * u;
+                v[u] = i < nreal ? __ldcg(reinterpret_cast<const float4 *>(ysrc + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = base + 128 * u;
+                if (i >= a.K_next) break;
+                const float x[4] = {v[u].x * scale, v[u].y * scale, v[u].z * scale, v[u].w * scale};
+                __align__(8) __nv_bfloat16 p0[4], p1[4], p2[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) write_planes(x[e], a.nplanes, p0[e], p1[e], p2[e]);
+                *reinterpret_cast<uint2 *>(d0 + i) = *reinterpret_cast<const uint2 *>(p0);
+                *reinterpret_cast<uint2 *>(d1 + i) = *reinterpret_cast<const uint2 *>(p1);
+                if (d2) *reinterpret_cast<uint2 *>(d2 + i) = *reinterpret_cast<const uint2 *>(p2);
+            }
         }
     } else {
         for (int i = lane; i < a.K_next; i += 32) {

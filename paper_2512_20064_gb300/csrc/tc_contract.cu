@@ -19,14 +19,13 @@
 // Two accumulator buffers of 256 columns let the epilogue of tile i overlap
 // the main loop of tile i+1.
 //
-// Fused variant (320 threads): warps 6-9 measure.  After storing a tile, the
-// epilogue publishes it (fence, then a per-m-tile counter in global memory);
-// the thread block that completes the last n-tile of an m-tile hands that
-// m-tile to its measurement warps through a shared-memory ring.  They combine
-// the per-tile sums of squares of the 128 rows (written by other blocks, read
-// through L2), draw the outcomes and write the renormalised selected blocks as
-// the next left rows (Algorithm 2) while the tensor cores continue with the
-// next tiles; the scratch rows are still hot in L2.
+// Fused variant (320 threads): warps 6-9 measure.  Each thread block owns
+// whole m-tiles (128 rows) and walks all their n-tiles in order; after the
+// last n-tile of an m-tile the epilogue hands it to the block's measurement
+// warps through a shared-memory mbarrier ring (CTA-scope ordering only).
+// They combine the per-tile sums of squares of the 128 rows in FP64, draw the
+// outcomes and write the renormalised selected blocks as the next left rows
+// (Algorithm 2) while the tensor cores work on the next m-tile.
 //
 // Every wait is bounded (common.cuh); on a timeout the kernel records an
 // error word, drains its own in-flight copies and MMAs, frees tensor memory
@@ -49,7 +48,7 @@ constexpr int kBM = 128;
 constexpr int kBK = 64;                      // BF16 elements per k-block = one 128-byte swizzle row
 constexpr int kThreads = 192;                // TMA + MMA + 4 epilogue warps
 constexpr int kThreadsFused = 320;           // + 4 measurement warps
-constexpr int kRing = 4;                     // m-tiles queued for the measurement warps
+constexpr int kRing = 4;                     // finished m-tiles queued for the measurement warps
 constexpr int kBarrierBytes = 2048;          // mbarriers, ring, measurement staging
 constexpr uint32_t kTmemCols = 512;          // 2 accumulators x 256 columns
 constexpr uint32_t kAccStride = 256;
@@ -71,7 +70,6 @@ struct TcParams {
     int rows_valid;
     int *err;
     // fused measurement
-    int *tile_cnt;     // per m-tile count of finished n-tiles (zero at launch; reset by the measurer)
     MeasureArgs m;
 };
 
@@ -109,6 +107,24 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity) 
         if (global_ns() - t0 > 200000000ull) return false;
     }
     return true;
+}
+
+// The block's i-th tile.  Unfused: tiles are dealt round-robin in n-fastest
+// order.  Fused: the block owns m-tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// and visits all n-tiles of each (i % num_n_tiles == num_n_tiles - 1 ends an
+// m-tile).  Returns false past the last tile.
+template <bool kFused>
+__device__ __forceinline__ bool tile_of(const TcParams &p, int i, int &mt, int &nt) {
+    if (kFused) {
+        const int q = i / p.num_n_tiles;
+        nt = i - q * p.num_n_tiles;
+        mt = blockIdx.x + q * gridDim.x;
+        return mt < p.num_m_tiles;
+    }
+    const int tile = blockIdx.x + i * gridDim.x;
+    mt = tile / p.num_n_tiles;
+    nt = tile - mt * p.num_n_tiles;
+    return tile < p.num_m_tiles * p.num_n_tiles;
 }
 
 template <bool kFused>
@@ -167,7 +183,6 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int total = p.num_m_tiles * p.num_n_tiles;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -177,9 +192,8 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             int last_parity[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) last_parity[s] = -1;
             bool failed = false;
-            for (int tile = blockIdx.x; tile < total && !failed; tile += gridDim.x) {
-                const int mt = tile / p.num_n_tiles;
-                const int nt = tile - mt * p.num_n_tiles;
+            int mt, nt;
+            for (int i = 0; !failed && tile_of<kFused>(p, i, mt, nt); ++i) {
                 const int y_a = p.row0 + mt * kBM;
                 const int y_b = nt * p.bn;
                 for (int kb = 0; kb < p.num_k_blocks; ++kb) {
@@ -219,7 +233,8 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             int lt = 0;
             bool failed = false;
             bool issued = false;
-            for (int tile = blockIdx.x; tile < total && !failed; tile += gridDim.x, ++lt) {
+            int mt, nt;
+            for (int i = 0; !failed && tile_of<kFused>(p, i, mt, nt); ++i, ++lt) {
                 const int buf = lt & 1;
                 const uint32_t use = (uint32_t)(lt >> 1);
                 if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag)) {
@@ -275,11 +290,10 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
         int lt = 0;
         int ring = 0;               // (fused) next ring slot and its phase, tracked by thread 64
         uint32_t ring_phase = 0;
-        for (int tile = blockIdx.x; tile < total; tile += gridDim.x, ++lt) {
+        int mt, nt;
+        for (int i = 0; tile_of<kFused>(p, i, mt, nt); ++i, ++lt) {
             const int buf = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
-            const int mt = tile / p.num_n_tiles;
-            const int nt = tile - mt * p.num_n_tiles;
             const bool ready = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag);
             if (kFused ? named_bar_any(1, 128, !ready) : !ready) {
                 record_error(p.err, abort_flag, kDevTimeoutEpilogue);
@@ -311,23 +325,19 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             tc_fence_before();
             mbar_arrive(&tempty[buf]);
             if (valid) p.P[(int64_t)row * p.ldP + nt] = ss;
-            if (kFused) {
-                // publish this tile; the block that completes the m-tile measures it
-                __threadfence();
+            if (kFused && (i + 1) % p.num_n_tiles == 0) {
+                // the m-tile is complete: the group barrier orders the 128 threads' stores before
+                // the mbarrier arrive that hands the m-tile to the measurement warps
                 named_bar_sync(1, 128);
                 if (threadIdx.x == 64) {
-                    const int done = atomicAdd(&p.tile_cnt[mt], 1);
-                    if (done == p.num_n_tiles - 1) {
-                        __threadfence();
-                        if (!mbar_wait_bounded(&mempty[ring], ring_phase ^ 1u, abort_flag)) {
-                            record_error(p.err, abort_flag, kDevTimeoutEpilogue);
-                        } else {
-                            mt_slot[ring] = mt;
-                            mbar_arrive(&mfull[ring]);
-                            if (++ring == kRing) {
-                                ring = 0;
-                                ring_phase ^= 1u;
-                            }
+                    if (!mbar_wait_bounded(&mempty[ring], ring_phase ^ 1u, abort_flag)) {
+                        record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                    } else {
+                        mt_slot[ring] = mt;
+                        mbar_arrive(&mfull[ring]);
+                        if (++ring == kRing) {
+                            ring = 0;
+                            ring_phase ^= 1u;
                         }
                     }
                 }
@@ -360,8 +370,6 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                 ring_phase ^= 1u;
             }
             if (mt < 0) break;
-            __threadfence();
-            if (m == 0) p.tile_cnt[mt] = 0;
             const int row = mt * kBM + m;
             int sstar = 0;
             float scale = 0.f;
@@ -377,14 +385,6 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                 measure_write_row(p.m, lane, ysrc, m_scale[mw * 32 + j], p.m.row0 + r);
             }
             named_bar_sync(2, 128);
-            // the m-tile's scratch rows are not read again: drop them from L2 so that they are
-            // never written back to DRAM
-            const int rr = mt * kBM + m;
-            if (rr < p.rows_valid) {
-                const float *yr = p.Y + (int64_t)rr * p.ldY;
-                const int lines = (int)(p.ldY / 32);
-                for (int l = 0; l < lines; ++l) discard_l2_line(yr + 32 * l);
-            }
         }
     }
 
@@ -412,7 +412,7 @@ int tc_max_smem_ok(int device) {
 }
 
 cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int num_sms, int *d_err,
-                               cudaStream_t st, const MeasureArgs *fused, int *tile_cnt) {
+                               cudaStream_t st, const MeasureArgs *fused) {
     TcParams p;
     p.num_m_tiles = a.rows_pad / kBM;
     p.num_n_tiles = L.ncols / L.bn;
@@ -442,16 +442,14 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     p.ldP = o.ldP;
     p.rows_valid = o.rows_valid;
     p.err = d_err;
-    p.tile_cnt = tile_cnt;
     if (fused) {
-        if (!tile_cnt) return cudaErrorInvalidValue;
         p.m = *fused;
     } else {
         memset(&p.m, 0, sizeof(p.m));
     }
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kBarrierBytes;
-    const int total = p.num_m_tiles * p.num_n_tiles;
-    const int grid = total < num_sms ? total : num_sms;
+    const int units = fused ? p.num_m_tiles : p.num_m_tiles * p.num_n_tiles;  // fused blocks own m-tiles
+    const int grid = units < num_sms ? units : num_sms;
     if (grid <= 0) return cudaSuccess;
     const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
     const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
