@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--workload", default="precision", choices=["precision", "plain", "tiny"])
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4"])
     ap.add_argument("--macro", type=int, default=None, help="rows per step (macro-batch)")
+    ap.add_argument("--sites", type=int, default=None,
+                    help="shorter chain of the same shape (for profiling captures; not a benchmark config)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -199,6 +201,10 @@ def run_ours(args, rank, ws, local):
 
     torch.cuda.set_device(local)
     w = gen.WORKLOADS[args.workload]
+    if args.sites:
+        import dataclasses
+
+        w = dataclasses.replace(w, M=args.sites, note=w.note + f" (chain shortened to M={args.sites} for profiling)")
     precision = args.precision or DEFAULTS[args.workload][0]
     macro = args.macro or DEFAULTS[args.workload][1]
     macro = min(macro, w.N)
