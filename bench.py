@@ -144,6 +144,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes (read + write) of one contraction launch at an interior site, from the committed ncu
+# captures (scaled by rows to the bench's launch size); None where no capture of the current kernel exists.
+CONTRACT_TRAFFIC = {
+    ("precision", "bf16x2"): (2.76e9, "profiles/tc_contract_precision_bf16x2.md"),
+    ("plain", "bf16x2"): (1.297e9, "profiles/tc_contract_plain_bf16x2.md"),
+}
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -269,8 +277,10 @@ def run_ours(args, rank, ws, local):
         peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
         achieved = flops_alg / (contract_ms / 1e3) / 1e12
         achieved_issued = flops_iss / (contract_ms / 1e3) / 1e12
+        tr = CONTRACT_TRAFFIC.get((args.workload, precision)) if not args.sites and not args.fused_measure else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": f"{peak_src} bf16_tflops_sustained",
+                "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None,
+                "peak_source": f"{peak_src} bf16_tflops_sustained",
                 "achieved_issued": achieved_issued, "frac_issued": achieved_issued / peak,
                 "kernel": "tc_contract_kernel", "avg_launch_ms": contract_ms / max(1, contract_launches)}
     else:
