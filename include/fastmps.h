@@ -61,6 +61,10 @@ extern "C" {
 #define FASTMPS_BF16X3 2  /* V0 B0 + V1 B0 + V0 B1: B to ~16 bits, v to ~16 bits; 3 products */
 #define FASTMPS_BF16X3L 3 /* V0 B0 + V1 B0 + V2 B0: B in BF16, v to ~24 bits; 3 products */
 #define FASTMPS_BF16X4 4  /* V0 B0 + V1 B0 + V2 B0 + V0 B1: B ~16 bits, v ~24 bits; 4 products */
+/* Experiment: B = e4m3(A * 2^a) with a per-site power of two putting max |Re|,|Im| in [224, 448],
+ * each left row e4m3(v * 2^r) with a per-row power of two likewise; one kind::f8f6f4 product.
+ * Both scales cancel in w / Z.  Resident residency only. */
+#define FASTMPS_FP8X1 5
 
 /* Where site tensors live between uses (Sec. 3.1: I/O overlapped by a double buffer). */
 #define FASTMPS_RESIDENT_HBM 0    /* repacked once at load time, kept in device memory */
@@ -73,7 +77,7 @@ extern "C" {
 #define FASTMPS_C128 1  /* interleaved complex double (re, im) */
 
 typedef struct fastmps_options {
-    int precision;          /* FASTMPS_FP32 | FASTMPS_BF16X2 | _BF16X3 | _BF16X3L | _BF16X4 */
+    int precision;          /* FASTMPS_FP32 | FASTMPS_BF16X2 | _BF16X3 | _BF16X3L | _BF16X4 | _FP8X1 */
     int residency;          /* FASTMPS_RESIDENT_HBM | FASTMPS_HOST_STREAM (BF16 modes only) */
     int64_t max_microbatch; /* rows per contraction launch; 0 = chosen from free memory */
     int autotune;           /* 1: time the candidate tile shapes once per new shape */

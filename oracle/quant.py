@@ -79,7 +79,7 @@ def e4m3_round(x) -> np.ndarray:
 def e4m3_site_scale(A) -> float:
     """Power-of-two scale of an FP8 site store: the largest 2^j with max|Re, Im| * 2^j <= 448."""
     A = np.asarray(A)
-    m = float(max(np.abs(A.real).max(), np.abs(A.imag).max()))
+    m = float(max(np.abs(np.asarray(A.real, np.float32)).max(), np.abs(np.asarray(A.imag, np.float32)).max()))
     if m == 0.0:
         return 1.0
     return float(2.0 ** np.floor(np.log2(E4M3_MAX / m)))

@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <map>
 #include <memory>
@@ -92,7 +93,8 @@ struct DevBuf {
 struct Tensor {
     SiteLayout L;
     // resident operands (device)
-    DevBuf B_hi, B_lo, Bt;
+    DevBuf B_hi, B_lo, Bt, B8;
+    float fp8_scale = 1.f;  // FP8: stored value = e4m3(A * fp8_scale)
     CUtensorMap tmB[2];
     // streamed operand (pinned host, compact BF16 [chi_l][d][chi_r] (re, im), hi block then lo block)
     DevBuf host_compact;
@@ -134,7 +136,9 @@ int cuda_fail(fastmps_handle h, cudaError_t e, const char *what) {
     return fail(h, e == cudaErrorMemoryAllocation ? FASTMPS_ERR_OOM : FASTMPS_ERR_CUDA, m);
 }
 
+// Tensor-core precision modes (BF16 split planes or FP8); FP32 is the SIMT path.
 bool is_bf16(const fastmps_handle h) { return h->opt.precision != FASTMPS_FP32; }
+bool is_fp8(const fastmps_handle h) { return h->opt.precision == FASTMPS_FP8X1; }
 
 // Planes of the split-precision operands and the products accumulated per precision mode.
 struct PrecisionPlan {
@@ -148,6 +152,7 @@ PrecisionPlan plan_of(int precision) {
         case FASTMPS_BF16X3: return {2, 2, 3, {0, 1, 0, 0}, {0, 0, 1, 0}};
         case FASTMPS_BF16X3L: return {3, 1, 3, {0, 1, 2, 0}, {0, 0, 0, 0}};
         case FASTMPS_BF16X4: return {3, 2, 4, {0, 1, 2, 0}, {0, 0, 0, 1}};
+        case FASTMPS_FP8X1: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
         default: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
     }
 }
@@ -157,7 +162,8 @@ SiteLayout make_layout(int precision, int chi_l, int d, int chi_r) {
     L.chi_l = chi_l;
     L.d = d;
     L.chi_r = chi_r;
-    L.K_pad = (int)roundup(2 * (int64_t)chi_l, 64);
+    L.bk = precision == FASTMPS_FP8X1 ? 128 : 64;
+    L.K_pad = (int)roundup(2 * (int64_t)chi_l, L.bk);
     if (precision == FASTMPS_FP32) {
         L.bn = 128;
     } else {
@@ -169,18 +175,28 @@ SiteLayout make_layout(int precision, int chi_l, int d, int chi_r) {
     return L;
 }
 
-bool encode_2d_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
-                    uint32_t box_inner, uint32_t box_outer) {
+bool encode_2d(CUtensorMap *map, CUtensorMapDataType type, int elem_bytes, const void *base, uint64_t inner,
+               uint64_t outer, uint64_t ld_elems, uint32_t box_inner, uint32_t box_outer) {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn) return false;
     cuuint64_t gdim[2] = {inner, outer};
-    cuuint64_t gstride[1] = {ld_elems * 2};
+    cuuint64_t gstride[1] = {ld_elems * (uint64_t)elem_bytes};
     cuuint32_t box[2] = {box_inner, box_outer};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), gdim, gstride, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(map, type, 2, const_cast<void *>(base), gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+bool encode_2d_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                    uint32_t box_inner, uint32_t box_outer) {
+    return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, inner, outer, ld_elems, box_inner, box_outer);
+}
+
+// FP8 operands: rows of ld_elems bytes, 128-byte (128-element) boxes along K
+bool encode_2d_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                  uint32_t box_outer) {
+    return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, base, inner, outer, ld_elems, 128, box_outer);
 }
 
 // Host round-to-nearest-even float -> bfloat16 bits (finite inputs).
@@ -257,7 +273,20 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
                         h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "copy of site tensor");
     const size_t op_elems = (size_t)t.L.ncols * t.L.K_pad;
-    if (is_bf16(h)) {
+    if (is_fp8(h)) {
+        // per-site power-of-two scale that puts the largest |Re|, |Im| in [224, 448]
+        if (!t.B8.ensure(op_elems) || !h->err.ensure(256)) return fail(h, FASTMPS_ERR_OOM, "allocation failed");
+        float amax = 0.f;
+        launch_absmax(h->staging.p, dtype == FASTMPS_C128, nelem, h->err.as<float>(), h->stream);
+        e = cudaMemcpyAsync(&amax, h->err.p, sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "site tensor maximum");
+        t.fp8_scale = amax > 0.f ? (float)std::exp2(std::floor(std::log2(448.0 / (double)amax))) : 1.f;
+        launch_repack_e4m3(h->staging.p, dtype == FASTMPS_C128, t.L, t.fp8_scale, t.B8.as<uint8_t>(), h->stream);
+        if (!encode_2d_u8(&t.tmB[0], t.B8.p, t.L.K_pad, t.L.ncols, t.L.K_pad, t.L.bn))
+            return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+        t.tmB[1] = t.tmB[0];
+    } else if (is_bf16(h)) {
         if (!t.B_hi.ensure(op_elems * 2)) return fail(h, FASTMPS_ERR_OOM, "site operand allocation failed");
         __nv_bfloat16 *lo = nullptr;
         if (plan_of(h->opt.precision).b_planes > 1) {
@@ -372,14 +401,16 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     const int64_t J = (N + N2 - 1) / N2;  // micro-batches per site
 
     // ---- buffers -------------------------------------------------------------
+    const bool fp8 = is_fp8(h);
     const int planes = bf16 ? plan.a_planes : 1;
-    const size_t elem = bf16 ? 2 : 4;
+    const size_t elem = fp8 ? 1 : (bf16 ? 2 : 4);
+    if (fp8) ldV = (int)roundup(ldV, 128);
     for (int x = 0; x < 2; ++x)
         for (int p = 0; p < planes; ++p)
             if (!h->V[x][p].ensure((size_t)N_pad * ldV * elem))
                 return fail(h, FASTMPS_ERR_OOM, "left-operand allocation failed");
     // BF16 modes measure inside the contraction kernel (no second launch, one scratch buffer)
-    const bool fused = bf16 && h->opt.fused_measure;
+    const bool fused = bf16 && !fp8 && h->opt.fused_measure;
     const int nybuf = (J > 1 && !fused) ? 2 : 1;
 
     for (int b = 0; b < nybuf; ++b)
@@ -418,8 +449,10 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     cudaMemsetAsync(h->logp.p, 0, (size_t)N_pad * 8, st);
     __nv_bfloat16 *Vp[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     for (int x = 0; x < 2; ++x)
-        for (int p = 0; p < planes && bf16; ++p) Vp[x][p] = h->V[x][p].as<__nv_bfloat16>();
-    if (bf16)
+        for (int p = 0; p < planes && bf16 && !fp8; ++p) Vp[x][p] = h->V[x][p].as<__nv_bfloat16>();
+    if (fp8)
+        launch_init_left_e4m3(h->V[0][0].as<uint8_t>(), N_pad, ldV, st);
+    else if (bf16)
         launch_init_left_bf16(Vp[0], planes, N_pad, ldV, st);
     else
         launch_init_left_f32(h->V[0][0].as<float>(), N_pad, ldV, st);
@@ -492,10 +525,12 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 ta.prod_a[q] = plan.pa[q];
                 ta.prod_b[q] = plan.pb[q];
             }
+            ta.fp8 = fp8;
             for (int p = 0; p < 3; ++p) {
                 const int src = p < plan.a_planes ? p : 0;
-                if (!encode_2d_bf16(&ta.tmA[p], h->V[cur][src].p, L.K_pad, N_pad, ldV, 64, 128))
-                    return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+                const bool ok = fp8 ? encode_2d_u8(&ta.tmA[p], h->V[cur][src].p, L.K_pad, N_pad, ldV, 128)
+                                    : encode_2d_bf16(&ta.tmA[p], h->V[cur][src].p, L.K_pad, N_pad, ldV, 64, 128);
+                if (!ok) return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
             }
         }
         for (int64_t r0 = 0; r0 < N; r0 += N2, ++g) {
@@ -530,8 +565,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.ld_next = ldV;
             ma.K_next = K_next;
             ma.V32 = bf16 ? nullptr : h->V[nxt][0].as<float>();
-            for (int p = 0; p < 3; ++p) ma.Vp[p] = Vp[nxt][p];
+            for (int p = 0; p < 3; ++p) ma.Vp[p] = fp8 ? nullptr : Vp[nxt][p];
             ma.nplanes = planes;
+            ma.V8 = fp8 ? h->V[nxt][0].as<uint8_t>() : nullptr;
             ma.outcomes = h->O.as<uint8_t>() + (int64_t)k * N_pad + r0;
             ma.logp = h->logp.as<double>();
             ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
@@ -630,7 +666,7 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
     fastmps_options o;
     fastmps_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_BF16X4) {
+    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_FP8X1) {
         g_create_error = "unknown precision";
         return FASTMPS_ERR_INVALID_ARG;
     }
@@ -638,7 +674,7 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
         g_create_error = "unknown residency";
         return FASTMPS_ERR_INVALID_ARG;
     }
-    if (o.residency == FASTMPS_HOST_STREAM && o.precision == FASTMPS_FP32) {
+    if (o.residency == FASTMPS_HOST_STREAM && (o.precision == FASTMPS_FP32 || o.precision == FASTMPS_FP8X1)) {
         g_create_error = "host streaming keeps BF16 tensors: use a BF16 precision";
         return FASTMPS_ERR_UNSUPPORTED;
     }

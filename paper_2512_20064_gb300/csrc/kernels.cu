@@ -1,6 +1,7 @@
 // Site-tensor repacking, FP32 SIMT contraction, measurement (Algorithm 2) and
 // output transposition kernels.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -115,6 +116,31 @@ __global__ void repack_f32_kernel(const void *__restrict__ src, int is_f64, int 
     }
 }
 
+__global__ void repack_e4m3_kernel(const void *__restrict__ src, int is_f64, int chi_l, int d, int chi_r, int Cs,
+                                   int ncols, int K_pad, float scale, uint8_t *__restrict__ B8) {
+    const int64_t total = (int64_t)ncols * K_pad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / K_pad);
+        const int kappa = (int)(i - (int64_t)c * K_pad);
+        const StackedPos q = stacked_pos(c, kappa, chi_l, d, chi_r, Cs);
+        float x = 0.f;
+        if (!q.zero) x = q.sign * load_part(src, is_f64, q.cidx, q.re_part ? 0 : 1);
+        B8[i] = (uint8_t)__nv_cvt_float_to_fp8(x * scale, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+// max over |Re|, |Im| (as float) of n complex entries; non-negative floats order like their bit patterns
+__global__ void absmax_kernel(const void *__restrict__ src, int is_f64, int64_t n2, float *out) {
+    float m = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        const float x = is_f64 ? (float)static_cast<const double *>(src)[i] : static_cast<const float *>(src)[i];
+        m = fmaxf(m, fabsf(x));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int *>(out), __float_as_uint(m));
+}
+
 static int grid_for(int64_t total, int block) {
     int64_t g = (total + block - 1) / block;
     if (g > 152 * 32) g = 152 * 32;
@@ -134,6 +160,18 @@ void launch_expand_bf16(const __nv_bfloat16 *compact, int planes, const SiteLayo
     const int64_t total = (int64_t)L.ncols * L.K_pad;
     expand_bf16_kernel<<<grid_for(total, 256), 256, 0, st>>>(compact, planes, L.chi_l, L.d, L.chi_r, L.Cs, L.ncols,
                                                               L.K_pad, B_hi, B_lo);
+}
+
+void launch_repack_e4m3(const void *src, int is_f64, const SiteLayout &L, float scale, uint8_t *B8,
+                        cudaStream_t st) {
+    const int64_t total = (int64_t)L.ncols * L.K_pad;
+    repack_e4m3_kernel<<<grid_for(total, 256), 256, 0, st>>>(src, is_f64, L.chi_l, L.d, L.chi_r, L.Cs, L.ncols,
+                                                              L.K_pad, scale, B8);
+}
+
+void launch_absmax(const void *src, int is_f64, int64_t n_complex, float *out_dev, cudaStream_t st) {
+    cudaMemsetAsync(out_dev, 0, sizeof(float), st);
+    absmax_kernel<<<grid_for(2 * n_complex, 256), 256, 0, st>>>(src, is_f64, 2 * n_complex, out_dev);
 }
 
 void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *Bt, cudaStream_t st) {
@@ -160,6 +198,16 @@ __global__ void init_left_f32_kernel(float *V, int64_t rows, int ld) {
     const int64_t total = rows * ld;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
         V[i] = (i % ld) == 0 ? 1.f : 0.f;
+}
+
+__global__ void init_left_e4m3_kernel(uint8_t *V8, int64_t rows, int ld) {
+    const int64_t total = rows * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        V8[i] = (uint8_t)__nv_cvt_float_to_fp8((i % ld) == 0 ? 1.f : 0.f, __NV_SATFINITE, __NV_E4M3);
+}
+
+void launch_init_left_e4m3(uint8_t *V8, int64_t rows, int ld, cudaStream_t st) {
+    init_left_e4m3_kernel<<<grid_for(rows * ld, 256), 256, 0, st>>>(V8, rows, ld);
 }
 
 void launch_init_left_bf16(__nv_bfloat16 *const *Vp, int nplanes, int64_t rows, int ld, cudaStream_t st) {

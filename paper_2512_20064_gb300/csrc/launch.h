@@ -18,8 +18,9 @@ struct SiteLayout {
     int bn = 0;        // n-tile width of the contraction kernel
     int Cs = 0;        // columns per outcome block (multiple of bn)
     int ncols = 0;     // d * Cs
-    int K_pad = 0;     // roundup(2 chi_l, 64)
+    int K_pad = 0;     // roundup(2 chi_l, bk)
     int tiles_per_s = 0;
+    int bk = 64;       // operand elements per k-block: one 128-byte swizzle row (64 BF16 or 128 FP8)
 };
 
 // ---- repack of a complex site tensor (device staging copy) -----------------
@@ -31,6 +32,11 @@ void launch_repack_bf16(const void *src, int is_f64, const SiteLayout &L, __nv_b
 // (planes = 1: hi only; planes = 2: hi block followed by lo block).
 void launch_expand_bf16(const __nv_bfloat16 *compact, int planes, const SiteLayout &L, __nv_bfloat16 *B_hi,
                         __nv_bfloat16 *B_lo, cudaStream_t st);
+// FP8 E4M3 operand B[c][kappa] (K-major, ld = K_pad bytes) of value * scale (scale a power of two).
+void launch_repack_e4m3(const void *src, int is_f64, const SiteLayout &L, float scale, uint8_t *B8,
+                        cudaStream_t st);
+// Largest |Re| or |Im| of an interleaved complex tensor (as float), into *out_dev (zeroed first).
+void launch_absmax(const void *src, int is_f64, int64_t n_complex, float *out_dev, cudaStream_t st);
 // FP32 SIMT operand: Bt[kappa][c] (N-major, ld = ncols), float.
 void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *Bt, cudaStream_t st);
 
@@ -38,6 +44,7 @@ void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *
 // Set rows [0, rows) of V to the boundary vector v_0 = [1] (row = [1, 0, ... 0], ld elements).
 void launch_init_left_bf16(__nv_bfloat16 *const *Vp, int nplanes, int64_t rows, int ld, cudaStream_t st);
 void launch_init_left_f32(float *V, int64_t rows, int ld, cudaStream_t st);
+void launch_init_left_e4m3(uint8_t *V8, int64_t rows, int ld, cudaStream_t st);
 
 // ---- contraction kernels ---------------------------------------------------
 struct ContractOut {
@@ -57,6 +64,7 @@ void launch_contract_f32(const float *V, int64_t ldV, int64_t row0, int64_t rows
 // products accumulated are (prod_a[q], prod_b[q]) for q < nprod.
 constexpr int kMaxProducts = 4;
 struct TcArgs {
+    bool fp8 = false;  // E4M3 operands (one plane each), kind::f8f6f4
     CUtensorMap tmA[3];
     CUtensorMap tmB[2];
     int a_planes, b_planes;
@@ -90,6 +98,7 @@ struct MeasureArgs {
     float *V32;               // FP32 path (or nullptr)
     __nv_bfloat16 *Vp[3];     // BF16 paths: planes of successive residuals
     int nplanes;              // 2 or 3
+    uint8_t *V8 = nullptr;    // FP8 path: E4M3 row scaled by a per-row power of two
     uint8_t *outcomes;        // [rows] outcome bytes of this site (site-major buffer slice)
     double *logp;             // [rows] accumulated log-probability
     double *trace;            // nullable: [trace_rows][d] normalised conditionals of this site

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include "common.cuh"
@@ -62,6 +63,21 @@ __device__ __forceinline__ void measure_write_row(const MeasureArgs &a, int lane
             }
         } else {
             for (int i = lane; i < a.K_next; i += 32) dst[i] = i < nreal ? ysrc[i] * scale : 0.f;
+        }
+        return;
+    }
+    if (a.V8) {
+        // E4M3 row: scale the unit-norm row by the power of two that puts its largest entry in
+        // [224, 448] (the scale cancels in w/Z at the next site), then round to nearest even
+        float m = 0.f;
+        for (int i = lane; i < nreal; i += 32) m = fmaxf(m, fabsf(__ldcg(ysrc + i) * scale));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const float s8 = m > 0.f ? exp2f(floorf(log2f(448.f / m))) : 1.f;
+        uint8_t *dst = a.V8 + grow * a.ld_next;
+        for (int i = lane; i < a.K_next; i += 32) {
+            const float x = i < nreal ? __ldcg(ysrc + i) * scale * s8 : 0.f;
+            dst[i] = (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
         }
         return;
     }

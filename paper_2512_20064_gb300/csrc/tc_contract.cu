@@ -45,7 +45,7 @@ namespace fastmps {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kBK = 64;                      // BF16 elements per k-block = one 128-byte swizzle row
+constexpr int kBK = 64;                      // BF16 elements per k-block = one 128-byte swizzle row (FP8: 128)
 constexpr int kThreads = 192;                // TMA + MMA + 4 epilogue warps
 constexpr int kThreadsFused = 320;           // + 4 measurement warps
 constexpr int kRing = 4;                     // finished m-tiles queued for the measurement warps
@@ -127,7 +127,7 @@ __device__ __forceinline__ bool tile_of(const TcParams &p, int i, int &mt, int &
     return tile < p.num_m_tiles * p.num_n_tiles;
 }
 
-template <bool kFused>
+template <bool kFused, bool kFp8>
 __global__ void __launch_bounds__(kFused ? kThreadsFused : kThreads, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
@@ -204,7 +204,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                     }
                     uint8_t *sbase = smem + (size_t)stage * p.stage_bytes;
                     mbar_arrive_expect_tx(&full[stage], p.stage_bytes);
-                    const int x = kb * kBK;
+                    const int x = kb * (kFp8 ? 2 * kBK : kBK);  // 128-byte rows: 64 BF16 or 128 FP8
                     tma_load_2d(sbase, &tmA0, &full[stage], x, y_a);
                     if (p.a_planes > 1) tma_load_2d(sbase + kATileBytes, &tmA1, &full[stage], x, y_a);
                     if (p.a_planes > 2) tma_load_2d(sbase + 2 * kATileBytes, &tmA2, &full[stage], x, y_a);
@@ -263,8 +263,13 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
 #pragma unroll
                         for (int k16 = 0; k16 < kBK / 16; ++k16) {
                             // +32 bytes along K inside the swizzle row = +2 in the address field
-                            tc_mma_bf16(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), p.idesc,
-                                        (kb | q | k16) != 0 ? 1u : 0u);
+                            // (16 BF16 or 32 FP8 elements per MMA)
+                            if (kFp8)
+                                tc_mma_f8(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), p.idesc,
+                                          (kb | q | k16) != 0 ? 1u : 0u);
+                            else
+                                tc_mma_bf16(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), p.idesc,
+                                            (kb | q | k16) != 0 ? 1u : 0u);
                         }
                     }
                     issued = true;
@@ -416,7 +421,7 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     TcParams p;
     p.num_m_tiles = a.rows_pad / kBM;
     p.num_n_tiles = L.ncols / L.bn;
-    p.num_k_blocks = L.K_pad / kBK;
+    p.num_k_blocks = L.K_pad / L.bk;
     p.bn = L.bn;
     p.a_planes = a.a_planes;
     p.b_planes = a.b_planes;
@@ -430,12 +435,13 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
             return cudaErrorInvalidValue;
         p.prod_code |= ((uint32_t)a.prod_a[q] | ((uint32_t)a.prod_b[q] << 2)) << (4 * q);
     }
-    p.b_plane_bytes = (uint32_t)L.bn * kBK * 2;
+    p.b_plane_bytes = (uint32_t)L.bn * 128;  // bn rows of one 128-byte swizzle row
     p.stage_bytes = (uint32_t)a.a_planes * kATileBytes + (uint32_t)a.b_planes * p.b_plane_bytes;
     p.stages = stages_for(p.stage_bytes);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
     p.row0 = (int)a.row0;
-    p.idesc = idesc_bf16_f32(kBM, L.bn);
+    p.idesc = a.fp8 ? idesc_e4m3_f32(kBM, L.bn) : idesc_bf16_f32(kBM, L.bn);
+    if (a.fp8 && (fused || a.a_planes != 1 || a.b_planes != 1 || a.nprod != 1)) return cudaErrorInvalidValue;
     p.Y = o.Y;
     p.ldY = o.ldY;
     p.P = o.P;
@@ -445,7 +451,7 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     if (fused) {
         p.m = *fused;
     } else {
-        memset(&p.m, 0, sizeof(p.m));
+        p.m = MeasureArgs{};
     }
     const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kBarrierBytes;
     const int units = fused ? p.num_m_tiles : p.num_m_tiles * p.num_n_tiles;  // fused blocks own m-tiles
@@ -454,14 +460,21 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
     const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
     cudaError_t e;
-    if (fused) {
-        e = cudaFuncSetAttribute(tc_contract_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (a.fp8) {
+        e = cudaFuncSetAttribute(tc_contract_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit);
         if (e != cudaSuccess) return e;
-        tc_contract_kernel<true><<<grid, kThreadsFused, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
+        tc_contract_kernel<false, true><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
+    } else if (fused) {
+        e = cudaFuncSetAttribute(tc_contract_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit);
+        if (e != cudaSuccess) return e;
+        tc_contract_kernel<true, false><<<grid, kThreadsFused, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
     } else {
-        e = cudaFuncSetAttribute(tc_contract_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+        e = cudaFuncSetAttribute(tc_contract_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSmemLimit);
         if (e != cudaSuccess) return e;
-        tc_contract_kernel<false><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
+        tc_contract_kernel<false, false><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
     }
     return cudaGetLastError();
 }

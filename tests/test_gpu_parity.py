@@ -192,3 +192,19 @@ def test_fused_and_separate_measurement_agree(lib, precision):
     assert np.array_equal(out[False][0], out[True][0])
     assert np.array_equal(out[False][1], out[True][1])
     assert np.array_equal(out[False][2], out[True][2])
+
+
+def test_fp8_experiment_reports_its_error(lib, tiny):
+    """FP8 E4M3 experiment: its conditional-probability error against the oracle on the tensors the FP8
+    store represents is measured and reported (no accuracy target; sanity bound only)."""
+    w, b, ts = tiny
+    with lib.Sampler(precision="fp8x1") as s:
+        s.load_chain(ts)
+        smp, lp, tr = s.sample(b, w.d, 2000, w.sampler_seed, trace_rows=2000)
+    ots = [quant.dequant_e4m3(A) for A in ts]
+    r = oracle.replay(b, ots, w.sampler_seed, np.arange(2000), smp)
+    err = np.abs(np.transpose(tr, (1, 0, 2)) - r["probs"]).max()
+    mism = float((r["own"] != smp).mean())
+    print(f"fp8x1 tiny: max conditional error {err:.3e}, outcome mismatch fraction {mism:.3e}")
+    assert np.isfinite(lp).all() and smp.max() < w.d
+    assert err < 0.1
