@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="precision", choices=["precision", "plain", "tiny"])
-    ap.add_argument("--precision", default=None, choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4"])
+    ap.add_argument("--precision", default=None, choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4", "fp8x1"])
     ap.add_argument("--macro", type=int, default=None, help="rows per step (macro-batch)")
     ap.add_argument("--sites", type=int, default=None,
                     help="shorter chain of the same shape (for profiling captures; not a benchmark config)")

@@ -196,6 +196,39 @@ int fastmps_sample_ex(fastmps_handle h, int M, int d, const int *bond_dims, int6
 int fastmps_sample_noalloc(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N,
                            uint64_t seed, uint32_t job, uint8_t *out_samples, double *out_logprob);
 
+/*
+ * Batched sampling of many independent MPS in one engine call (the paper's
+ * many-sample data parallelism extended to many chains; chains may differ in
+ * M, d, bond dimensions and sample count).
+ *
+ * Each job names a handle `chain` whose sites hold that MPS (loaded with
+ * fastmps_load_site / fastmps_load_pool); every chain must live on the
+ * runner's device and use the runner's precision (a BF16 mode) with resident
+ * tensors.  The runner executes all jobs together: at every "round" each
+ * active job advances one site for one chunk of its rows, and one grouped
+ * tcgen05 contraction launch plus one grouped measurement launch serve all
+ * jobs of the round.  The whole sequence of rounds is captured into a CUDA
+ * graph on the first call with a given job table and replayed by later calls
+ * with the same table (same chains, shapes, rows, seeds and output pointers).
+ * Per job: rows n0 .. n0+N-1, Philox counter word `job`; outputs as in
+ * fastmps_sample_ex (host or device, or NULL).  Statistics of the call are
+ * available from the runner with fastmps_get_stats.
+ */
+typedef struct fastmps_job {
+    fastmps_handle chain;
+    int M;
+    int d;
+    const int *bond_dims; /* M+1 entries, host memory */
+    int64_t n0;
+    int64_t N;
+    uint64_t seed;
+    uint32_t job;
+    uint8_t *out_samples; /* N*M bytes or NULL */
+    double *out_logprob;  /* N doubles or NULL */
+} fastmps_job;
+
+int fastmps_sample_batch(fastmps_handle runner, int count, const fastmps_job *jobs);
+
 /* Statistics of the last fastmps_sample* call. */
 int fastmps_get_stats(fastmps_handle h, fastmps_stats *out);
 

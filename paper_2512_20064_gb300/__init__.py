@@ -22,7 +22,8 @@ from .native import LIB, build
 __all__ = [
     "FastMPSError", "Sampler", "load_library", "build", "PRECISIONS", "RESIDENCIES",
     "fastmps_create", "fastmps_destroy", "fastmps_last_error", "fastmps_load_site", "fastmps_load_pool",
-    "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_sample_noalloc", "fastmps_get_stats",
+    "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_sample_noalloc", "fastmps_sample_batch",
+    "fastmps_get_stats",
     "fastmps_version",
     "fastmps_default_options",
 ]
@@ -45,6 +46,13 @@ class fastmps_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("contract_launches", ctypes.c_int64),
                 ("flops_algorithmic", ctypes.c_double), ("flops_issued", ctypes.c_double),
                 ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+
+class fastmps_job(ctypes.Structure):
+    _fields_ = [("chain", ctypes.c_void_p), ("M", ctypes.c_int), ("d", ctypes.c_int),
+                ("bond_dims", ctypes.POINTER(ctypes.c_int)), ("n0", ctypes.c_int64), ("N", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("job", ctypes.c_uint32), ("out_samples", ctypes.c_void_p),
+                ("out_logprob", ctypes.c_void_p)]
 
 
 class FastMPSError(RuntimeError):
@@ -96,6 +104,8 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
                                                ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                                ctypes.c_void_p]
         lib.fastmps_sample_noalloc.restype = ctypes.c_int
+        lib.fastmps_sample_batch.argtypes = [H, ctypes.c_int, P(fastmps_job)]
+        lib.fastmps_sample_batch.restype = ctypes.c_int
         lib.fastmps_get_stats.argtypes = [H, P(fastmps_stats)]
         lib.fastmps_get_stats.restype = ctypes.c_int
         lib.fastmps_version.argtypes = []
@@ -223,6 +233,28 @@ def fastmps_sample(h, M: int, d: int, bonds, N: int, seed: int, out_samples, out
     _check(lib, h, lib.fastmps_sample(h, M, d, b, N, seed, _ptr(out_samples), _ptr(out_logprob)))
 
 
+def fastmps_sample_batch(runner, jobs) -> None:
+    """Sample many independent MPS together.  ``jobs``: list of dicts with keys chain (a handle),
+    bonds, d, N, seed and optionally n0, job, out_samples, out_logprob (numpy arrays or torch tensors)."""
+    lib = load_library()
+    arr = (fastmps_job * max(1, len(jobs)))()
+    keep = []
+    for i, j in enumerate(jobs):
+        bonds = (ctypes.c_int * len(j["bonds"]))(*[int(x) for x in j["bonds"]])
+        keep.append(bonds)
+        arr[i].chain = j["chain"].value if isinstance(j["chain"], ctypes.c_void_p) else j["chain"]
+        arr[i].M = len(j["bonds"]) - 1
+        arr[i].d = int(j["d"])
+        arr[i].bond_dims = bonds
+        arr[i].n0 = int(j.get("n0", 0))
+        arr[i].N = int(j["N"])
+        arr[i].seed = int(j["seed"])
+        arr[i].job = int(j.get("job", 0))
+        arr[i].out_samples = _ptr(j.get("out_samples"))
+        arr[i].out_logprob = _ptr(j.get("out_logprob"))
+    _check(lib, runner, lib.fastmps_sample_batch(runner, len(jobs), arr))
+
+
 def fastmps_get_stats(h) -> dict:
     lib = load_library()
     s = fastmps_stats()
@@ -234,9 +266,10 @@ class Sampler:
     """A handle of the library: load site tensors once, then sample many times."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", residency: str = "hbm", max_microbatch: int = 0,
-                 stream=None, fused_measure: bool = False):
+                 stream=None, fused_measure: bool = False, autotune: bool = False):
         o = fastmps_default_options()
         o.fused_measure = int(bool(fused_measure))
+        o.autotune = int(bool(autotune))
         o.precision = PRECISIONS[precision]
         o.residency = RESIDENCIES[residency]
         o.max_microbatch = int(max_microbatch)

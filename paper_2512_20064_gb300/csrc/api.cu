@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -19,6 +21,7 @@
 #include <chrono>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -28,6 +31,10 @@
 #include "launch.h"
 
 using namespace fastmps;
+
+namespace fastmps {
+void batch_release(fastmps_handle h);
+}
 
 namespace {
 
@@ -157,7 +164,8 @@ PrecisionPlan plan_of(int precision) {
     }
 }
 
-SiteLayout make_layout(int precision, int chi_l, int d, int chi_r) {
+// bn_override > 0 (tensor-core modes): n-tile width chosen by the autotuner.
+SiteLayout make_layout(int precision, int chi_l, int d, int chi_r, int bn_override = 0) {
     SiteLayout L;
     L.chi_l = chi_l;
     L.d = d;
@@ -168,6 +176,7 @@ SiteLayout make_layout(int precision, int chi_l, int d, int chi_r) {
         L.bn = 128;
     } else {
         L.bn = (int)std::min<int64_t>(256, roundup(2 * (int64_t)chi_r, 32));
+        if (bn_override > 0 && bn_override < L.bn) L.bn = bn_override;
     }
     L.Cs = (int)roundup(2 * (int64_t)chi_r, L.bn);
     L.ncols = d * L.Cs;
@@ -235,12 +244,132 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner: n-tile width of the tensor-core contraction per site shape.
+// Candidates are 256, 128 and 64 columns (those not wider than the padded
+// block 2 chi_r); each is timed on a probe contraction of 8192 rows of the
+// real operand layout, best of three.  Results are cached per process and,
+// when FASTMPS_TUNE_CACHE names a file, in that file as a flat JSON object
+// {"precision:chi_l:d:chi_r": bn, ...}.
+// ---------------------------------------------------------------------------
+std::mutex g_tune_mutex;
+std::map<std::string, int> g_tuned;
+bool g_tune_loaded = false;
+
+std::string tune_key(int precision, int chi_l, int d, int chi_r) {
+    return std::to_string(precision) + ":" + std::to_string(chi_l) + ":" + std::to_string(d) + ":" +
+           std::to_string(chi_r);
+}
+
+void tune_cache_load() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *path = getenv("FASTMPS_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    std::string text;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, n);
+    fclose(f);
+    size_t i = 0;
+    while ((i = text.find('"', i)) != std::string::npos) {
+        const size_t j = text.find('"', i + 1);
+        if (j == std::string::npos) break;
+        const size_t c = text.find(':', j);
+        if (c == std::string::npos) break;
+        g_tuned[text.substr(i + 1, j - i - 1)] = atoi(text.c_str() + c + 1);
+        i = j + 1;
+    }
+}
+
+void tune_cache_store() {
+    const char *path = getenv("FASTMPS_TUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    fputc('{', f);
+    bool first = true;
+    for (auto &kv : g_tuned) {
+        fprintf(f, "%s\"%s\": %d", first ? "" : ", ", kv.first.c_str(), kv.second);
+        first = false;
+    }
+    fputs("}\n", f);
+    fclose(f);
+}
+
+// Times one probe contraction per candidate width on the staged tensor; returns the fastest width.
+int autotune_bn(fastmps_handle h, int chi_l, int d, int chi_r, int is_f64) {
+    const PrecisionPlan plan = plan_of(h->opt.precision);
+    const int widest = (int)std::min<int64_t>(256, roundup(2 * (int64_t)chi_r, 32));
+    const int64_t rows = 8192;
+    int best = widest;
+    float best_ms = 1e30f;
+    for (int bn : {256, 128, 64}) {
+        if (bn > widest) continue;
+        SiteLayout L = make_layout(h->opt.precision, chi_l, d, chi_r, bn);
+        DevBuf B[2], V[3], Y, P, err;
+        bool ok = true;
+        for (int p = 0; p < plan.b_planes; ++p) ok = ok && B[p].ensure((size_t)L.ncols * L.K_pad * 2);
+        for (int p = 0; p < plan.a_planes; ++p) ok = ok && V[p].ensure((size_t)rows * L.K_pad * 2);
+        ok = ok && Y.ensure((size_t)rows * L.ncols * 4) && P.ensure((size_t)rows * (L.ncols / L.bn) * 4) &&
+             err.ensure(sizeof(int));
+        if (!ok) break;
+        launch_repack_bf16(h->staging.p, is_f64, L, B[0].as<__nv_bfloat16>(),
+                           plan.b_planes > 1 ? B[1].as<__nv_bfloat16>() : nullptr, h->stream);
+        for (int p = 0; p < plan.a_planes; ++p) cudaMemsetAsync(V[p].p, 0, V[p].bytes, h->stream);
+        cudaMemsetAsync(err.p, 0, sizeof(int), h->stream);
+        TcArgs ta;
+        ta.a_planes = plan.a_planes;
+        ta.b_planes = plan.b_planes;
+        ta.nprod = plan.nprod;
+        for (int q = 0; q < kMaxProducts; ++q) {
+            ta.prod_a[q] = plan.pa[q];
+            ta.prod_b[q] = plan.pb[q];
+        }
+        for (int p = 0; p < 3; ++p)
+            ok = ok && encode_2d_bf16(&ta.tmA[p], V[p < plan.a_planes ? p : 0].p, L.K_pad, rows, L.K_pad, 64, 128);
+        for (int p = 0; p < 2; ++p)
+            ok = ok && encode_2d_bf16(&ta.tmB[p], B[p < plan.b_planes ? p : 0].p, L.K_pad, L.ncols, L.K_pad, 64, L.bn);
+        if (!ok) break;
+        ta.row0 = 0;
+        ta.rows_pad = (int)rows;
+        ContractOut co{Y.as<float>(), L.ncols, P.as<float>(), L.ncols / L.bn, (int)rows};
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, h->stream);
+            launch_contract_tc(ta, L, co, h->num_sms, err.as<int>(), h->stream);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_min = std::min(ms_min, ms);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            cudaGetLastError();
+            break;
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best = bn;
+        }
+    }
+    return best;
+}
+
 // Copy and repack one tensor into t.
 int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const void *A, int dtype) {
     int rc = check_shape_args(h, chi_l, d, chi_r, A, dtype);
     if (rc) return rc;
     t.L = make_layout(h->opt.precision, chi_l, d, chi_r);
     const int64_t nelem = (int64_t)chi_l * d * chi_r;
+    const bool tune = h->opt.autotune && is_bf16(h) && !is_fp8(h) && h->opt.residency == FASTMPS_RESIDENT_HBM;
     const size_t src_bytes = (size_t)nelem * (dtype == FASTMPS_C128 ? 16 : 8);
     cudaError_t e;
     const bool a_on_device = is_device_ptr(A);
@@ -287,6 +416,22 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
             return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
         t.tmB[1] = t.tmB[0];
     } else if (is_bf16(h)) {
+        if (tune) {
+            std::lock_guard<std::mutex> lock(g_tune_mutex);
+            tune_cache_load();
+            const std::string key = tune_key(h->opt.precision, chi_l, d, chi_r);
+            auto it = g_tuned.find(key);
+            int bn;
+            if (it != g_tuned.end()) {
+                bn = it->second;
+            } else {
+                bn = autotune_bn(h, chi_l, d, chi_r, dtype == FASTMPS_C128);
+                g_tuned[key] = bn;
+                tune_cache_store();
+            }
+            t.L = make_layout(h->opt.precision, chi_l, d, chi_r, bn);
+        }
+        const size_t op_elems = (size_t)t.L.ncols * t.L.K_pad;
         if (!t.B_hi.ensure(op_elems * 2)) return fail(h, FASTMPS_ERR_OOM, "site operand allocation failed");
         __nv_bfloat16 *lo = nullptr;
         if (plan_of(h->opt.precision).b_planes > 1) {
@@ -731,6 +876,7 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
 void fastmps_destroy(fastmps_handle h) {
     if (!h) return;
     cudaSetDevice(h->device);
+    fastmps::batch_release(h);
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
     if (h->measure_stream) cudaStreamSynchronize(h->measure_stream);
@@ -846,6 +992,8 @@ int site_view(fastmps_handle h, int k, SiteView *out) {
 }
 
 int set_error(fastmps_handle h, int code, const char *msg) { return fail(h, code, msg); }
+
+fastmps_stats *handle_stats(fastmps_handle h) { return &h->stats; }
 
 void precision_products(int precision, int *a_planes, int *b_planes, int *nprod, int *pa, int *pb) {
     const PrecisionPlan p = plan_of(precision);

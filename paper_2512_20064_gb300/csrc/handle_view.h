@@ -36,4 +36,9 @@ void precision_products(int precision, int *a_planes, int *b_planes, int *nprod,
 bool encode_bf16_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
                      uint32_t box_outer);
 
+// Statistics of the handle's last call (written by the batch engine).
+fastmps_stats *handle_stats(fastmps_handle h);
+// Releases the batch engine's state of a handle (called by fastmps_destroy).
+void batch_release(fastmps_handle h);
+
 }  // namespace fastmps

@@ -111,3 +111,41 @@ void launch_measure(const MeasureArgs &a, cudaStream_t st);
 void launch_transpose_outcomes(const uint8_t *O, int64_t ldO, int64_t N, int M, uint8_t *out, cudaStream_t st);
 
 }  // namespace fastmps
+
+namespace fastmps {
+
+// ---- grouped (batched) contraction + measurement ---------------------------
+// One segment = one job's chunk of rows at one site.  The grouped kernels run
+// the tiles (and rows) of all segments of a round in one launch; segment
+// tables live in device memory (64-byte aligned for the tensor maps).
+struct TcSegment {  // 64-byte aligned through its CUtensorMap members
+    CUtensorMap tmA[3];
+    CUtensorMap tmB[2];
+    int tile_begin;      // first global tile index of the segment
+    int num_m_tiles, num_n_tiles, num_k_blocks, bn;
+    uint32_t idesc, tx_bytes;
+    int row0;            // first row of the chunk in the job's left-operand buffers (TMA y coordinate)
+    float *Y;
+    int64_t ldY;
+    float *P;
+    int ldP;
+    int rows_valid;
+    int row_block_begin; // first global 32-row block of the segment (grouped measurement)
+};
+
+struct GroupedArgs {
+    const TcSegment *segs;     // device
+    const MeasureArgs *meas;   // device, one per segment
+    int nseg;
+    int total_tiles;
+    int total_row_blocks;
+    int a_planes, b_planes, nprod;
+    int prod_a[kMaxProducts], prod_b[kMaxProducts];
+};
+
+// Sets the kernel's shared-memory attribute (call once before launching, outside stream capture).
+cudaError_t prepare_contract_grouped();
+cudaError_t launch_contract_grouped(const GroupedArgs &g, int num_sms, int *d_err, cudaStream_t st);
+void launch_measure_grouped(const GroupedArgs &g, cudaStream_t st);
+
+}  // namespace fastmps

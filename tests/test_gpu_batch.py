@@ -1,0 +1,88 @@
+"""Batched sampling of independent MPS of different shapes in grouped launches (needs a GB300).
+
+Each job's result from fastmps_sample_batch must equal, bitwise, the same job sampled alone with
+fastmps_sample_ex (the grouped kernels do the same arithmetic per tile and per row); a second call
+replays the captured CUDA graph and must give the same result again.
+"""
+import numpy as np
+import pytest
+
+import gen
+import parity
+from oracle import quant
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [  # (M, d, chi, N, skew)
+    (12, 3, 16, 1000, None),
+    (20, 2, 32, 3000, 1.5),
+    (16, 4, 64, 500, 1.5),
+    (10, 6, 24, 2000, 1.5),
+    (30, 3, 128, 700, 1.5),
+]
+
+
+@pytest.mark.parametrize("precision", ["bf16x2", "bf16x3l"])
+def test_batch_equals_separate_runs(precision):
+    import paper_2512_20064_gb300 as F
+
+    chains, jobs, refs = [], [], []
+    for i, (M, d, chi, N, skew) in enumerate(SHAPES):
+        b, ts, _ = gen.mps_tensors(M, d, chi, base_seed=500 + 37 * i, skew=skew)
+        s = F.Sampler(precision=precision)
+        s.load_chain(ts)
+        chains.append((s, b, ts))
+        refs.append(s.sample(b, d, N, 100 + i, n0=11 * i, job=i))
+        jobs.append({"chain": s.h, "bonds": b, "d": d, "N": N, "seed": 100 + i, "n0": 11 * i, "job": i,
+                     "out_samples": np.empty((N, M), np.uint8), "out_logprob": np.empty(N, np.float64)})
+    with F.Sampler(precision=precision) as runner:
+        for call in range(2):
+            for j in jobs:
+                j["out_samples"][:] = 255
+                j["out_logprob"][:] = np.nan
+            F.fastmps_sample_batch(runner.h, jobs)
+            for j, (ref_s, ref_l) in zip(jobs, refs):
+                assert np.array_equal(j["out_samples"], ref_s), call
+                assert np.array_equal(j["out_logprob"], ref_l), call
+        st = runner.stats()
+        print(precision, {k: st[k] for k in ("ms_total", "ms_contract", "launches", "contract_launches")})
+    # oracle parity of one job of the batch
+    s, b, ts = chains[2]
+    M, d, chi, N, _ = SHAPES[2]
+    rep = parity.check(b, [quant.dequant_bf16(A, 1) for A in ts], 102, np.arange(11 * 2, 11 * 2 + N),
+                       jobs[2]["out_samples"], jobs[2]["out_logprob"], 1e-4, job=2)
+    print(rep)
+    for s, _, _ in chains:
+        s.close()
+
+
+def test_batch_rejects_mismatched_precision():
+    import paper_2512_20064_gb300 as F
+
+    b, ts, _ = gen.mps_tensors(8, 2, 8, base_seed=1)
+    with F.Sampler(precision="fp32") as chain, F.Sampler(precision="bf16x2") as runner:
+        chain.load_chain(ts)
+        with pytest.raises(F.FastMPSError) as e:
+            F.fastmps_sample_batch(runner.h, [{"chain": chain.h, "bonds": b, "d": 2, "N": 10, "seed": 1}])
+        assert e.value.code == -1
+
+
+def test_autotuner_picks_a_width_caches_it_and_stays_correct(tmp_path, monkeypatch):
+    """autotune=1 times the candidate n-tile widths per site shape, records the choice in the JSON cache
+    file, and the sampler stays within tolerance of the oracle with the chosen layout."""
+    import json
+
+    import paper_2512_20064_gb300 as F
+
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("FASTMPS_TUNE_CACHE", str(cache))
+    b, ts, _ = gen.mps_tensors(24, 4, 256, base_seed=9, skew=1.5, dtype=np.complex64)
+    with F.Sampler(precision="bf16x2", autotune=True) as s:
+        s.load_chain(ts)
+        smp, lp, tr = s.sample(b, 4, 4096, 5, trace_rows=64)
+    table = json.loads(cache.read_text())
+    assert "1:256:4:256" in table and table["1:256:4:256"] in (64, 128, 256)
+    print("tuned widths", table)
+    rep = parity.check(b, [quant.dequant_bf16(A, 1) for A in ts], 5, np.arange(64), smp[:64], lp[:64], 1e-4,
+                       dev_trace=tr, trace_rows=64)
+    print(rep)
