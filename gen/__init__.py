@@ -33,6 +33,7 @@ __all__ = [
     "ghz_chain",
     "Workload",
     "WORKLOADS",
+    "batch_jobs",
 ]
 
 
@@ -230,3 +231,20 @@ WORKLOADS = {
     "streaming": Workload("streaming", M=2048, d=3, chi=10_000, N=1 << 16, skew=1.5, pool=16,
                           note="M=2048 d=3 chi=1e4, pool of 16 interior isometries, host-streamed BF16, N=2^16"),
 }
+
+
+def batch_jobs(count: int = 64, seed: int = 2025, rows_cap: int | None = None):
+    """Job parameters of the batching workload: ``count`` independent MPS with M ~ U[64, 2048],
+    d in {2, 3, 4, 6}, chi log-uniform in [32, 2048] (bond profile capped at the chain ends as in
+    ``bond_dims``), N log-uniform in [10^3, 10^6]; ``rows_cap`` bounds the rows drawn per job.
+    Returns a list of dicts (M, d, chi, N, N_full, base_seed, sampler_seed)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jobs = []
+    for j in range(count):
+        M = int(rng.integers(64, 2049))
+        d = int(rng.choice([2, 3, 4, 6]))
+        chi = int(round(math.exp(rng.uniform(math.log(32), math.log(2048)))))
+        N = int(round(math.exp(rng.uniform(math.log(1e3), math.log(1e6)))))
+        jobs.append({"M": M, "d": d, "chi": chi, "N_full": N, "N": min(N, rows_cap) if rows_cap else N,
+                     "base_seed": 10_000 * (j + 1), "sampler_seed": 7 + j})
+    return jobs
