@@ -89,6 +89,12 @@ def barrier(ws):
         dist.barrier()
 
 
+def step_rows(step: int, rank: int, ws: int, rows: int) -> int:
+    """First sample index of a rank's rows at a step: steps and ranks tile [0, steps*ws*rows) without
+    overlap, so N replicas draw disjoint samples of one Philox stream (no collective on the data path)."""
+    return (step * ws + rank) * rows
+
+
 def max_over_ranks(x: float, ws: int) -> float:
     if ws == 1:
         return x
@@ -247,11 +253,11 @@ def run_ours(args, rank, ws, local):
     out_l = torch.empty(macro, dtype=torch.float64, device=device)
 
     def step(i):
-        n0 = ((rank * 1000003 + i) * macro) % max(1, (1 << 40))
-        s.sample(b, w.d, macro, w.sampler_seed, n0=n0, out_samples=out_s, out_logprob=out_l)
+        s.sample(b, w.d, macro, w.sampler_seed, n0=step_rows(i, rank, ws, macro), out_samples=out_s,
+                 out_logprob=out_l)
 
     for i in range(args.warmup):
-        step(-1 - i)
+        step(args.steps + i)
     barrier(ws)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
