@@ -324,6 +324,9 @@ def run_ours(args, rank, ws, local):
 
     if residency == "host_stream":
         line["config"]["residency"] = "host_stream (pinned-host BF16 tensors copied per site, double-buffered)"
+        st = s.stats()
+        line["h2d"] = {"bytes_per_step": int(st["h2d_bytes"]), "copy_ms_per_step": st["ms_h2d"],
+                       "GB_per_s_while_copying": st["h2d_bytes"] / max(1e-9, st["ms_h2d"] / 1e3) / 1e9}
     if rank == 0 and not args.no_e2e and residency == "host_stream":
         # the timed path already streams every site tensor from pinned host memory; time it once more
         # with host output buffers

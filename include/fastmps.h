@@ -100,6 +100,7 @@ typedef struct fastmps_stats {
     double flops_issued;    /* algorithmic x the number of split products (BF16 modes) */
     int64_t h2d_bytes;      /* host->device bytes copied during the call */
     int64_t d2h_bytes;      /* device->host bytes copied during the call */
+    double ms_h2d;          /* device time of the site-tensor copies (host streaming; CUDA events) */
 } fastmps_stats;
 
 /* Fill *opt with the defaults: FP32, resident, automatic micro-batch, no autotune, own stream,

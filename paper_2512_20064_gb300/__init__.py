@@ -45,7 +45,7 @@ class fastmps_stats(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double), ("ms_contract", ctypes.c_double), ("ms_measure", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("contract_launches", ctypes.c_int64),
                 ("flops_algorithmic", ctypes.c_double), ("flops_issued", ctypes.c_double),
-                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64), ("ms_h2d", ctypes.c_double)]
 
 
 class fastmps_job(ctypes.Structure):

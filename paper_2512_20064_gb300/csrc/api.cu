@@ -467,7 +467,7 @@ Tensor *site_tensor_of(fastmps_handle h, int k) {
 
 struct EventTimer {
     fastmps_handle h;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> contract, measure;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> contract, measure, copy;
     size_t used = 0;
     explicit EventTimer(fastmps_handle hh) : h(hh) {}
     cudaEvent_t get() {
@@ -618,9 +618,13 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         const int slot = k & 1;
         cudaError_t ee = cudaStreamWaitEvent(h->copy_stream, h->slot_free[slot], 0);
         if (ee != cudaSuccess) return ee;
+        cudaEvent_t q0 = timer.get(), q1 = timer.get();
+        cudaEventRecord(q0, h->copy_stream);
         ee = cudaMemcpyAsync(h->slot_compact[slot].p, ts[k]->host_compact.p, ts[k]->host_compact.bytes,
                              cudaMemcpyHostToDevice, h->copy_stream);
         if (ee != cudaSuccess) return ee;
+        cudaEventRecord(q1, h->copy_stream);
+        timer.copy.push_back({q0, q1});
         h->stats.h2d_bytes += (int64_t)ts[k]->host_compact.bytes;
         return cudaEventRecord(h->copy_done[slot], h->copy_stream);
     };
@@ -778,6 +782,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     if (e != cudaSuccess) return cuda_fail(h, e, "sampling");
     h->stats.ms_contract = timer.total(timer.contract);
     h->stats.ms_measure = timer.total(timer.measure);
+    h->stats.ms_h2d = timer.total(timer.copy);
     h->stats.ms_total =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     if (herr == kDevNumeric)
