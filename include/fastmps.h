@@ -233,6 +233,17 @@ int fastmps_sample_batch(fastmps_handle runner, int count, const fastmps_job *jo
 /* Statistics of the last fastmps_sample* call. */
 int fastmps_get_stats(fastmps_handle h, fastmps_stats *out);
 
+/*
+ * Self-test of the bounded device-side waits (no fault, no hang): launches one
+ * thread block on `device` that waits on a shared-memory barrier nothing ever
+ * completes, with the same bounded-wait routine the pipelined kernels use,
+ * giving up after limit_ms.  *status receives FASTMPS_ERR_TIMEOUT when the
+ * wait ran out (the expected outcome) and *waited_ms the device time waited.
+ * Returns FASTMPS_OK if the self-test ran.  (Library test hook; the paper
+ * has no counterpart.)
+ */
+int fastmps_selftest_bounded_wait(int device, double limit_ms, int *status, double *waited_ms);
+
 /* Library version string (static storage). */
 const char *fastmps_version(void);
 

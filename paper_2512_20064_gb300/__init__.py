@@ -108,6 +108,9 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
         lib.fastmps_sample_batch.restype = ctypes.c_int
         lib.fastmps_get_stats.argtypes = [H, P(fastmps_stats)]
         lib.fastmps_get_stats.restype = ctypes.c_int
+        lib.fastmps_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.c_double, P(ctypes.c_int),
+                                                      P(ctypes.c_double)]
+        lib.fastmps_selftest_bounded_wait.restype = ctypes.c_int
         lib.fastmps_version.argtypes = []
         lib.fastmps_version.restype = ctypes.c_char_p
         if path is None:
@@ -123,6 +126,16 @@ def _check(lib, h, rc):
     if rc != OK:
         msg = lib.fastmps_last_error(h)
         raise FastMPSError(rc, msg.decode() if msg else "")
+
+
+def fastmps_selftest_bounded_wait(device: int = 0, limit_ms: float = 50.0):
+    """Run the bounded-wait self-test; returns (status code, device milliseconds waited)."""
+    lib = load_library()
+    st = ctypes.c_int()
+    ms = ctypes.c_double()
+    rc = lib.fastmps_selftest_bounded_wait(device, limit_ms, ctypes.byref(st), ctypes.byref(ms))
+    _check(lib, None, rc)
+    return st.value, ms.value
 
 
 def fastmps_version() -> str:

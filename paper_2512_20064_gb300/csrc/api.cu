@@ -66,6 +66,20 @@ struct Error {
     std::string msg;
 };
 
+// Host-side fault injection for tests: FASTMPS_FAIL_ALLOC_AFTER=n makes the
+// (n+1)-th and later device allocations of work buffers report failure.
+long long g_alloc_budget = -2;  // -2: not read yet, -1: no injection
+bool injected_alloc_failure() {
+    if (g_alloc_budget == -2) {
+        const char *v = getenv("FASTMPS_FAIL_ALLOC_AFTER");
+        g_alloc_budget = v ? atoll(v) : -1;
+    }
+    if (g_alloc_budget < 0) return false;
+    if (g_alloc_budget == 0) return true;
+    --g_alloc_budget;
+    return false;
+}
+
 // A device or pinned-host buffer that only grows.
 struct DevBuf {
     void *p = nullptr;
@@ -84,6 +98,7 @@ struct DevBuf {
         if (want <= bytes) return true;
         release();
         if (want == 0) return true;
+        if (!host && injected_alloc_failure()) return false;
         cudaError_t e = host ? cudaHostAlloc(&p, want, cudaHostAllocDefault) : cudaMalloc(&p, want);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -964,6 +979,32 @@ int fastmps_get_stats(fastmps_handle h, fastmps_stats *out) {
 }
 
 const char *fastmps_version(void) { return "fastmps-gb300 0.1 (sm_103a)"; }
+
+int fastmps_selftest_bounded_wait(int device, double limit_ms, int *status, double *waited_ms) {
+    if (!status || !waited_ms || limit_ms <= 0) return FASTMPS_ERR_INVALID_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return FASTMPS_ERR_CUDA;
+    }
+    int *d_status = nullptr;
+    unsigned long long *d_ns = nullptr;
+    if (cudaMalloc(&d_status, sizeof(int)) != cudaSuccess || cudaMalloc(&d_ns, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        if (d_status) cudaFree(d_status);
+        return FASTMPS_ERR_OOM;
+    }
+    launch_bounded_wait_selftest((uint64_t)(limit_ms * 1e6), d_status, d_ns, 0);
+    int st = -1;
+    unsigned long long ns = 0;
+    cudaError_t e = cudaMemcpy(&st, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost);
+    cudaFree(d_status);
+    cudaFree(d_ns);
+    if (e != cudaSuccess) return FASTMPS_ERR_CUDA;
+    *status = st == kDevOk ? FASTMPS_OK : FASTMPS_ERR_TIMEOUT;
+    *waited_ms = (double)ns / 1e6;
+    return FASTMPS_OK;
+}
 
 }  // extern "C"
 

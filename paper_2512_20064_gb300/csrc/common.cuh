@@ -104,8 +104,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Wait until the phase with the given parity has completed.  Gives up after
-// kWaitLimitNs, or as soon as *abort_flag becomes non-zero; returns false then.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+// limit_ns (default kWaitLimitNs), or as soon as *abort_flag becomes
+// non-zero; returns false then.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     uint32_t iter = 0;
@@ -113,7 +115,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
         if (mbar_try_wait(bar, parity)) return true;
         if (((++iter) & 255u) == 0u) {
             if (*abort_flag) return false;
-            if (global_ns() - t0 > kWaitLimitNs) return false;
+            if (global_ns() - t0 > limit_ns) return false;
         }
     }
 }

@@ -373,3 +373,31 @@ void launch_transpose_outcomes(const uint8_t *O, int64_t ldO, int64_t N, int M, 
 }
 
 }  // namespace fastmps
+
+namespace fastmps {
+
+// Self-test of the bounded wait used by the pipelined kernels: waits on an
+// mbarrier that nothing ever arrives on; the wait gives up after limit_ns and
+// the kernel records kDevTimeoutProducer and returns (no fault, no hang).
+__global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, int *status, unsigned long long *waited_ns) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = global_ns();
+        const bool ok = mbar_wait_bounded(&bar, 0u, &abort_flag, limit_ns);
+        *waited_ns = global_ns() - t0;
+        *status = ok ? kDevOk : kDevTimeoutProducer;
+    }
+}
+
+void launch_bounded_wait_selftest(uint64_t limit_ns, int *status, unsigned long long *waited_ns, cudaStream_t st) {
+    bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, status, waited_ns);
+}
+
+}  // namespace fastmps

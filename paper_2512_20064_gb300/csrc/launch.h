@@ -107,6 +107,9 @@ struct MeasureArgs {
 };
 void launch_measure(const MeasureArgs &a, cudaStream_t st);
 
+// Self-test: one bounded mbarrier wait that nothing completes (status, device time waited).
+void launch_bounded_wait_selftest(uint64_t limit_ns, int *status, unsigned long long *waited_ns, cudaStream_t st);
+
 // out[n * M + k] = O[k * ldO + n] for n < N, k < M.
 void launch_transpose_outcomes(const uint8_t *O, int64_t ldO, int64_t N, int M, uint8_t *out, cudaStream_t st);
 
