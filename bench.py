@@ -185,28 +185,48 @@ def make_workload(w, device, gen_device="cuda"):
 
 def cpu_oracle_rate(w, b, tensors_host_fn, cpu_seconds: float, rows_max: int = 512):
     """Time the FP64 oracle (as it stands) on a bounded sample of the workload: R rows through the
-    first K sites (interior sites cost 8 chi^2 d flops each, like the bulk of the chain).
-
-    A short probe sizes the sample so that the timed part takes about ``cpu_seconds``.
-    Returns (cpu_baseline dict, R, K, seconds).
-    """
+    first K sites.  A probe measures the oracle's flop rate on the leading sites; R and K are then
+    chosen from the per-site flop counts so that the timed part takes about ``cpu_seconds``.
+    Returns (cpu_baseline dict, R, K, seconds)."""
     import oracle
 
     cores = oracle.num_threads()
-    # probe: one row per core through the first sites
+    site_flops = [8.0 * b[k] * w.d * b[k + 1] for k in range(w.M)]
     Kp = min(w.M, max(8, (b.index(w.chi) + 2) if w.chi in b else 8))
     tsp = tensors_host_fn(Kp)
     t0 = time.perf_counter()
     oracle.sample_prefix(b, tsp, w.sampler_seed, cores, Kp, nthreads=cores)
     probe = max(1e-3, time.perf_counter() - t0)
-    rate = cores * Kp / probe                      # sample-sites/s, a slight underestimate
-    units = max(cores, int(rate * cpu_seconds))
-    K = int(min(w.M, max(Kp, units // (4 * cores))))
-    R = int(max(cores, min(rows_max, units // K)))
+    flop_rate = cores * sum(site_flops[:Kp]) / probe
+    budget = flop_rate * cpu_seconds                       # flops the timed sample may take
+    R = cores * 4
+    K, acc = 0, 0.0
+    while K < w.M and acc + R * site_flops[K] <= budget:
+        acc += R * site_flops[K]
+        K += 1
+    K = max(K, min(w.M, Kp))
+    if K == w.M:                                           # the whole chain fits: add rows instead
+        R = int(min(rows_max, max(cores, budget // max(1.0, sum(site_flops)))))
     ts = tensors_host_fn(K)
     t0 = time.perf_counter()
     oracle.sample_prefix(b, ts, w.sampler_seed, R, K, nthreads=cores)
     dt = time.perf_counter() - t0
+    if dt < 0.4 * cpu_seconds:
+        # the leading sites under-predict the rate of the bulk: resize once from this measurement
+        scale = cpu_seconds / max(dt, 1e-3)
+        if K < w.M:
+            K2, acc = K, R * sum(site_flops[:K])
+            target = scale * R * sum(site_flops[:K])
+            while K2 < w.M and acc + R * site_flops[K2] <= target:
+                acc += R * site_flops[K2]
+                K2 += 1
+            K = K2
+            ts = tensors_host_fn(K)
+        else:
+            R = int(min(rows_max, max(R, R * scale)))
+        t0 = time.perf_counter()
+        oracle.sample_prefix(b, ts, w.sampler_seed, R, K, nthreads=cores)
+        dt = time.perf_counter() - t0
     return {"value": R * K / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{R} rows x the first {K} of {w.M} sites (FP64 complex oracle, OpenMP over rows), "
                       f"{dt:.1f} s"}, R, K, dt
@@ -422,7 +442,7 @@ def run_reference(args, rank, ws):
             out.append(cache[k])
         return out
 
-    per_step = max(2.0, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    per_step = max(2.0, min(args.cpu_seconds, 90.0 / max(1, args.steps + args.warmup)))
     rates = []
     for i in range(args.warmup + args.steps):
         cb, R, K, dt = cpu_oracle_rate(w, b, host_tensors, per_step)
