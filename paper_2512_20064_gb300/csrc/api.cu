@@ -217,6 +217,11 @@ bool encode_2d_bf16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t
     return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, inner, outer, ld_elems, box_inner, box_outer);
 }
 
+// FP32 contraction scratch [rows][ld] (TMA-store epilogue): 32 x 128 boxes, 128-byte swizzle
+bool encode_2d_f32_scratch(CUtensorMap *map, const void *base, uint64_t cols, uint64_t rows, uint64_t ld_elems) {
+    return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, cols, rows, ld_elems, 32, 128);
+}
+
 // FP8 operands: rows of ld_elems bytes, 128-byte (128-element) boxes along K
 bool encode_2d_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
                   uint32_t box_outer) {
@@ -351,6 +356,7 @@ int autotune_bn(fastmps_handle h, int chi_l, int d, int chi_r, int is_f64) {
         ta.row0 = 0;
         ta.rows_pad = (int)rows;
         ContractOut co{Y.as<float>(), L.ncols, P.as<float>(), L.ncols / L.bn, (int)rows};
+        ta.has_tmY = encode_2d_f32_scratch(&ta.tmY, Y.p, L.ncols, rows, L.ncols);
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
@@ -742,6 +748,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             if (bf16) {
                 ta.row0 = r0;
                 ta.rows_pad = (int)rows_pad;
+                ta.has_tmY = !fused && encode_2d_f32_scratch(&ta.tmY, co.Y, L.ncols, rows, L.ncols);
                 e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st, fused ? &ma : nullptr);
                 if (e != cudaSuccess) return cuda_fail(h, e, "contraction launch");
             } else {

@@ -65,6 +65,8 @@ void launch_contract_f32(const float *V, int64_t ldV, int64_t row0, int64_t rows
 constexpr int kMaxProducts = 4;
 struct TcArgs {
     bool fp8 = false;  // E4M3 operands (one plane each), kind::f8f6f4
+    bool has_tmY = false;  // tmY maps the FP32 scratch (ncols x rows, 32 x 128 boxes): TMA-store epilogue
+    CUtensorMap tmY;
     CUtensorMap tmA[3];
     CUtensorMap tmB[2];
     int a_planes, b_planes;

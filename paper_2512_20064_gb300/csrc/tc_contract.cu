@@ -50,6 +50,7 @@ constexpr int kThreads = 192;                // TMA + MMA + 4 epilogue warps
 constexpr int kThreadsFused = 320;           // + 4 measurement warps
 constexpr int kRing = 4;                     // finished m-tiles queued for the measurement warps
 constexpr int kBarrierBytes = 2048;          // mbarriers, ring, measurement staging
+constexpr uint32_t kYStageBytes = 16384;     // one 128 x 32 FP32 chunk of the scratch tile (two buffers)
 constexpr uint32_t kTmemCols = 512;          // 2 accumulators x 256 columns
 constexpr uint32_t kAccStride = 256;
 constexpr uint32_t kATileBytes = kBM * kBK * 2;  // 16 KB
@@ -60,6 +61,7 @@ struct TcParams {
     int num_m_tiles, num_n_tiles, num_k_blocks, bn;
     int a_planes, b_planes, stages, nprod;
     uint32_t prod_code;  // product q uses A plane (code >> 4q) & 3 and B plane (code >> (4q+2)) & 3
+    int tma_store;       // epilogue stages 128 x 32 chunks in shared memory and stores them with TMA
     uint32_t stage_bytes, b_plane_bytes;
     int row0;
     uint32_t idesc;
@@ -131,12 +133,14 @@ template <bool kFused, bool kFp8>
 __global__ void __launch_bounds__(kFused ? kThreadsFused : kThreads, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
-                   const __grid_constant__ CUtensorMap tmB1, const TcParams p) {
+                   const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmY,
+                   const TcParams p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
 
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)p.stages * p.stage_bytes);
+    uint8_t *ystage = smem + (size_t)p.stages * p.stage_bytes;  // 2 x 16 KB when p.tma_store
+    uint64_t *full = reinterpret_cast<uint64_t *>(ystage + (p.tma_store ? 2 * kYStageBytes : 0u));
     uint64_t *empty = full + p.stages;
     uint64_t *tfull = empty + p.stages;
     uint64_t *tempty = tfull + 2;
@@ -296,11 +300,13 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
         int ring = 0;               // (fused) next ring slot and its phase, tracked by thread 64
         uint32_t ring_phase = 0;
         int mt, nt;
+        int chunk = 0;  // chunks staged so far (alternating staging buffers)
+        const bool group_sync = kFused || p.tma_store;
         for (int i = 0; tile_of<kFused>(p, i, mt, nt); ++i, ++lt) {
             const int buf = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
             const bool ready = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag);
-            if (kFused ? named_bar_any(1, 128, !ready) : !ready) {
+            if (group_sync ? named_bar_any(1, 128, !ready) : !ready) {
                 record_error(p.err, abort_flag, kDevTimeoutEpilogue);
                 break;
             }
@@ -319,7 +325,26 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                     const float v = __uint_as_float(r[j]);
                     ss = fmaf(v, v, ss);
                 }
-                if (valid) {
+                if (!kFused && p.tma_store) {
+                    // stage the 128 x 32 chunk (row = TMEM lane) with the 128-byte swizzle the tensor
+                    // map expects, then one thread stores it with TMA
+                    uint8_t *sb = ystage + (uint32_t)(chunk & 1) * kYStageBytes;
+                    if (threadIdx.x == 64) bulk_wait_read_1();  // the store two chunks back has read sb
+                    named_bar_sync(1, 128);
+                    const int rl = quad * 32 + lane;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        *reinterpret_cast<float4 *>(sb + rl * 128 + ((j ^ (rl & 7)) * 16)) =
+                            make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                        __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                    fence_proxy_async_smem();
+                    named_bar_sync(1, 128);
+                    if (threadIdx.x == 64) {
+                        tma_store_2d(&tmY, sb, nt * p.bn + ch * 32, mt * kBM);
+                        bulk_commit();
+                    }
+                    ++chunk;
+                } else if (valid) {
                     float4 *dst = reinterpret_cast<float4 *>(yrow + ch * 32);
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
@@ -349,6 +374,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                 __syncwarp();
             }
         }
+        if (!kFused && p.tma_store && threadIdx.x == 64) bulk_wait_all();  // scratch stores complete
         if (kFused && threadIdx.x == 64) {
             // no more m-tiles from this block: stop the measurement warps
             if (mbar_wait_bounded(&mempty[ring], ring_phase ^ 1u, abort_flag)) {
@@ -401,8 +427,8 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     }
 }
 
-int stages_for(uint32_t stage_bytes) {
-    const int fixed = 1024 /* alignment */ + kBarrierBytes;
+int stages_for(uint32_t stage_bytes, uint32_t extra = 0) {
+    const int fixed = 1024 /* alignment */ + kBarrierBytes + (int)extra;
     int s = (kSmemLimit - fixed) / (int)stage_bytes;
     if (s > kMaxStages) s = kMaxStages;
     return s;
@@ -439,6 +465,15 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     p.stage_bytes = (uint32_t)a.a_planes * kATileBytes + (uint32_t)a.b_planes * p.b_plane_bytes;
     p.stages = stages_for(p.stage_bytes);
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
+    // TMA-store epilogue when the staging buffers fit beside at least two pipeline stages
+    p.tma_store = 0;
+    if (a.has_tmY && !fused) {
+        const int st2 = stages_for(p.stage_bytes, 2 * kYStageBytes);
+        if (st2 >= 2) {
+            p.stages = st2;
+            p.tma_store = 1;
+        }
+    }
     p.row0 = (int)a.row0;
     p.idesc = a.fp8 ? idesc_e4m3_f32(kBM, L.bn) : idesc_bf16_f32(kBM, L.bn);
     if (a.fp8 && (fused || a.a_planes != 1 || a.b_planes != 1 || a.nprod != 1)) return cudaErrorInvalidValue;
@@ -453,28 +488,29 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     } else {
         p.m = MeasureArgs{};
     }
-    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kBarrierBytes;
+    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kBarrierBytes + (p.tma_store ? 2 * kYStageBytes : 0);
     const int units = fused ? p.num_m_tiles : p.num_m_tiles * p.num_n_tiles;  // fused blocks own m-tiles
     const int grid = units < num_sms ? units : num_sms;
     if (grid <= 0) return cudaSuccess;
     const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
     const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
+    const CUtensorMap &ty = a.has_tmY ? a.tmY : a.tmA[0];  // unused when p.tma_store == 0
     cudaError_t e;
     if (a.fp8) {
         e = cudaFuncSetAttribute(tc_contract_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemLimit);
         if (e != cudaSuccess) return e;
-        tc_contract_kernel<false, true><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
+        tc_contract_kernel<false, true><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
     } else if (fused) {
         e = cudaFuncSetAttribute(tc_contract_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemLimit);
         if (e != cudaSuccess) return e;
-        tc_contract_kernel<true, false><<<grid, kThreadsFused, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
+        tc_contract_kernel<true, false><<<grid, kThreadsFused, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
     } else {
         e = cudaFuncSetAttribute(tc_contract_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemLimit);
         if (e != cudaSuccess) return e;
-        tc_contract_kernel<false, false><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, p);
+        tc_contract_kernel<false, false><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
     }
     return cudaGetLastError();
 }
