@@ -156,7 +156,10 @@ class ClockSampler:
 
 # DRAM bytes (read + write) of one contraction launch at an interior site, from the committed ncu
 # captures (scaled by rows to the bench's launch size); None where no capture of the current kernel exists.
-CONTRACT_TRAFFIC = {}
+CONTRACT_TRAFFIC = {
+    ("precision", "bf16x2"): (2.89e9, "profiles/tc_contract_precision_bf16x2.md"),
+    ("plain", "bf16x2"): (1.287e9, "profiles/tc_contract_plain_bf16x2.md"),
+}
 
 
 def measured_peaks():
