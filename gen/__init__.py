@@ -34,6 +34,9 @@ __all__ = [
     "Workload",
     "WORKLOADS",
     "batch_jobs",
+    "vidal_form",
+    "gbs_amplitudes",
+    "decaying_vidal_chain",
 ]
 
 
@@ -248,3 +251,78 @@ def batch_jobs(count: int = 64, seed: int = 2025, rows_cap: int | None = None):
         jobs.append({"M": M, "d": d, "chi": chi, "N_full": N, "N": min(N, rows_cap) if rows_cap else N,
                      "base_seed": 10_000 * (j + 1), "sampler_seed": 7 + j})
     return jobs
+
+
+# ---------------------------------------------------------------------------
+# Vidal form and GBS displacement amplitudes (inputs of the Vidal-form and
+# displaced sampling entry points)
+# ---------------------------------------------------------------------------
+
+def vidal_form(bonds, tensors):
+    """Vidal form ``(Gammas, Lambdas)`` of the state held by right-canonical ``tensors``.
+
+    A left-to-right sweep of singular value decompositions (FP64): with
+    ``R_0 = [[1]]``, the matrix ``(R_k A_k)`` reshaped to ``(chi_l d) x chi_r`` is
+    ``U S V^dagger``; ``U`` is the left-canonical tensor ``L_k``, ``Lambda_k = S``
+    (Schmidt coefficients of the cut right of site k, descending) and
+    ``R_{k+1} = S V^dagger``.  Then ``Gamma_k = Lambda_{k-1}^{-1} L_k`` (``Lambda_{-1} = [1]``),
+    so that ``Gamma_0 Lambda_0 Gamma_1 Lambda_1 ... Gamma_{M-1} Lambda_{M-1}`` is the
+    same state and ``Gamma_k Lambda_k`` is right-canonical.  The bond dimensions
+    are kept (the profile ``bond_dims`` never exceeds the rank of a cut).
+    """
+    M = len(bonds) - 1
+    R = np.ones((1, 1), np.complex128)
+    lam_prev = np.ones(1)
+    gammas, lams = [], []
+    for k in range(M):
+        A = np.asarray(tensors[k], np.complex128)
+        cl, d, cr = A.shape
+        T = np.einsum("xa,asb->xsb", R, A).reshape(cl * d, cr)
+        U, S, Vh = np.linalg.svd(T, full_matrices=False)
+        if S.shape[0] != cr:
+            raise ValueError(f"cut {k + 1} has rank {S.shape[0]} < bond {cr}")
+        # fix the gauge of each singular pair: largest entry of V^dagger's row real positive
+        j = np.argmax(np.abs(Vh), axis=1)
+        ph = Vh[np.arange(cr), j] / np.abs(Vh[np.arange(cr), j])
+        U = U * ph[None, :]
+        Vh = Vh * ph.conj()[:, None]
+        L = U.reshape(cl, d, cr)
+        gammas.append(L / lam_prev[:, None, None])
+        lams.append(S.copy())
+        R = S[:, None] * Vh
+        lam_prev = S
+    return gammas, lams
+
+
+def gbs_amplitudes(M: int, N: int, sigma: float = 0.3, seed: int = 4242, dtype=np.complex64) -> np.ndarray:
+    """Random displacement amplitudes ``mu[k, n]`` for M sites and N samples.
+
+    Stand-in for the classical noise of a lossy Gaussian boson sampler: the
+    thermal part of the state is a random displacement with a complex Gaussian
+    amplitude per mode and sample.  Here each amplitude is drawn i.i.d.,
+    ``Re mu, Im mu ~ N(0, sigma^2 / 2)`` (so ``E|mu|^2 = sigma^2``).
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mu = (rng.standard_normal((M, N)) + 1j * rng.standard_normal((M, N))) * (sigma / math.sqrt(2.0))
+    return mu.astype(dtype)
+
+
+def decaying_vidal_chain(M: int, d: int, chi: int, decay: float = 0.35, seed: int = 99):
+    """A Vidal-form chain whose Schmidt spectra decay like ``exp(-decay * j)``, bond by bond.
+
+    Built from a right-canonical chain by re-weighting: ``Lambda_k`` is the
+    normalised spectrum ``exp(-decay * j)`` (descending), and ``Gamma_k`` is chosen
+    so that ``Gamma_k Lambda_k`` equals a Haar-random right-canonical tensor: the
+    chain is then a valid MPS (``Gamma_k Lambda_k`` right-canonical), the Lambda
+    weights of Algorithm 2 are non-trivial and truncation of the smallest
+    values removes a controlled weight.  Returns ``(bonds, Gammas, Lambdas)``.
+    """
+    bonds, As, _ = mps_tensors(M, d, chi, base_seed=seed, skew=1.5)
+    gammas, lams = [], []
+    for k in range(M):
+        cr = bonds[k + 1]
+        lam = np.exp(-decay * np.arange(cr))
+        lam /= np.linalg.norm(lam)
+        gammas.append(As[k] / lam[None, None, :])
+        lams.append(lam)
+    return bonds, gammas, lams

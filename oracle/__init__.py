@@ -14,6 +14,12 @@ Functions
 ``replay``        teacher-forced replay: follow given outcomes and report the
                   oracle's conditionals, its own draw and the CDF margin.
 ``born_logprob``  ``log |A_0[s_0] ... A_{M-1}[s_{M-1}]|^2`` (plain definition).
+``displacement``  the Zassenhaus displacement matrix of Sec. 3.4.1 (GBS).
+
+``sample`` and ``replay`` also take ``lams`` (Vidal form: the tensors are
+Gamma_k and ``lams[k]`` the Schmidt coefficients right of site k) and ``mu``
+(GBS: one complex displacement amplitude per sample and site, ``mu[k, i]``
+for row i of the call).
 ``brute_force``   ``|psi(s)|^2`` for all ``d^M`` configurations.
 ``philox``/``uniform``  the counter-based generator.
 """
@@ -71,8 +77,10 @@ def _bind(lib):
         ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p), ctypes.c_int, ctypes.c_uint64,
         ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-        ctypes.c_int]
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
     lib.orc_sample_segment.restype = ctypes.c_int
+    lib.orc_displacement.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
+    lib.orc_displacement.restype = None
     lib.orc_born_logprob.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p),
                                      ctypes.c_void_p]
     lib.orc_born_logprob.restype = ctypes.c_double
@@ -142,6 +150,44 @@ def _vp(a):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
+class _Extras:
+    """Optional Vidal weights and GBS displacement amplitudes of one call."""
+
+    def __init__(self, M, bonds, lams=None, mu=None, rows=None, N=None):
+        self.lam_ptrs = None
+        self._lams = None
+        if lams is not None:
+            if len(lams) != M:
+                raise ValueError("lams must have M entries")
+            self._lams = [np.ascontiguousarray(np.asarray(l, dtype=np.float64)) for l in lams]
+            for k, l in enumerate(self._lams):
+                if l.shape != (bonds[k + 1],):
+                    raise ValueError(f"lams[{k}] must have bond[{k + 1}] = {bonds[k + 1]} entries")
+            self.lam_ptrs = (ctypes.c_void_p * M)(*[l.ctypes.data for l in self._lams])
+        self.mu = None
+        if mu is not None:
+            mu = np.asarray(mu)
+            if mu.ndim != 2 or mu.shape[0] != M:
+                raise ValueError("mu must have shape (M, N)")
+            self.mu = np.ascontiguousarray(mu.astype(np.complex128))
+
+    def mu_rows(self, i, j):
+        """(pointer, ld) of the amplitudes of call rows i .. j-1."""
+        if self.mu is None:
+            return None, 0
+        sub = np.ascontiguousarray(self.mu[:, i:j])
+        self._keep = sub
+        return ctypes.c_void_p(sub.ctypes.data), sub.shape[1]
+
+
+def displacement(mu: complex, n: int, lib=None) -> np.ndarray:
+    """``exp(-|mu|^2/2) exp(mu a^dag) exp(-mu^* a)`` in the n-level truncation (complex128, n x n)."""
+    lib = _load(lib)
+    out = np.zeros(2 * n * n, np.float64)
+    lib.orc_displacement(float(np.real(mu)), float(np.imag(mu)), int(n), _vp(out))
+    return (out[0::2] + 1j * out[1::2]).reshape(n, n)
+
+
 def philox(ctr, key, lib=None) -> np.ndarray:
     lib = _load(lib)
     c = (ctypes.c_uint32 * 4)(*[int(x) & 0xFFFFFFFF for x in ctr])
@@ -160,16 +206,23 @@ def num_threads(lib=None) -> int:
 
 
 def sample(bonds, tensors, seed: int, N: int, n0: int = 0, job: int = 0, site_index=None,
-           want_probs: bool = False, nthreads: int = 0, lib=None):
-    """Sample rows ``n0..n0+N-1``.  Returns ``(samples[N,M] u8, logprob[N] f64[, probs[N,M,d]])``."""
+           want_probs: bool = False, nthreads: int = 0, lib=None, lams=None, mu=None):
+    """Sample rows ``n0..n0+N-1``.  Returns ``(samples[N,M] u8, logprob[N] f64[, probs[N,M,d]])``.
+
+    ``lams``: Vidal form (``tensors`` are Gamma_k).  ``mu``: GBS displacement
+    amplitudes, shape (M, N), column i for row ``n0 + i``."""
     lib = _load(lib)
     ch = _Chain(bonds, tensors, site_index)
     M, d = ch.M, ch.d
+    ex = _Extras(M, bonds, lams, mu)
+    if ex.mu is not None and ex.mu.shape[1] != N:
+        raise ValueError("mu must have N columns")
+    mp, ld = ex.mu_rows(0, N)
     smp = np.zeros((N, M), np.uint8)
     lp = np.zeros(N, np.float64)
     pr = np.zeros((N, M, d), np.float64) if want_probs else None
     rc = lib.orc_sample_segment(M, d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, job, n0, N, 0, M, None, 0,
-                                _vp(smp), _vp(lp), _vp(pr), None, None, None, nthreads)
+                                _vp(smp), _vp(lp), _vp(pr), None, None, None, nthreads, ex.lam_ptrs, mp, ld)
     if rc != 0:
         raise RuntimeError(f"orc_sample_segment failed ({rc})")
     return (smp, lp, pr) if want_probs else (smp, lp)
@@ -186,14 +239,14 @@ def sample_prefix(bonds, tensors, seed: int, N: int, K: int, n0: int = 0, nthrea
     smp = np.zeros((N, M), np.uint8)
     lp = np.zeros(N, np.float64)
     rc = lib.orc_sample_segment(M, ch.d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, 0, n0, N, 0, K, _vp(vstate),
-                                ldv, _vp(smp), _vp(lp), None, None, None, None, nthreads)
+                                ldv, _vp(smp), _vp(lp), None, None, None, None, nthreads, None, None, 0)
     if rc != 0:
         raise RuntimeError(f"orc_sample_segment failed ({rc})")
     return smp[:, :K], lp
 
 
 def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=None, nthreads: int = 0, lib=None,
-           site_chunk: int | None = None):
+           site_chunk: int | None = None, lams=None, mu=None):
     """Teacher-forced replay of rows ``rows`` (sample indices) along ``forced[R, M]``.
 
     Returns a dict with ``probs[R,M,d]`` (the oracle's conditionals along the
@@ -205,10 +258,12 @@ def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=Non
     ``tensors`` may be a list, or a callable ``tensors(k) -> A_k``; with
     ``site_chunk`` the chain is replayed ``site_chunk`` sites at a time,
     carrying the left vectors between segments, so only one chunk of tensors
-    needs to be in host memory.
+    needs to be in host memory.  ``lams`` / ``mu`` as in :func:`sample`; for
+    ``mu`` column r belongs to replayed row ``rows[r]`` (shape (M, R)).
     """
     lib = _load(lib)
     M = len(bonds) - 1
+    ex = _Extras(M, bonds, lams, mu)
     rows = np.asarray(rows, dtype=np.int64)
     forced = np.ascontiguousarray(np.asarray(forced, dtype=np.uint8))
     R = rows.shape[0]
@@ -239,9 +294,11 @@ def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=Non
             j = i + 1
             while j < R and rows[j] == rows[j - 1] + 1:
                 j += 1
+            mp, ld = ex.mu_rows(i, j)
             rc = lib.orc_sample_segment(M, ch.d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, job, int(rows[i]), j - i,
                                         k0, k1, _vp(vstate[i:j]), ldv, None, _vp(lp[i:j]), _vp(probs[i:j]),
-                                        _vp(forced[i:j]), _vp(own[i:j]), _vp(margin[i:j]), nthreads)
+                                        _vp(forced[i:j]), _vp(own[i:j]), _vp(margin[i:j]), nthreads, ex.lam_ptrs,
+                                        mp, ld)
             if rc != 0:
                 raise RuntimeError(f"orc_sample_segment (replay) failed ({rc})")
             i = j

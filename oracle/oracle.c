@@ -27,10 +27,23 @@
  * Site tensors are passed as interleaved complex doubles, A_k[a][s][b]
  * row-major with shape (chi_l = bond[k], d, chi_r = bond[k+1]).
  *
+ * Two extensions of the same loop (both optional per call):
+ *  - Vidal form (Sec. 2.2: the workflow contracts Gamma_i into the left
+ *    environment; Algorithm 2 takes the coefficient vector Lambda): the site
+ *    tensors are Gamma_k and lam[k] holds Lambda_k, the Schmidt coefficients
+ *    on the bond to the right of site k.  Then temp_s = v Gamma_k[:, s, :],
+ *    w_s = sum_b |temp_s[b]|^2 Lambda_k[b]^2, and the carried left vector is
+ *    v_{k+1}[b] = temp_{s*}[b] Lambda_k[b] / sqrt(w_{s*}).
+ *  - GBS random displacement (Sec. 3.4.1): sample n at site k carries a complex
+ *    amplitude mu[n, k]; the physical index of the contracted tensor is mixed
+ *    by the displacement matrix D(mu) of Eq. (zass),
+ *    temp_s <- sum_t D[s, t] temp_t, before the probabilities are formed.
+ *
  * Parity pins for every function are in tests/test_oracle_pins.py: brute
  * force over all d^M configurations, closed forms, special cases (product
  * state, GHZ chain), Philox known-answer vectors and marginal statistics.
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -148,6 +161,106 @@ static int orc_draw(const double *w, int d, double u, double *Z_out, double *mar
 }
 
 /* ------------------------------------------------------------------------ */
+/* GBS displacement (Sec. 3.4.1, Eq. (zass))                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Z = X Y for n x n complex matrices (row-major). */
+static void orc_cmatmul(int n, const double complex *X, const double complex *Y, double complex *Z)
+{
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            double complex acc = 0.0;
+            for (int q = 0; q < n; ++q) acc += X[i * n + q] * Y[q * n + j];
+            Z[i * n + j] = acc;
+        }
+}
+
+/* E = exp(X) for a nilpotent X (X^n = 0): the power series ends after n terms,
+ * E = sum_{m=0}^{n-1} X^m / m!. */
+static void orc_exp_nilpotent(int n, const double complex *X, double complex *E, double complex *term,
+                              double complex *tmp)
+{
+    for (int i = 0; i < n * n; ++i) {
+        E[i] = (i / n == i % n) ? 1.0 : 0.0;
+        term[i] = E[i];
+    }
+    for (int m = 1; m < n; ++m) {
+        orc_cmatmul(n, term, X, tmp);
+        for (int i = 0; i < n * n; ++i) {
+            term[i] = tmp[i] / (double)m;
+            E[i] += term[i];
+        }
+    }
+}
+
+/*
+ * D = exp(-|mu|^2 / 2) exp(mu a^dag) exp(-mu^* a), the paper's Zassenhaus
+ * approximation of the displacement operator exp(mu a^dag - mu^* a), in the
+ * n-level truncation: a|j> = sqrt(j)|j-1>, so a[j-1][j] = sqrt(j) and
+ * a^dag = a^T.  Both exponents are nilpotent there (strictly triangular), so
+ * the two exponentials are finite sums: exp(mu a^dag) is lower and
+ * exp(-mu^* a) upper triangular.  D is written row-major as n*n interleaved
+ * complex doubles (D[2*(s*n+t)], D[2*(s*n+t)+1]).
+ */
+void orc_displacement(double mu_re, double mu_im, int n, double *D)
+{
+    const double complex mu = mu_re + I * mu_im;
+    const size_t nn = (size_t)n * n;
+    double complex *buf = (double complex *)calloc(7 * nn, sizeof(double complex));
+    if (!buf) {
+        for (size_t i = 0; i < 2 * nn; ++i) D[i] = NAN;
+        return;
+    }
+    double complex *X = buf, *Y = buf + nn, *EX = buf + 2 * nn, *EY = buf + 3 * nn, *term = buf + 4 * nn,
+                   *tmp = buf + 5 * nn, *P = buf + 6 * nn;
+    for (int j = 1; j < n; ++j) {
+        const double r = sqrt((double)j);
+        X[j * n + (j - 1)] = mu * r;          /* mu a^dag:  (a^dag)[j][j-1] = sqrt(j) */
+        Y[(j - 1) * n + j] = -conj(mu) * r;   /* -mu^* a:   a[j-1][j] = sqrt(j)       */
+    }
+    orc_exp_nilpotent(n, X, EX, term, tmp);
+    orc_exp_nilpotent(n, Y, EY, term, tmp);
+    orc_cmatmul(n, EX, EY, P);
+    const double g = exp(-0.5 * (mu_re * mu_re + mu_im * mu_im));
+    for (size_t i = 0; i < nn; ++i) {
+        D[2 * i] = g * creal(P[i]);
+        D[2 * i + 1] = g * cimag(P[i]);
+    }
+    free(buf);
+}
+
+/* y_s <- sum_t D[s][t] y_t for every column b (D: d x d interleaved complex). */
+static void orc_displace(double *y, int d, int chi_r, const double *D, double *tmp)
+{
+    for (int s = 0; s < d; ++s)
+        for (int b = 0; b < chi_r; ++b) {
+            double re = 0.0, im = 0.0;
+            for (int t = 0; t < d; ++t) {
+                const double dr = D[2 * (s * d + t)], di = D[2 * (s * d + t) + 1];
+                const double yr = y[2 * (t * chi_r + b)], yi = y[2 * (t * chi_r + b) + 1];
+                re += dr * yr - di * yi;
+                im += dr * yi + di * yr;
+            }
+            tmp[2 * (s * chi_r + b)] = re;
+            tmp[2 * (s * chi_r + b) + 1] = im;
+        }
+    memcpy(y, tmp, sizeof(double) * 2 * (size_t)d * chi_r);
+}
+
+/* Vidal form: w_s = sum_b |temp_s[b]|^2 Lambda[b]^2 */
+static void orc_block_norms_lambda(const double *y, int d, int chi_r, const double *lam, double *w)
+{
+    for (int s = 0; s < d; ++s) {
+        double acc = 0.0;
+        for (int b = 0; b < chi_r; ++b) {
+            const double re = y[2 * (s * chi_r + b)], im = y[2 * (s * chi_r + b) + 1];
+            acc += (re * re + im * im) * lam[b] * lam[b];
+        }
+        w[s] = acc;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sampling                                                                  */
 /* ------------------------------------------------------------------------ */
 
@@ -175,15 +288,20 @@ static int max_bond(int M, const int *bond)
  * own uniform would have picked and margin (nullable, [N][M]) the distance
  * min_s |u - C_s/Z| of that uniform to the nearest interior CDF boundary.
  * A holds one pointer per site, interleaved complex doubles or, with
- * a_is_f32, complex floats.  Returns 0, -1 on bad arguments, -2 on
- * allocation failure.
+ * a_is_f32, complex floats.  lam (nullable): Vidal form, lam[k] = Lambda_k
+ * (bond[k+1] doubles) and A[k] = Gamma_k.  mu (nullable): GBS displacement,
+ * interleaved complex doubles, amplitude of row i at site k at
+ * mu[2*(k*ldmu + i)] (re) and +1 (im).  Returns 0, -1 on bad arguments, -2
+ * on allocation failure.
  */
 int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int a_is_f32, uint64_t seed,
                        uint32_t job, int64_t n0, int64_t N, int k0, int k1, double *vstate, int ldv,
                        uint8_t *samples, double *logprob, double *probs, const uint8_t *forced,
-                       uint8_t *own_draw, double *margin, int nthreads)
+                       uint8_t *own_draw, double *margin, int nthreads, const double *const *lam,
+                       const double *mu, int64_t ldmu)
 {
     if (M < 1 || d < 2 || d > 255 || N < 0 || !bond || !A) return -1;
+    if (mu && ldmu < N) return -1;
     if (k0 < 0 || k1 > M || k0 > k1) return -1;
     if (!vstate && k0 != 0) return -1;
     if (bond[0] != 1 || bond[M] != 1) return -1;
@@ -198,7 +316,9 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
         double *v = (double *)malloc(sizeof(double) * 2 * (size_t)chi);
         double *y = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi);
         double *w = (double *)malloc(sizeof(double) * (size_t)d);
-        if (!v || !y || !w) bad = 1;
+        double *Dm = (double *)malloc(sizeof(double) * 2 * (size_t)d * d);
+        double *ytmp = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi);
+        if (!v || !y || !w || !Dm || !ytmp) bad = 1;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
@@ -224,7 +344,15 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
                     continue;
                 }
                 orc_contract(v, cl, d, cr, A[k], a_is_f32, y);
-                orc_block_norms(y, d, cr, w);
+                if (mu) {
+                    const double *m = mu + 2 * ((size_t)k * ldmu + (size_t)i);
+                    orc_displacement(m[0], m[1], d, Dm);
+                    orc_displace(y, d, cr, Dm, ytmp);
+                }
+                if (lam)
+                    orc_block_norms_lambda(y, d, cr, lam[k], w);
+                else
+                    orc_block_norms(y, d, cr, w);
                 const double u = orc_uniform(seed, n, (uint32_t)k, job);
                 double Z, mg;
                 const int mine = orc_draw(w, d, u, &Z, &mg);
@@ -246,6 +374,11 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
                     v[2 * b] = y[2 * (s * cr + b)] * inv;
                     v[2 * b + 1] = y[2 * (s * cr + b) + 1] * inv;
                 }
+                if (lam)
+                    for (int b = 0; b < cr; ++b) {
+                        v[2 * b] *= lam[k][b];
+                        v[2 * b + 1] *= lam[k][b];
+                    }
             }
             if (logprob) logprob[i] += lp;
             if (vstate)
@@ -254,6 +387,8 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
         free(v);
         free(y);
         free(w);
+        free(Dm);
+        free(ytmp);
     }
     return bad ? -2 : 0;
 }
@@ -266,7 +401,7 @@ int orc_sample(int M, int d, const int *bond, const double *const *A, uint64_t s
     if (logprob)
         for (int64_t i = 0; i < N; ++i) logprob[i] = 0.0;
     return orc_sample_segment(M, d, bond, (const void *const *)A, 0, seed, job, n0, N, 0, M, NULL, 0, samples,
-                              logprob, probs, forced, own_draw, margin, nthreads);
+                              logprob, probs, forced, own_draw, margin, nthreads, NULL, NULL, 0);
 }
 
 /* ------------------------------------------------------------------------ */

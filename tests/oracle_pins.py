@@ -26,6 +26,17 @@ What pins what
   closed-form log |A_0[s_0] ... A_{M-1}[s_{M-1}]|^2 (per-sample rescaling).
 * ``pin_marginals``       -- single-site and nearest-pair marginals of 10^5 samples
   within 5 sigma of brute force (in test_oracle_pins only; slow for mutants).
+* ``pin_displacement_closed_form`` -- the Zassenhaus matrix of Sec. 3.4.1 equals the
+  matrix elements of the displacement operator, <m|D(mu)|n> = sqrt(n!/m!) mu^(m-n)
+  exp(-|mu|^2/2) L_n^(m-n)(|mu|^2) (generalised Laguerre polynomial, scipy), and the
+  top-left block of a dense FP64 expm (scipy) of the generator in a 60-level space.
+* ``pin_displaced_conditionals_vs_brute`` -- with per-sample displacements, each
+  conditional equals the marginal of the full state vector displaced (closed-form
+  matrices, numpy) on sites 0..k, right of k summed out.
+* ``pin_vidal_conditionals_vs_brute`` / ``pin_vidal_logprob`` -- Vidal-form sampling
+  (Gamma, Lambda) reproduces the brute-force Born law of the state
+  Gamma_0 Lambda_0 Gamma_1 Lambda_1 ... for a converted chain and for a chain with
+  decaying Schmidt spectra.
 """
 from __future__ import annotations
 
@@ -191,8 +202,114 @@ def pin_long_chain(lib=None, N=8, seed=3):
     return True, ""
 
 
+def displacement_closed_form(mu: complex, n: int) -> np.ndarray:
+    """<m|D(mu)|j> for m, j < n from the Laguerre closed form (Cahill-Glauber)."""
+    from scipy.special import eval_genlaguerre
+
+    x = abs(mu) ** 2
+    g = math.exp(-x / 2)
+    D = np.zeros((n, n), np.complex128)
+    for m in range(n):
+        for j in range(n):
+            if m >= j:
+                D[m, j] = math.sqrt(math.factorial(j) / math.factorial(m)) * mu ** (m - j) * g * \
+                    eval_genlaguerre(j, m - j, x)
+            else:
+                D[m, j] = math.sqrt(math.factorial(m) / math.factorial(j)) * (-np.conj(mu)) ** (j - m) * g * \
+                    eval_genlaguerre(m, j - m, x)
+    return D
+
+
+def pin_displacement_closed_form(lib=None):
+    import scipy.linalg
+
+    big = 60
+    a = np.diag(np.sqrt(np.arange(1, big)), 1)
+    rng = np.random.Generator(np.random.PCG64(17))
+    for n in (2, 3, 4, 6, 10):
+        for _ in range(6):
+            mu = complex(*(rng.standard_normal(2) * 0.6))
+            got = oracle.displacement(mu, n, lib=lib)
+            want = displacement_closed_form(mu, n)
+            err = np.abs(got - want).max()
+            if not err < 1e-12:
+                return False, f"n={n} mu={mu:.3f}: |D - closed form| = {err:.3e}"
+            E = scipy.linalg.expm(mu * a.T - np.conj(mu) * a)[:n, :n]
+            err = np.abs(got - E).max()
+            if not err < 1e-10:
+                return False, f"n={n} mu={mu:.3f}: |D - expm block| = {err:.3e}"
+    return True, ""
+
+
+def _state_vector(bonds, tensors):
+    """psi[s_0, ..., s_{M-1}] by plain tensor contraction (numpy)."""
+    psi = np.ones((1, 1), np.complex128)          # [configs so far, bond]
+    for A in tensors:
+        cl, d, cr = A.shape
+        psi = np.einsum("xa,asb->xsb", psi, A).reshape(-1, cr)
+    return psi.reshape(-1)
+
+
+def pin_displaced_conditionals_vs_brute(lib=None, rows=12, seed=77):
+    M, d, chi = 7, 3, 9
+    b, ts, _ = gen.mps_tensors(M, d, chi, base_seed=31, skew=1.5)
+    psi = _state_vector(b, ts).reshape((d,) * M)
+    mu = gen.gbs_amplitudes(M, rows, sigma=0.5, seed=5).astype(np.complex128)
+    smp, lp, pr = oracle.sample(b, ts, seed, rows, want_probs=True, lib=lib, mu=mu)
+    worst = 0.0
+    for i in range(rows):
+        Ds = [displacement_closed_form(complex(mu[k, i]), d) for k in range(M)]
+        phi = psi
+        for k in range(M):
+            phi = np.moveaxis(np.tensordot(Ds[k], phi, axes=([1], [k])), 0, k)   # displace site k
+            pre = tuple(int(x) for x in smp[i, :k])
+            block = np.abs(phi[pre]) ** 2                                       # axes: s_k, s_{k+1}, ...
+            marg = block.reshape(d, -1).sum(axis=1)
+            worst = max(worst, float(np.abs(pr[i, k] - marg / marg.sum()).max()))
+    if not worst < 1e-12:
+        return False, f"max |p_oracle - p_brute| = {worst:.3e}"
+    return True, ""
+
+
+def _vidal_cases():
+    b, ts = _tiny()
+    g1, l1 = gen.vidal_form(b, ts)
+    b2, g2, l2 = gen.decaying_vidal_chain(8, 3, 12, decay=0.4, seed=3)
+    return [(b, ts, g1, l1), (b2, [g2[k] * l2[k][None, None, :] for k in range(8)], g2, l2)]
+
+
+def pin_vidal_conditionals_vs_brute(lib=None, rows=25, seed=8):
+    worst = 0.0
+    for b, state, G, L in _vidal_cases():
+        bf = oracle.brute_force(b, state)           # Born law of Gamma_0 Lambda_0 Gamma_1 Lambda_1 ...
+        smp, lp, pr = oracle.sample(b, G, seed, rows, want_probs=True, lib=lib, lams=L)
+        M = len(b) - 1
+        for i in range(rows):
+            for k in range(M):
+                pre = list(smp[i, :k])
+                den = _prefix_marg(bf, pre)
+                for s in range(bf.shape[0]):
+                    worst = max(worst, abs(pr[i, k, s] - _prefix_marg(bf, pre + [s]) / den))
+    if not worst < 1e-11:
+        return False, f"max |p_vidal - p_brute| = {worst:.3e}"
+    return True, ""
+
+
+def pin_vidal_logprob(lib=None, rows=100, seed=21):
+    for b, state, G, L in _vidal_cases():
+        bf = oracle.brute_force(b, state)
+        smp, lp = oracle.sample(b, G, seed, rows, lib=lib, lams=L)
+        for i in range(rows):
+            p = bf[tuple(smp[i])]
+            if not (p > 0 and abs(lp[i] - math.log(p)) < 1e-10):
+                return False, f"row {i}: logp {lp[i]!r} vs log |psi|^2 {math.log(p) if p > 0 else p!r}"
+    return True, ""
+
+
 FAST_PINS = [pin_philox_kat, pin_uniform_packing, pin_brute_force_normalised, pin_conditionals_vs_brute,
-             pin_logprob_vs_brute, pin_product_state, pin_ghz, pin_scale_invariance, pin_long_chain]
+             pin_logprob_vs_brute, pin_product_state, pin_ghz, pin_scale_invariance, pin_long_chain,
+             pin_displacement_closed_form, pin_displaced_conditionals_vs_brute, pin_vidal_conditionals_vs_brute,
+             pin_vidal_logprob]
 
 
 def marginals_5sigma(samples: np.ndarray, bf: np.ndarray):

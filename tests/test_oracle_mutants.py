@@ -27,6 +27,19 @@ MUTANTS = {
     "uniform_drops_second_word": ("| (uint64_t)(x[1] >> 11);", "| 0u;"),
     "select_previous_block": ("v[2 * b] = y[2 * (s * cr + b)] * inv;",
                               "v[2 * b] = y[2 * (((s + 1) % d) * cr + b)] * inv;"),
+    "vidal_lambda_not_squared": ("acc += (re * re + im * im) * lam[b] * lam[b];",
+                                 "acc += (re * re + im * im) * lam[b];"),
+    "vidal_carry_without_lambda": ("v[2 * b] *= lam[k][b];\n                        v[2 * b + 1] *= lam[k][b];",
+                                   "v[2 * b] *= 1.0;\n                        v[2 * b + 1] *= 1.0;"),
+    "displacement_transposed": ("const double dr = D[2 * (s * d + t)], di = D[2 * (s * d + t) + 1];",
+                                "const double dr = D[2 * (t * d + s)], di = D[2 * (t * d + s) + 1];"),
+    "zassenhaus_lowering_sign": ("Y[(j - 1) * n + j] = -conj(mu) * r;", "Y[(j - 1) * n + j] = conj(mu) * r;"),
+    "zassenhaus_missing_conjugate": ("Y[(j - 1) * n + j] = -conj(mu) * r;", "Y[(j - 1) * n + j] = -mu * r;"),
+    "zassenhaus_factor_order": ("orc_cmatmul(n, EX, EY, P);", "orc_cmatmul(n, EY, EX, P);"),
+    "zassenhaus_no_gaussian_factor": ("const double g = exp(-0.5 * (mu_re * mu_re + mu_im * mu_im));",
+                                      "const double g = 1.0;"),
+    "displacement_on_wrong_site": ("const double *m = mu + 2 * ((size_t)k * ldmu + (size_t)i);",
+                                   "const double *m = mu + 2 * ((size_t)((k + 1) % M) * ldmu + (size_t)i);"),
     "born_conjugates_one_factor": ("im += r[2 * a] * e[1] + r[2 * a + 1] * e[0];\n            }\n            t[2 * b] = re;",
                                    "im += -r[2 * a] * e[1] + r[2 * a + 1] * e[0];\n            }\n            t[2 * b] = re;"),
 }
