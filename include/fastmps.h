@@ -230,6 +230,57 @@ typedef struct fastmps_job {
 
 int fastmps_sample_batch(fastmps_handle runner, int count, const fastmps_job *jobs);
 
+/*
+ * Vidal-form sites (Sec. 2.2: the workflow contracts the tensors Gamma_i into
+ * the left environment; Algorithm 2 weights the squared amplitudes by the
+ * coefficient vector Lambda).  Gamma: [chi_l][d][chi_r] interleaved complex of
+ * type dtype; Lambda: chi_r real numbers of the same precision (double for
+ * FASTMPS_C128, float for FASTMPS_C64) -- the Schmidt coefficients of the bond
+ * right of site k ([1] for the last site).  Both host or device memory, owned
+ * by the caller and only read during the call.  The site is stored as
+ * A_k[a, s, b] = Gamma_k[a, s, b] * Lambda_k[b] (scaled on the device before the
+ * repack), which is right-canonical for a Vidal canonical form, and is then
+ * sampled exactly like a site loaded with fastmps_load_site: the outcome
+ * probabilities are sum_b |(v Gamma_k[s])_b|^2 Lambda_k[b]^2 / Z and the carried
+ * left vector is (v Gamma_k[s*]) Lambda_k / sqrt(w_{s*}).  Same requirements and
+ * error codes as fastmps_load_site / fastmps_load_pool, plus
+ * FASTMPS_ERR_INVALID_ARG for a NULL Lambda.
+ */
+int fastmps_load_site_vidal(fastmps_handle h, int k, int chi_l, int d, int chi_r, const void *Gamma,
+                            const void *Lambda, int dtype);
+int fastmps_load_pool_vidal(fastmps_handle h, int j, int chi_l, int d, int chi_r, const void *Gamma,
+                            const void *Lambda, int dtype);
+
+/*
+ * Gaussian-boson-sampling random displacement (Sec. 3.4.1).
+ *
+ * fastmps_displacement: for N complex amplitudes mu[n] (interleaved complex64,
+ * host or device) write the d x d matrices
+ *     D(mu) = exp(-|mu|^2 / 2) exp(mu a^+) exp(-mu^* a)
+ * (the paper's Zassenhaus approximation of the displacement operator
+ * exp(mu a^+ - mu^* a) in the d-level truncation, a|j> = sqrt(j)|j-1>) as
+ * interleaved complex64 with the batch index last: D[2*((s*d + t)*N + n)] (re)
+ * and +1 (im) for row s, column t, sample n (host or device memory, d*d*N
+ * complex entries).  Device arrays must be 8-byte aligned.  The product of the
+ * two triangular factors is computed entry by entry from their closed forms in
+ * FP32; it equals the matrix elements <s|D(mu)|t> of the untruncated operator.
+ * Runs on the handle's stream and returns when D is complete.
+ *
+ * fastmps_sample_displaced: as fastmps_sample_ex, with the physical index of
+ * every sample's contracted tensor mixed by its own displacement before the
+ * measurement: y_s <- sum_t D(mu)[s, t] y_t with mu = mu[2*(k*ld_mu + i)] (re),
+ * +1 (im) for call row i (sample n0+i) at site k (interleaved complex64, host or
+ * device, ld_mu >= N).  The probabilities, draw, log-probability and next left
+ * vector are then those of fastmps_sample_ex on the mixed blocks.  Needs
+ * 2 <= d <= 16 and the FP32 or a BF16 precision (FASTMPS_ERR_SHAPE /
+ * FASTMPS_ERR_UNSUPPORTED otherwise); the measurement runs as a separate kernel
+ * (fused_measure is ignored).
+ */
+int fastmps_displacement(fastmps_handle h, int64_t N, int d, const float *mu, float *D);
+int fastmps_sample_displaced(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N,
+                             uint64_t seed, uint32_t job, const float *mu, int64_t ld_mu, uint8_t *out_samples,
+                             double *out_logprob, int64_t trace_rows, double *trace_probs);
+
 /* Statistics of the last fastmps_sample* call. */
 int fastmps_get_stats(fastmps_handle h, fastmps_stats *out);
 

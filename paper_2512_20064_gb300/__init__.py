@@ -23,7 +23,8 @@ __all__ = [
     "FastMPSError", "Sampler", "load_library", "build", "PRECISIONS", "RESIDENCIES",
     "fastmps_create", "fastmps_destroy", "fastmps_last_error", "fastmps_load_site", "fastmps_load_pool",
     "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_sample_noalloc", "fastmps_sample_batch",
-    "fastmps_get_stats",
+    "fastmps_get_stats", "fastmps_load_site_vidal", "fastmps_load_pool_vidal", "fastmps_displacement",
+    "fastmps_sample_displaced",
     "fastmps_version",
     "fastmps_default_options",
 ]
@@ -91,6 +92,18 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
             f = getattr(lib, name)
             f.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
             f.restype = ctypes.c_int
+        for name in ("fastmps_load_site_vidal", "fastmps_load_pool_vidal"):
+            f = getattr(lib, name)
+            f.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_int]
+            f.restype = ctypes.c_int
+        lib.fastmps_displacement.argtypes = [H, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        lib.fastmps_displacement.restype = ctypes.c_int
+        lib.fastmps_sample_displaced.argtypes = [H, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
+                                                 ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                                 ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                                 ctypes.c_void_p]
+        lib.fastmps_sample_displaced.restype = ctypes.c_int
         lib.fastmps_map_site.argtypes = [H, ctypes.c_int, ctypes.c_int]
         lib.fastmps_map_site.restype = ctypes.c_int
         lib.fastmps_sample.argtypes = [H, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
@@ -197,6 +210,70 @@ def fastmps_load_pool(h, j: int, A) -> None:
     lib = load_library()
     ptr, keep, dt, (cl, d, cr) = _tensor_arg(A)
     _check(lib, h, lib.fastmps_load_pool(h, j, cl, d, cr, ptr, dt))
+    del keep
+
+
+def _lambda_arg(Lam, dt):
+    """(pointer, keep-alive) of Schmidt coefficients in the real type matching tensor dtype code dt."""
+    if hasattr(Lam, "data_ptr") and hasattr(Lam, "is_cuda"):
+        import torch
+
+        Lam = Lam.to(torch.float64 if dt == C128 else torch.float32).contiguous()
+        return Lam.data_ptr(), Lam
+    Lam = np.ascontiguousarray(np.asarray(Lam, dtype=np.float64 if dt == C128 else np.float32))
+    return Lam.ctypes.data, Lam
+
+
+def fastmps_load_site_vidal(h, k: int, Gamma, Lam) -> None:
+    """Load a Vidal-form site: Gamma (chi_l, d, chi_r) complex and Lambda (chi_r,) real."""
+    lib = load_library()
+    ptr, keep, dt, (cl, d, cr) = _tensor_arg(Gamma)
+    lp, lkeep = _lambda_arg(Lam, dt)
+    _check(lib, h, lib.fastmps_load_site_vidal(h, k, cl, d, cr, ptr, lp, dt))
+    del keep, lkeep
+
+
+def fastmps_load_pool_vidal(h, j: int, Gamma, Lam) -> None:
+    lib = load_library()
+    ptr, keep, dt, (cl, d, cr) = _tensor_arg(Gamma)
+    lp, lkeep = _lambda_arg(Lam, dt)
+    _check(lib, h, lib.fastmps_load_pool_vidal(h, j, cl, d, cr, ptr, lp, dt))
+    del keep, lkeep
+
+
+def _complex64_arg(x):
+    """(pointer, keep-alive, shape) of a complex64 array: numpy (converted if needed) or torch (host or CUDA)."""
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        import torch
+
+        x = x.to(torch.complex64).contiguous()
+        return x.data_ptr(), x, tuple(x.shape)
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.complex64))
+    return x.ctypes.data, x, x.shape
+
+
+def fastmps_displacement(h, mu, d: int, out=None):
+    """Zassenhaus displacement matrices of N amplitudes: returns D[s, t, n] (complex64, batch last)."""
+    lib = load_library()
+    mp, keep, shape = _complex64_arg(mu)
+    N = int(np.prod(shape))
+    if out is None:
+        out = np.empty((d, d, N), np.complex64)
+    _check(lib, h, lib.fastmps_displacement(h, N, d, mp, _ptr(out)))
+    del keep
+    return out
+
+
+def fastmps_sample_displaced(h, M: int, d: int, bonds, n0: int, N: int, seed: int, job: int, mu, out_samples,
+                             out_logprob, trace_rows: int = 0, trace_probs=None) -> None:
+    """``mu``: complex64 amplitudes of shape (M, N) (numpy, or a torch tensor on the host or the device)."""
+    lib = load_library()
+    mp, keep, shape = _complex64_arg(mu)
+    if len(shape) != 2 or shape[0] != M:
+        raise ValueError("mu must have shape (M, ld) with ld >= N")
+    b = (ctypes.c_int * (M + 1))(*[int(x) for x in bonds])
+    _check(lib, h, lib.fastmps_sample_displaced(h, M, d, b, n0, N, seed, job, mp, shape[1], _ptr(out_samples),
+                                                _ptr(out_logprob), trace_rows, _ptr(trace_probs)))
     del keep
 
 
@@ -323,12 +400,25 @@ class Sampler:
             for k, j in enumerate(site_index):
                 fastmps_map_site(self.h, k, j)
 
+    def load_site_vidal(self, k: int, Gamma, Lam):
+        fastmps_load_site_vidal(self.h, k, Gamma, Lam)
+
+    def load_chain_vidal(self, gammas, lams):
+        """Load a whole chain given in Vidal form (Gamma_k, Lambda_k)."""
+        for k, (G, L) in enumerate(zip(gammas, lams)):
+            fastmps_load_site_vidal(self.h, k, G, L)
+
+    def displacement(self, mu, d: int):
+        """Batched Zassenhaus displacement matrices, D[s, t, n]."""
+        return fastmps_displacement(self.h, mu, d)
+
     def sample(self, bonds, d: int, N: int, seed: int, n0: int = 0, job: int = 0, out_samples=None,
-               out_logprob=None, trace_rows: int = 0):
+               out_logprob=None, trace_rows: int = 0, mu=None):
         """Draw rows ``n0 .. n0+N-1``.  Returns ``(samples[N, M] uint8, logprob[N] float64[, trace[M, R, d]])``.
 
         Outputs are numpy arrays unless ``out_samples`` / ``out_logprob`` are given
-        (numpy arrays or torch tensors, host or CUDA).
+        (numpy arrays or torch tensors, host or CUDA).  ``mu`` (shape (M, N), complex):
+        per-sample GBS displacement amplitudes (Sec. 3.4.1).
         """
         M = len(bonds) - 1
         if out_samples is None:
@@ -336,7 +426,11 @@ class Sampler:
         if out_logprob is None:
             out_logprob = np.empty(N, np.float64)
         trace = np.empty((M, trace_rows, d), np.float64) if trace_rows > 0 else None
-        fastmps_sample_ex(self.h, M, d, bonds, n0, N, seed, job, out_samples, out_logprob, trace_rows, trace)
+        if mu is not None:
+            fastmps_sample_displaced(self.h, M, d, bonds, n0, N, seed, job, mu, out_samples, out_logprob,
+                                     trace_rows, trace)
+        else:
+            fastmps_sample_ex(self.h, M, d, bonds, n0, N, seed, job, out_samples, out_logprob, trace_rows, trace)
         if trace is not None:
             return out_samples, out_logprob, trace
         return out_samples, out_logprob

@@ -139,6 +139,9 @@ struct fastmps_ctx {
     DevBuf V[2][3];  // [ping-pong][plane]  BF16 planes, or V[x][0] FP32
     DevBuf Y[2], P[2], logp, O, Dout, Dlogp, trace, err;
     DevBuf staging;  // device copy of a tensor being loaded
+    DevBuf lam;      // device copy of the Schmidt coefficients of a Vidal-form site being loaded
+    DevBuf mu;       // device copy of host displacement amplitudes (displaced sampling)
+    DevBuf disp_io;  // device staging of fastmps_displacement's host inputs / outputs
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
     cudaEvent_t contract_done[2] = {nullptr, nullptr}, measure_done[2] = {nullptr, nullptr};
@@ -384,10 +387,13 @@ int autotune_bn(fastmps_handle h, int chi_l, int d, int chi_r, int is_f64) {
     return best;
 }
 
-// Copy and repack one tensor into t.
-int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const void *A, int dtype) {
+// Copy and repack one tensor into t.  lam (nullable, host or device, chi_r entries of the
+// tensor's real type): Vidal form, the stored tensor is A[a][s][b] * lam[b].
+int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const void *A, int dtype,
+                const void *lam = nullptr) {
     int rc = check_shape_args(h, chi_l, d, chi_r, A, dtype);
     if (rc) return rc;
+    const size_t lam_bytes = (size_t)chi_r * (dtype == FASTMPS_C128 ? 8 : 4);
     t.L = make_layout(h->opt.precision, chi_l, d, chi_r);
     const int64_t nelem = (int64_t)chi_l * d * chi_r;
     const bool tune = h->opt.autotune && is_bf16(h) && !is_fp8(h) && h->opt.residency == FASTMPS_RESIDENT_HBM;
@@ -401,6 +407,13 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
         if (e != cudaSuccess) return cuda_fail(h, e, "copy of site tensor");
         A = host_copy.data();
     }
+    std::vector<uint8_t> lam_host;
+    if (lam && h->opt.residency == FASTMPS_HOST_STREAM) {
+        lam_host.resize(lam_bytes);
+        e = cudaMemcpy(lam_host.data(), lam, lam_bytes, is_device_ptr(lam) ? cudaMemcpyDeviceToHost
+                                                                             : cudaMemcpyHostToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of Schmidt coefficients");
+    }
     if (h->opt.residency == FASTMPS_HOST_STREAM) {
         // compact BF16 copy in pinned host memory
         t.planes = plan_of(h->opt.precision).b_planes;
@@ -410,8 +423,15 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
         uint16_t *dst = t.host_compact.as<uint16_t>();
         const int64_t n2 = nelem * 2;
         for (int64_t i = 0; i < n2; ++i) {
-            float x = dtype == FASTMPS_C128 ? (float)static_cast<const double *>(A)[i]
-                                            : static_cast<const float *>(A)[i];
+            float x;
+            if (dtype == FASTMPS_C128) {
+                double v = static_cast<const double *>(A)[i];
+                if (lam) v *= reinterpret_cast<const double *>(lam_host.data())[(i >> 1) % chi_r];
+                x = (float)v;
+            } else {
+                x = static_cast<const float *>(A)[i];
+                if (lam) x *= reinterpret_cast<const float *>(lam_host.data())[(i >> 1) % chi_r];
+            }
             uint16_t hb = host_bf16_bits(x);
             dst[i] = hb;
             if (t.planes > 1) dst[n2 + i] = host_bf16_bits(x - host_bf16_float(hb));
@@ -422,6 +442,13 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
     e = cudaMemcpyAsync(h->staging.p, A, src_bytes, a_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                         h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "copy of site tensor");
+    if (lam) {
+        if (!h->lam.ensure(lam_bytes)) return fail(h, FASTMPS_ERR_OOM, "allocation failed");
+        e = cudaMemcpyAsync(h->lam.p, lam, lam_bytes, is_device_ptr(lam) ? cudaMemcpyDeviceToDevice
+                                                                          : cudaMemcpyHostToDevice, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of Schmidt coefficients");
+        launch_scale_columns(h->staging.p, dtype == FASTMPS_C128, nelem, chi_r, h->lam.p, h->stream);
+    }
     const size_t op_elems = (size_t)t.L.ncols * t.L.K_pad;
     if (is_fp8(h)) {
         // per-site power-of-two scale that puts the largest |Re|, |Im| in [224, 448]
@@ -510,8 +537,10 @@ struct EventTimer {
     }
 };
 
+// mu_dev (nullable, device): displaced sampling, amplitude of call row i at site k at mu_dev[k * ld_mu + i].
 int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int64_t N, uint64_t seed, uint32_t job,
-               uint8_t *out_samples, double *out_logprob, int64_t trace_rows, double *trace_probs) {
+               uint8_t *out_samples, double *out_logprob, int64_t trace_rows, double *trace_probs,
+               const float2 *mu_dev = nullptr, int64_t ld_mu = 0) {
     auto t_start = std::chrono::steady_clock::now();
     h->stats = fastmps_stats{};
     if (M < 1 || !bonds || N < 0 || n0 < 0) return fail(h, FASTMPS_ERR_INVALID_ARG, "need M >= 1, bonds, N >= 0, n0 >= 0");
@@ -561,7 +590,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         // the fused BF16 kernel gives each thread block whole m-tiles: use whole waves of
         // (128 rows x SMs) so that every block gets the same number of m-tiles
         const int64_t wave = (int64_t)128 * h->num_sms;
-        if (bf16 && h->opt.fused_measure && N2 >= wave && N_pad > N2) N2 = N2 / wave * wave;
+        if (bf16 && h->opt.fused_measure && !mu_dev && N2 >= wave && N_pad > N2) N2 = N2 / wave * wave;
     }
     N2 = std::min(N2, N_pad);
     const int64_t J = (N + N2 - 1) / N2;  // micro-batches per site
@@ -576,7 +605,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             if (!h->V[x][p].ensure((size_t)N_pad * ldV * elem))
                 return fail(h, FASTMPS_ERR_OOM, "left-operand allocation failed");
     // BF16 modes measure inside the contraction kernel (no second launch, one scratch buffer)
-    const bool fused = bf16 && !fp8 && h->opt.fused_measure;
+    const bool fused = bf16 && !fp8 && h->opt.fused_measure && !mu_dev;
     const int nybuf = (J > 1 && !fused) ? 2 : 1;
 
     for (int b = 0; b < nybuf; ++b)
@@ -743,6 +772,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
             ma.trace_rows = (int)trace_rows;
             ma.err = d_err;
+            ma.mu = mu_dev ? mu_dev + (int64_t)k * ld_mu + r0 : nullptr;
             cudaEvent_t c0 = timer.get(), c1 = timer.get();
             cudaEventRecord(c0, st);
             if (bf16) {
@@ -763,7 +793,8 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 cudaEventRecord(h->contract_done[yb], st);
                 cudaStreamWaitEvent(ms, h->contract_done[yb], 0);
                 cudaEventRecord(m0, ms);
-                launch_measure(ma, ms);
+                if (ma.mu) launch_measure_displaced(ma, ms);
+                else launch_measure(ma, ms);
                 h->stats.launches += 1;
                 cudaEventRecord(m1, ms);
                 cudaEventRecord(h->measure_done[yb], ms);
@@ -977,6 +1008,109 @@ int fastmps_sample_ex(fastmps_handle h, int M, int d, const int *bond_dims, int6
 int fastmps_sample(fastmps_handle h, int M, int d, const int *bond_dims, int64_t N, uint64_t seed,
                    uint8_t *out_samples, double *out_logprob) {
     return fastmps_sample_ex(h, M, d, bond_dims, 0, N, seed, 0, out_samples, out_logprob, 0, nullptr);
+}
+
+int fastmps_load_site_vidal(fastmps_handle h, int k, int chi_l, int d, int chi_r, const void *Gamma,
+                            const void *Lambda, int dtype) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    if (k < 0 || k >= 65536) return fail(h, FASTMPS_ERR_INVALID_ARG, "site index out of range");
+    if (!Lambda) return fail(h, FASTMPS_ERR_INVALID_ARG, "Lambda is NULL");
+    cudaSetDevice(h->device);
+    std::unique_ptr<Tensor> t(new (std::nothrow) Tensor());
+    if (!t) return fail(h, FASTMPS_ERR_OOM, "out of host memory");
+    int rc = load_tensor(h, *t, chi_l, d, chi_r, Gamma, dtype, Lambda);
+    if (rc) return rc;
+    h->site_tensor[k] = std::move(t);
+    h->site_pool.erase(k);
+    return FASTMPS_OK;
+}
+
+int fastmps_load_pool_vidal(fastmps_handle h, int j, int chi_l, int d, int chi_r, const void *Gamma,
+                            const void *Lambda, int dtype) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    if (j < 0 || j >= 65536) return fail(h, FASTMPS_ERR_INVALID_ARG, "pool index out of range");
+    if (!Lambda) return fail(h, FASTMPS_ERR_INVALID_ARG, "Lambda is NULL");
+    cudaSetDevice(h->device);
+    std::unique_ptr<Tensor> t(new (std::nothrow) Tensor());
+    if (!t) return fail(h, FASTMPS_ERR_OOM, "out of host memory");
+    int rc = load_tensor(h, *t, chi_l, d, chi_r, Gamma, dtype, Lambda);
+    if (rc) return rc;
+    h->pool_tensor[j] = std::move(t);
+    return FASTMPS_OK;
+}
+
+int fastmps_sample_displaced(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N,
+                             uint64_t seed, uint32_t job, const float *mu, int64_t ld_mu, uint8_t *out_samples,
+                             double *out_logprob, int64_t trace_rows, double *trace_probs) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    cudaSetDevice(h->device);
+    try {
+        if (!mu) return fail(h, FASTMPS_ERR_INVALID_ARG, "mu is NULL");
+        if (M < 1 || N < 0 || ld_mu < N) return fail(h, FASTMPS_ERR_INVALID_ARG, "need M >= 1, N >= 0, ld_mu >= N");
+        if (d < 2 || d > kMaxDisplacedD)
+            return fail(h, FASTMPS_ERR_SHAPE, "displaced sampling supports 2 <= d <= " +
+                                                  std::to_string(kMaxDisplacedD));
+        if (is_fp8(h)) return fail(h, FASTMPS_ERR_UNSUPPORTED, "displaced sampling needs FP32 or a BF16 precision");
+        if (N == 0) return run_sample(h, M, d, bond_dims, n0, N, seed, job, out_samples, out_logprob, trace_rows,
+                                      trace_probs);
+        const float2 *mu_dev;
+        int64_t ld = ld_mu;
+        if (is_device_ptr(mu)) {
+            if (reinterpret_cast<uintptr_t>(mu) % 8 != 0)
+                return fail(h, FASTMPS_ERR_INVALID_ARG, "device mu must be 8-byte aligned");
+            mu_dev = reinterpret_cast<const float2 *>(mu);
+        } else {
+            if (!h->mu.ensure((size_t)M * N * 8)) return fail(h, FASTMPS_ERR_OOM, "amplitude allocation failed");
+            cudaError_t e = cudaMemcpy2DAsync(h->mu.p, (size_t)N * 8, mu, (size_t)ld_mu * 8, (size_t)N * 8, M,
+                                              cudaMemcpyHostToDevice, h->stream);
+            if (e != cudaSuccess) return cuda_fail(h, e, "copy of displacement amplitudes");
+            mu_dev = h->mu.as<float2>();
+            ld = N;
+        }
+        int rc = run_sample(h, M, d, bond_dims, n0, N, seed, job, out_samples, out_logprob, trace_rows,
+                            trace_probs, mu_dev, ld);
+        if (rc == FASTMPS_OK && !is_device_ptr(mu)) h->stats.h2d_bytes += (int64_t)M * N * 8;
+        return rc;
+    } catch (const std::bad_alloc &) {
+        return fail(h, FASTMPS_ERR_OOM, "out of host memory");
+    } catch (...) {
+        return fail(h, FASTMPS_ERR_CUDA, "unexpected host exception");
+    }
+}
+
+int fastmps_displacement(fastmps_handle h, int64_t N, int d, const float *mu, float *D) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    if (!mu || !D || N < 0) return fail(h, FASTMPS_ERR_INVALID_ARG, "need mu, D and N >= 0");
+    if (d < 1 || d > 255) return fail(h, FASTMPS_ERR_SHAPE, "need 1 <= d <= 255");
+    if (N == 0) return FASTMPS_OK;
+    cudaSetDevice(h->device);
+    const bool mu_dev = is_device_ptr(mu), D_dev = is_device_ptr(D);
+    if ((mu_dev && reinterpret_cast<uintptr_t>(mu) % 8) || (D_dev && reinterpret_cast<uintptr_t>(D) % 8))
+        return fail(h, FASTMPS_ERR_INVALID_ARG, "device arrays must be 8-byte aligned");
+    const size_t mu_bytes = (size_t)N * 8, D_bytes = (size_t)N * d * d * 8;
+    const size_t off = roundup((int64_t)mu_bytes, 256);
+    if ((!mu_dev || !D_dev) && !h->disp_io.ensure(off + D_bytes))
+        return fail(h, FASTMPS_ERR_OOM, "staging allocation failed");
+    cudaStream_t st = h->stream;
+    cudaError_t e;
+    const float2 *mu_d = reinterpret_cast<const float2 *>(mu);
+    if (!mu_dev) {
+        e = cudaMemcpyAsync(h->disp_io.p, mu, mu_bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of amplitudes");
+        mu_d = h->disp_io.as<float2>();
+    }
+    float2 *D_d = D_dev ? reinterpret_cast<float2 *>(D)
+                        : reinterpret_cast<float2 *>(static_cast<char *>(h->disp_io.p) + off);
+    launch_displacement(mu_d, N, d, D_d, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(h, e, "displacement launch");
+    if (!D_dev) {
+        e = cudaMemcpyAsync(D, D_d, D_bytes, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of displacement matrices");
+    }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "displacement");
+    return FASTMPS_OK;
 }
 
 int fastmps_get_stats(fastmps_handle h, fastmps_stats *out) {

@@ -101,6 +101,7 @@ struct MeasureArgs {
     __nv_bfloat16 *Vp[3];     // BF16 paths: planes of successive residuals
     int nplanes;              // 2 or 3
     uint8_t *V8 = nullptr;    // FP8 path: E4M3 row scaled by a per-row power of two
+    const float2 *mu = nullptr;  // displaced measurement: amplitude of each row of this micro-batch
     uint8_t *outcomes;        // [rows] outcome bytes of this site (site-major buffer slice)
     double *logp;             // [rows] accumulated log-probability
     double *trace;            // nullable: [trace_rows][d] normalised conditionals of this site
@@ -108,6 +109,16 @@ struct MeasureArgs {
     int *err;
 };
 void launch_measure(const MeasureArgs &a, cudaStream_t st);
+
+// ---- Vidal form and GBS displacement (gbs.cu) ------------------------------
+constexpr int kMaxDisplacedD = 16;
+// A[a][s][b] *= lam[b] on an interleaved complex tensor (float or double, lam of the same type).
+void launch_scale_columns(void *A, int is_f64, int64_t n_complex, int chi_r, const void *lam, cudaStream_t st);
+// D[(s*d + t) * N + n] = Zassenhaus displacement matrix of mu[n] (complex64, batch index last).
+void launch_displacement(const float2 *mu, int64_t N, int d, float2 *D, cudaStream_t st);
+// Measurement with the physical index of each row mixed by D(a.mu[row]) first (a.mu != nullptr,
+// d <= kMaxDisplacedD, FP32 or BF16-plane next rows).
+void launch_measure_displaced(const MeasureArgs &a, cudaStream_t st);
 
 // Self-test: one bounded mbarrier wait that nothing completes (status, device time waited).
 void launch_bounded_wait_selftest(uint64_t limit_ns, int *status, unsigned long long *waited_ns, cudaStream_t st);

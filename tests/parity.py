@@ -20,17 +20,19 @@ import oracle
 
 
 def check(bonds, tensors, seed, rows, dev_samples, dev_logprob, tol, dev_trace=None, trace_rows=0,
-          site_index=None, job=0, nthreads=0, site_chunk=None):
+          site_index=None, job=0, nthreads=0, site_chunk=None, lams=None, mu=None):
     """rows: sample indices checked; dev_samples[i], dev_logprob[i] belong to rows[i].
 
     dev_trace: [M, trace_rows, d] device conditionals of rows 0..trace_rows-1
-    (rows[i] < trace_rows are compared).  Returns a report dict; raises
+    (rows[i] < trace_rows are compared).  lams: Vidal form (tensors are Gamma_k).
+    mu: displacement amplitudes of the device call, shape (M, N) with column n
+    for sample n (the call started at n0 = 0).  Returns a report dict; raises
     AssertionError when a rule is broken.
     """
     rows = np.asarray(rows, np.int64)
     forced = np.ascontiguousarray(dev_samples)
     r = oracle.replay(bonds, tensors, seed, rows, forced, job=job, site_index=site_index, nthreads=nthreads,
-                      site_chunk=site_chunk)
+                      site_chunk=site_chunk, lams=lams, mu=None if mu is None else np.asarray(mu)[:, rows])
     M = forced.shape[1]
     mism = r["own"] != forced
     boundary = r["margin"] <= tol
