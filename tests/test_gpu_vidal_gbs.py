@@ -56,7 +56,7 @@ def test_displacement_matrices(lib, d):
         ref = oracle.displacement(complex(mu[n]), d)
         worst = max(worst, float(np.abs(D[:, :, n] - ref).max()))
     print("d", d, "max |D_gpu - D_oracle|", worst)
-    assert worst < 1e-5
+    assert worst < 1e-6
 
 
 def test_displacement_device_arrays_and_empty(lib):
