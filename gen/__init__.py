@@ -37,6 +37,7 @@ __all__ = [
     "vidal_form",
     "gbs_amplitudes",
     "decaying_vidal_chain",
+    "area_law_vidal_chain",
 ]
 
 
@@ -325,4 +326,28 @@ def decaying_vidal_chain(M: int, d: int, chi: int, decay: float = 0.35, seed: in
         lam /= np.linalg.norm(lam)
         gammas.append(As[k] / lam[None, None, :])
         lams.append(lam)
+    return bonds, gammas, lams
+
+
+def area_law_vidal_chain(M: int, d: int, chi: int, xi_max: float = 10.0, seed: int = 314):
+    """A chain in Vidal form whose Schmidt spectra decay fastest at the edges (Sec. 3.4.2: entanglement
+    grows from the edges to the centre).
+
+    Site k is a right-canonical isometry whose Gaussian is damped along the right bond index,
+    ``exp(-b / xi_k)`` with ``xi_k = 1 + xi_max sin(pi (k+1) / M)``, before the QR; the Vidal form
+    (true Schmidt coefficients, descending) then comes from ``vidal_form``.  Returns
+    ``(bonds, Gammas, Lambdas)`` with ``bonds = bond_dims(M, d, chi)``.
+    """
+    bonds = bond_dims(M, d, chi)
+    As = []
+    for k in range(M):
+        cl, cr = bonds[k], bonds[k + 1]
+        g = _gaussian(seed + k, d * cr, cl)
+        xi = 1.0 + xi_max * math.sin(math.pi * (k + 1) / M)
+        g = g * np.tile(np.exp(-np.arange(cr) / xi), d)[:, None]
+        q, r = np.linalg.qr(g, mode="reduced")
+        dg = np.diagonal(r)
+        q = q * (dg / np.abs(dg))[None, :]
+        As.append(np.ascontiguousarray(q.T.reshape(cl, d, cr)))
+    gammas, lams = vidal_form(bonds, As)
     return bonds, gammas, lams

@@ -183,3 +183,63 @@ def test_zassenhaus_vs_truncated_expm(n):
         rel = np.abs(Z - E)[sel] / np.abs(E)[sel]
         worst = max(worst, float(rel.max()))
     assert worst < 2e-3, worst
+
+
+# ---------------------------------------------------------------------------
+# dynamic bond-dimension filter (Sec. 3.4.2)
+# ---------------------------------------------------------------------------
+
+def test_bond_filter_geometric_spectrum_closed_form():
+    """Lambda_j^2 = q^j (n values): eps(c) = (q^c - q^n) / (1 - q^n); the least c with eps(c) <= e is
+    ceil(log(e (1 - q^n) + q^n) / log q)."""
+    from oracle import bond_filter as BF
+
+    for q, n, e in ((0.5, 40, 1e-6), (0.9, 200, 1e-3), (0.99, 500, 0.05), (0.7, 10, 1e-2)):
+        lam = [math.sqrt(q ** j) for j in range(n)]
+        want = math.ceil(math.log(e * (1 - q ** n) + q ** n) / math.log(q) - 1e-9)
+        bonds, disc, es = BF.filter_bonds([lam, [1.0]], d=n, chi=n, eps=e)
+        assert bonds[1] == max(1, want), (q, n, e, bonds[1], want)
+        assert disc[1] <= e and abs(disc[1] - (q ** bonds[1] - q ** n) / (1 - q ** n)) < 1e-12
+
+
+def test_bond_filter_invariants():
+    """Budget = the fixed-chi filter's largest error; every bond within it, minimal, <= chi; the maximum
+    error over bonds equals the fixed-chi one; edges keep fewer than the centre; isometry shapes hold."""
+    from oracle import bond_filter as BF
+
+    M, d, chi = 40, 3, 24
+    b, G, L = gen.area_law_vidal_chain(M, d, 64)                  # spectra of up to 64 values, cap 24
+    bonds, disc, es = BF.filter_bonds(L, d, chi)
+    fixed = [BF.discarded_weight(L[k], min(chi, len(L[k]))) for k in range(M - 1)]
+    assert es == max(fixed) > 0
+    assert max(disc) == es or max(disc) <= es
+    for k in range(M - 1):
+        c = bonds[k + 1]
+        assert 1 <= c <= min(chi, len(L[k]))
+        assert disc[k + 1] <= es
+        assert bonds[k] <= d * c
+    assert bonds[2] < bonds[M // 2] and bonds[M - 2] < bonds[M // 2]
+    assert sum(bonds) < sum(min(x, chi) for x in b)
+    # minimality where the isometry rule did not raise the count
+    for k in range(M - 1):
+        c = bonds[k + 1]
+        if c > 1 and c > -(-bonds[k] // d):
+            assert BF.discarded_weight(L[k], c - 1) > es
+
+
+def test_truncated_vidal_sampling_error_bounded():
+    """The Born law of the truncated chain stays within total-variation distance 2 sqrt(sum of discarded
+    weights) of the full chain's (norm bound of Schmidt truncation; tiny chain, exact laws by brute
+    force on both chains)."""
+    from oracle import bond_filter as BF
+
+    M, d, chi = 9, 3, 27
+    b, G, L = gen.area_law_vidal_chain(M, d, chi, xi_max=3.0, seed=5)
+    bonds, disc, es = BF.filter_bonds(L, d, chi, eps=1e-3)
+    Gt, Lt = BF.truncate_vidal(G, L, bonds)
+    full = oracle.brute_force(b, [G[k] * L[k][None, None, :] for k in range(M)])
+    trunc = oracle.brute_force(bonds, [Gt[k] * Lt[k][None, None, :] for k in range(M)])
+    trunc /= trunc.sum()
+    assert sum(bonds) < sum(b)
+    tv = 0.5 * np.abs(full - trunc).sum()
+    assert tv < 2 * math.sqrt(sum(disc)), (tv, sum(disc))
