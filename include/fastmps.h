@@ -281,6 +281,38 @@ int fastmps_sample_displaced(fastmps_handle h, int M, int d, const int *bond_dim
                              uint64_t seed, uint32_t job, const float *mu, int64_t ld_mu, uint8_t *out_samples,
                              double *out_logprob, int64_t trace_rows, double *trace_probs);
 
+/*
+ * Dynamic bond dimensions (Sec. 3.4.2: entanglement grows from the edges to
+ * the centre, so a fixed bond dimension is redundant at the edges; the filter
+ * keeps fewer coefficients there while the truncation error stays under
+ * control).  Host-only: no device work, no handle.
+ *   bond_in   M+1 ints, the bond dimensions of the chain (bond_in[0] = bond_in[M] = 1).
+ *   lambdas   M-1 host pointers; lambdas[k] holds the bond_in[k+1] Schmidt coefficients of the
+ *             bond right of site k (descending order is not required).
+ *   chi       the fixed bond dimension of the reference filter (keep at most chi per bond).
+ *   eps       discarded-weight budget per bond; eps <= 0 selects the largest discarded weight
+ *             that keeping min(chi, n) coefficients incurs on any bond of this chain.
+ *   bond_out  M+1 ints: bond_out[k+1] = the least c in [1, min(chi, n)] whose discarded weight
+ *             T_c / T_0 (T_c = sum_{j >= c} lambda_j^2, summed in FP64 from the last index down)
+ *             is <= the budget (min(chi, n) if none), then raised left to right to
+ *             ceil(bond_out[k] / d) so that d * chi_r >= chi_l holds at every site.
+ *   discarded_out (nullable) M+1 doubles: the discarded weight of each bond (0 at the ends).
+ * Returns FASTMPS_OK, FASTMPS_ERR_INVALID_ARG (null pointer, bad size, all-zero spectrum) or
+ * FASTMPS_ERR_SHAPE (ends not 1).  Keeping the leading coefficients assumes each spectrum is
+ * sorted in descending order, as Schmidt coefficients are.
+ */
+int fastmps_bond_filter(int M, int d, const int *bond_in, const double *const *lambdas, int chi, double eps,
+                        int *bond_out, double *discarded_out);
+
+/*
+ * Load the leading block Gamma[:keep_l, :, :keep_r], Lambda[:keep_r] of a Vidal-form site whose
+ * arrays have the full shape (chi_l, d, chi_r) and (chi_r) -- the truncation chosen by
+ * fastmps_bond_filter -- without a copy by the caller.  Otherwise as fastmps_load_site_vidal;
+ * needs 1 <= keep_l <= chi_l, 1 <= keep_r <= chi_r and d * keep_r >= keep_l.
+ */
+int fastmps_load_site_vidal_truncated(fastmps_handle h, int k, int chi_l, int d, int chi_r, const void *Gamma,
+                                      const void *Lambda, int dtype, int keep_l, int keep_r);
+
 /* Statistics of the last fastmps_sample* call. */
 int fastmps_get_stats(fastmps_handle h, fastmps_stats *out);
 

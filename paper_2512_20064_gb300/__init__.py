@@ -24,7 +24,7 @@ __all__ = [
     "fastmps_create", "fastmps_destroy", "fastmps_last_error", "fastmps_load_site", "fastmps_load_pool",
     "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_sample_noalloc", "fastmps_sample_batch",
     "fastmps_get_stats", "fastmps_load_site_vidal", "fastmps_load_pool_vidal", "fastmps_displacement",
-    "fastmps_sample_displaced",
+    "fastmps_sample_displaced", "fastmps_bond_filter", "fastmps_load_site_vidal_truncated",
     "fastmps_version",
     "fastmps_default_options",
 ]
@@ -97,6 +97,13 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
             f.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                           ctypes.c_int]
             f.restype = ctypes.c_int
+        lib.fastmps_load_site_vidal_truncated.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                          ctypes.c_int, ctypes.c_int]
+        lib.fastmps_load_site_vidal_truncated.restype = ctypes.c_int
+        lib.fastmps_bond_filter.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p),
+                                            ctypes.c_int, ctypes.c_double, P(ctypes.c_int), ctypes.c_void_p]
+        lib.fastmps_bond_filter.restype = ctypes.c_int
         lib.fastmps_displacement.argtypes = [H, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         lib.fastmps_displacement.restype = ctypes.c_int
         lib.fastmps_sample_displaced.argtypes = [H, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
@@ -239,6 +246,31 @@ def fastmps_load_pool_vidal(h, j: int, Gamma, Lam) -> None:
     lp, lkeep = _lambda_arg(Lam, dt)
     _check(lib, h, lib.fastmps_load_pool_vidal(h, j, cl, d, cr, ptr, lp, dt))
     del keep, lkeep
+
+
+def fastmps_load_site_vidal_truncated(h, k: int, Gamma, Lam, keep_l: int, keep_r: int) -> None:
+    """Load the leading block Gamma[:keep_l, :, :keep_r], Lambda[:keep_r] of a Vidal-form site."""
+    lib = load_library()
+    ptr, keep, dt, (cl, d, cr) = _tensor_arg(Gamma)
+    lp, lkeep = _lambda_arg(Lam, dt)
+    _check(lib, h, lib.fastmps_load_site_vidal_truncated(h, k, cl, d, cr, ptr, lp, dt, keep_l, keep_r))
+    del keep, lkeep
+
+
+def fastmps_bond_filter(bonds, lams, d: int, chi: int, eps: float = 0.0):
+    """Dynamic bond dimensions from the Schmidt spectra ``lams[k]`` (right of site k; host code, no GPU).
+
+    Returns ``(bonds_out[M+1], discarded[M+1])``."""
+    lib = load_library()
+    M = len(bonds) - 1
+    bi = (ctypes.c_int * (M + 1))(*[int(x) for x in bonds])
+    keep = [np.ascontiguousarray(np.asarray(lams[k], dtype=np.float64)) for k in range(max(0, M - 1))]
+    ptrs = (ctypes.c_void_p * max(1, M - 1))(*[a.ctypes.data for a in keep])
+    bo = (ctypes.c_int * (M + 1))()
+    disc = np.zeros(M + 1, np.float64)
+    rc = lib.fastmps_bond_filter(M, d, bi, ptrs, int(chi), float(eps), bo, disc.ctypes.data)
+    _check(lib, None, rc)
+    return [int(x) for x in bo], disc
 
 
 def _complex64_arg(x):
@@ -407,6 +439,11 @@ class Sampler:
         """Load a whole chain given in Vidal form (Gamma_k, Lambda_k)."""
         for k, (G, L) in enumerate(zip(gammas, lams)):
             fastmps_load_site_vidal(self.h, k, G, L)
+
+    def load_chain_vidal_truncated(self, gammas, lams, bonds):
+        """Load the leading blocks ``Gamma_k[:bonds[k], :, :bonds[k+1]]`` (e.g. from ``fastmps_bond_filter``)."""
+        for k, (G, L) in enumerate(zip(gammas, lams)):
+            fastmps_load_site_vidal_truncated(self.h, k, G, L, int(bonds[k]), int(bonds[k + 1]))
 
     def displacement(self, mu, d: int):
         """Batched Zassenhaus displacement matrices, D[s, t, n]."""

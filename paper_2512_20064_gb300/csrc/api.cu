@@ -142,6 +142,7 @@ struct fastmps_ctx {
     DevBuf lam;      // device copy of the Schmidt coefficients of a Vidal-form site being loaded
     DevBuf mu;       // device copy of host displacement amplitudes (displaced sampling)
     DevBuf disp_io;  // device staging of fastmps_displacement's host inputs / outputs
+    DevBuf trunc;    // device gather of the leading block of a truncated Vidal-form site
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
     cudaEvent_t contract_done[2] = {nullptr, nullptr}, measure_done[2] = {nullptr, nullptr};
@@ -1037,6 +1038,31 @@ int fastmps_load_pool_vidal(fastmps_handle h, int j, int chi_l, int d, int chi_r
     if (rc) return rc;
     h->pool_tensor[j] = std::move(t);
     return FASTMPS_OK;
+}
+
+int fastmps_load_site_vidal_truncated(fastmps_handle h, int k, int chi_l, int d, int chi_r, const void *Gamma,
+                                      const void *Lambda, int dtype, int keep_l, int keep_r) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    if (!Gamma || !Lambda) return fail(h, FASTMPS_ERR_INVALID_ARG, "Gamma or Lambda is NULL");
+    if (dtype != FASTMPS_C64 && dtype != FASTMPS_C128) return fail(h, FASTMPS_ERR_INVALID_ARG, "unknown dtype");
+    if (chi_l < 1 || chi_r < 1 || d < 2 || d > 255 || keep_l < 1 || keep_l > chi_l || keep_r < 1 || keep_r > chi_r)
+        return fail(h, FASTMPS_ERR_SHAPE, "need 1 <= keep_l <= chi_l, 1 <= keep_r <= chi_r, 2 <= d <= 255");
+    if (keep_l == chi_l && keep_r == chi_r) return fastmps_load_site_vidal(h, k, chi_l, d, chi_r, Gamma, Lambda, dtype);
+    cudaSetDevice(h->device);
+    const size_t elem = dtype == FASTMPS_C128 ? 16 : 8;
+    const size_t rows = (size_t)keep_l * d, width = (size_t)keep_r * elem, pitch = (size_t)chi_r * elem;
+    // rows (a, s) of Gamma are contiguous runs of chi_r entries: the leading block is a 2D copy
+    if (is_device_ptr(Gamma)) {
+        if (!h->trunc.ensure(rows * width)) return fail(h, FASTMPS_ERR_OOM, "allocation failed");
+        cudaError_t e = cudaMemcpy2DAsync(h->trunc.p, width, Gamma, pitch, width, rows, cudaMemcpyDeviceToDevice,
+                                          h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "gather of the leading block");
+        return fastmps_load_site_vidal(h, k, keep_l, d, keep_r, h->trunc.p, Lambda, dtype);
+    }
+    std::vector<uint8_t> block(rows * width);
+    const uint8_t *src = static_cast<const uint8_t *>(Gamma);
+    for (size_t r = 0; r < rows; ++r) memcpy(block.data() + r * width, src + r * pitch, width);
+    return fastmps_load_site_vidal(h, k, keep_l, d, keep_r, block.data(), Lambda, dtype);
 }
 
 int fastmps_sample_displaced(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N,

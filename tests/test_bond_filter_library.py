@@ -1,0 +1,58 @@
+"""The library's dynamic bond-dimension filter (host code, no GPU) against the oracle's restatement.
+
+Integer results (the kept counts) must be identical, and the discarded weights
+bitwise equal: both sides take every decision in FP64 with the same summation
+order.
+"""
+import numpy as np
+import pytest
+
+import gen
+from oracle import bond_filter as BF
+
+
+@pytest.fixture(scope="module")
+def F():
+    import paper_2512_20064_gb300 as F
+
+    F.load_library()
+    return F
+
+
+@pytest.mark.parametrize("M,d,chi_gen,chi,eps", [(40, 3, 64, 24, 0.0), (40, 3, 64, 64, 1e-4), (30, 4, 48, 8, 0.0),
+                                                  (25, 2, 32, 32, 0.0), (60, 3, 27, 20, 1e-6), (3, 5, 5, 2, 0.0)])
+def test_filter_matches_oracle(F, M, d, chi_gen, chi, eps):
+    b, G, L = gen.area_law_vidal_chain(M, d, chi_gen, seed=M + d)
+    got, disc = F.fastmps_bond_filter(b, L, d, chi, eps)
+    want, wdisc, es = BF.filter_bonds(L, d, chi, eps)
+    assert got == want
+    assert np.array_equal(disc, np.asarray(wdisc))
+    for k in range(M):
+        assert got[k] <= d * got[k + 1]
+
+
+def test_filter_random_spectra(F):
+    """Unsorted and degenerate spectra, a single site, and a budget no bond can meet."""
+    rng = np.random.Generator(np.random.PCG64(8))
+    for trial in range(40):
+        M = int(rng.integers(1, 12))
+        d = int(rng.integers(2, 5))
+        b = [1] + [int(rng.integers(1, 30)) for _ in range(M - 1)] + [1]
+        L = [rng.random(b[k + 1]) ** 3 for k in range(M - 1)] + [np.ones(1)]
+        if trial % 5 == 0 and M > 1:
+            L[0] = np.ones(b[1])                        # flat spectrum
+        chi = int(rng.integers(1, 35))
+        eps = [0.0, 1e-9, 1e-3, 0.3][trial % 4]
+        got, disc = F.fastmps_bond_filter(b, L, d, chi, eps)
+        want, wdisc, _ = BF.filter_bonds(L, d, chi, eps)
+        assert got == want, (trial, got, want)
+        assert np.array_equal(disc, np.asarray(wdisc))
+
+
+def test_filter_rejects_bad_input(F):
+    with pytest.raises(F.FastMPSError) as e:
+        F.fastmps_bond_filter([2, 3, 1], [np.ones(3), np.ones(1)], 3, 4)
+    assert e.value.code == -2
+    with pytest.raises(F.FastMPSError) as e:
+        F.fastmps_bond_filter([1, 3, 1], [np.zeros(3), np.ones(1)], 3, 4)
+    assert e.value.code == -1

@@ -244,3 +244,49 @@ def test_displaced_plain_size(lib):
     rep = parity.check(b, _dq(ts, "bf16x2"), w.sampler_seed, rows, smp[rows], lp[rows], TOL["bf16x2"],
                        dev_trace=tr, trace_rows=32, site_index=idx, mu=mu)
     print(rep, "ms_measure", st["ms_measure"], "ms_contract", st["ms_contract"])
+
+
+# ---------------------------------------------------------------------------
+# dynamic bond dimensions: truncated Vidal chains
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def area_law():
+    return gen.area_law_vidal_chain(60, 3, 64, seed=21)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2"])
+def test_truncated_vidal_parity(lib, area_law, precision):
+    from oracle import bond_filter as BF
+
+    b, G, L = area_law
+    bonds, disc = lib.fastmps_bond_filter(b, L, 3, 24)
+    assert sum(bonds) < sum(min(x, 24) for x in b)
+    Gt, Lt = BF.truncate_vidal(G, L, bonds)
+    N, seed = 3000, 17
+    with lib.Sampler(precision=precision, max_microbatch=1024) as s:
+        s.load_chain_vidal_truncated(G, L, bonds)
+        smp, lp, tr = s.sample(bonds, 3, N, seed, trace_rows=N)
+    if precision == "fp32":
+        rep = parity.check(bonds, Gt, seed, np.arange(N), smp, lp, TOL[precision], dev_trace=tr, trace_rows=N,
+                           lams=Lt)
+    else:
+        stored = _dq([Gt[k] * Lt[k][None, None, :] for k in range(len(Gt))], precision)
+        rep = parity.check(bonds, stored, seed, np.arange(N), smp, lp, TOL[precision], dev_trace=tr, trace_rows=N)
+    print(precision, bonds[:10], rep)
+
+
+def test_truncated_load_from_device_arrays(lib, area_law):
+    """The leading-block gather from device memory (2D copy) equals the host gather."""
+    import torch
+
+    b, G, L = area_law
+    bonds, _ = lib.fastmps_bond_filter(b, L, 3, 16)
+    with lib.Sampler(precision="bf16x2") as s:
+        s.load_chain_vidal_truncated(G, L, bonds)
+        h_s, h_l = s.sample(bonds, 3, 1500, 8)
+    with lib.Sampler(precision="bf16x2") as s:
+        s.load_chain_vidal_truncated([torch.from_numpy(g).cuda() for g in G],
+                                     [torch.from_numpy(l).cuda() for l in L], bonds)
+        d_s, d_l = s.sample(bonds, 3, 1500, 8)
+    assert np.array_equal(h_s, d_s) and np.array_equal(h_l, d_l)
