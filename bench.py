@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     ap.add_argument("--fused-measure", action="store_true",
                     help="BF16 modes: measurement warps inside the contraction kernel")
+    ap.add_argument("--gbs", type=float, default=None, metavar="SIGMA",
+                    help="GBS random displacement (Sec. 3.4.1): every sample and site gets its own complex "
+                         "amplitude, E|mu|^2 = SIGMA^2 (drawn once per run, resident on the device)")
     ap.add_argument("--gen-device", default="cuda", choices=["cuda", "cpu"],
                     help="where the synthetic isometries are drawn (QR); cpu is slower but needs no torch linalg")
     return ap.parse_args()
@@ -271,10 +274,17 @@ def run_ours(args, rank, ws, local):
 
     out_s = torch.empty((macro, w.M), dtype=torch.uint8, device=device)
     out_l = torch.empty(macro, dtype=torch.float64, device=device)
+    mu = None
+    if args.gbs is not None:
+        # displacement amplitudes: inputs of the method (random numbers drawn outside it), resident
+        g = torch.Generator(device=device)
+        g.manual_seed(4242 + rank)
+        mu = torch.complex(torch.randn((w.M, macro), generator=g, device=device),
+                           torch.randn((w.M, macro), generator=g, device=device)) * (args.gbs / 2 ** 0.5)
 
     def step(i):
         s.sample(b, w.d, macro, w.sampler_seed, n0=step_rows(i, rank, ws, macro), out_samples=out_s,
-                 out_logprob=out_l)
+                 out_logprob=out_l, mu=mu)
 
     for i in range(args.warmup):
         step(args.steps + i)
@@ -287,6 +297,7 @@ def run_ours(args, rank, ws, local):
     launches = 0
     contract_ms = 0.0
     contract_launches = 0
+    measure_ms = 0.0
     flops_alg = 0.0
     flops_iss = 0.0
     with torch.cuda.stream(stream):
@@ -297,6 +308,7 @@ def run_ours(args, rank, ws, local):
         launches += st["launches"]
         contract_ms += st["ms_contract"]
         contract_launches += st["contract_launches"]
+        measure_ms += st["ms_measure"]
         flops_alg += st["flops_algorithmic"]
         flops_iss += st["flops_issued"]
     with torch.cuda.stream(stream):
@@ -348,6 +360,21 @@ def run_ours(args, rank, ws, local):
         "setup_s": {"generate": t_gen, "load": t_load},
     }
 
+    if mu is not None:
+        # displaced measurement: reads the whole FP32 row (d blocks of 2 chi_r), the amplitude, writes the
+        # next left row (BF16 planes or FP32) and the outcome, updates the log-probability
+        planes = {"fp32": 1, "bf16x2": 2, "bf16x3": 2, "bf16x3l": 3, "bf16x4": 3}.get(precision, 2)
+        elem = 4 if precision == "fp32" else 2 * planes
+        per_row = sum(8 * w.d * b[k + 1] + 8 + elem * 2 * b[k + 1] + 1 + 16 for k in range(w.M))
+        bytes_alg = per_row * macro * args.steps
+        peaks, _ = measured_peaks()
+        gbs = bytes_alg / (measure_ms / 1e3) / 1e9
+        line["config"]["gbs_displacement"] = f"per sample and site, E|mu|^2 = {args.gbs}^2"
+        line["measure_roofline"] = {"kernel": "measure_displaced_kernel", "bound": "hbm", "achieved": gbs,
+                                    "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                                    "frac": gbs / float(peaks.get("hbm_gbs", 6800.0)),
+                                    "ms_per_step": measure_ms / args.steps,
+                                    "bytes_per_step_algorithmic": bytes_alg / args.steps}
     if residency == "host_stream":
         line["config"]["residency"] = "host_stream (pinned-host BF16 tensors copied per site, double-buffered)"
         st = s.stats()
@@ -365,7 +392,7 @@ def run_ours(args, rank, ws, local):
         line["e2e"] = {"value": macro * w.M / dt, "unit": UNIT, "h2d_bytes_per_step": int(st["h2d_bytes"]),
                        "d2h_bytes_per_step": int(st["d2h_bytes"]), "path": "host_stream + host outputs",
                        "steps": 1}
-    elif rank == 0 and not args.no_e2e:
+    elif rank == 0 and not args.no_e2e and mu is None:
         line["e2e"] = e2e_rate(args, w, b, ts, idx, precision, macro, local)
     if rank == 0 and not args.no_cpu_baseline:
         def host_tensors(K):

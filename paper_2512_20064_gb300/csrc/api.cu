@@ -143,6 +143,9 @@ struct fastmps_ctx {
     DevBuf mu;       // device copy of host displacement amplitudes (displaced sampling)
     DevBuf disp_io;  // device staging of fastmps_displacement's host inputs / outputs
     DevBuf trunc;    // device gather of the leading block of a truncated Vidal-form site
+    DevBuf disp_tab; // constants of the displacement entries for dimension disp_tab_d
+    int disp_tab_d = 0;
+    std::vector<double> disp_tab_host;
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
     cudaEvent_t contract_done[2] = {nullptr, nullptr}, measure_done[2] = {nullptr, nullptr};
@@ -538,6 +541,20 @@ struct EventTimer {
     }
 };
 
+// Device table of the displacement constants for dimension d (built and uploaded once per d).
+const double *displacement_table(fastmps_handle h, int d) {
+    if (h->disp_tab_d == d) return h->disp_tab.as<double>();
+    const size_t n = (size_t)d * d * (d + 1);
+    h->disp_tab_host.assign(n, 0.0);
+    build_displacement_table(d, h->disp_tab_host.data());
+    if (!h->disp_tab.ensure(n * sizeof(double))) return nullptr;
+    if (cudaMemcpyAsync(h->disp_tab.p, h->disp_tab_host.data(), n * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream) != cudaSuccess)
+        return nullptr;
+    h->disp_tab_d = d;
+    return h->disp_tab.as<double>();
+}
+
 // mu_dev (nullable, device): displaced sampling, amplitude of call row i at site k at mu_dev[k * ld_mu + i].
 int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int64_t N, uint64_t seed, uint32_t job,
                uint8_t *out_samples, double *out_logprob, int64_t trace_rows, double *trace_probs,
@@ -639,6 +656,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             return fail(h, FASTMPS_ERR_OOM, "streaming slot allocation failed");
     }
 
+    const double *disp_tab = nullptr;
+    if (mu_dev && !(disp_tab = displacement_table(h, d)))
+        return fail(h, FASTMPS_ERR_OOM, "displacement table allocation failed");
     int *d_err = h->err.as<int>();
     e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
@@ -774,6 +794,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.trace_rows = (int)trace_rows;
             ma.err = d_err;
             ma.mu = mu_dev ? mu_dev + (int64_t)k * ld_mu + r0 : nullptr;
+            ma.disp_tab = disp_tab;
             cudaEvent_t c0 = timer.get(), c1 = timer.get();
             cudaEventRecord(c0, st);
             if (bf16) {
@@ -1127,7 +1148,9 @@ int fastmps_displacement(fastmps_handle h, int64_t N, int d, const float *mu, fl
     }
     float2 *D_d = D_dev ? reinterpret_cast<float2 *>(D)
                         : reinterpret_cast<float2 *>(static_cast<char *>(h->disp_io.p) + off);
-    launch_displacement(mu_d, N, d, D_d, st);
+    const double *tab = displacement_table(h, d);
+    if (!tab) return fail(h, FASTMPS_ERR_OOM, "displacement table allocation failed");
+    launch_displacement(mu_d, N, d, tab, D_d, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "displacement launch");
     if (!D_dev) {

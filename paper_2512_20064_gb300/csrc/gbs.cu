@@ -10,8 +10,8 @@
 //   matrix, each of which has closed-form entries:
 //     exp(mu a^+)[s][m]  = mu^(s-m)      sqrt(s!/m!) / (s-m)!   (s >= m)
 //     exp(-mu^* a)[m][t] = (-mu^*)^(t-m) sqrt(t!/m!) / (t-m)!   (t >= m)
-//   so one entry of the product is a sum of min(s, t) + 1 terms (evaluated in
-//   FP64, rounded to complex64).  Every sample
+//   so one entry of the product is a sum of min(s, t) + 1 terms (the real
+//   series in FP64 from a table of constants).  Every sample
 //   has its own mu; batched matrices are written with the batch index last, so
 //   consecutive threads of a warp write consecutive samples (coalesced).
 // * Displaced measurement: for sample n at site k, the contracted blocks y_t
@@ -26,6 +26,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "launch.h"
@@ -66,47 +67,56 @@ void launch_scale_columns(void *A, int is_f64, int64_t n_complex, int chi_r, con
 //
 // D[s][t] = g sum_{m <= min(s,t)} L[s][m] U[m][t], g = exp(-|mu|^2/2).  Along the sum, consecutive
 // terms differ by a real factor:
-//   term_{m-1} / term_m = -|mu|^2 m / ((s-m+1)(t-m+1)),
-// so the sum is the leading term (m = min(s,t)) times a real alternating series.  For large d and
-// |mu| the series cancels heavily (terms of order 1, sum of order 1e-3 at d = 16, |mu| = 2), so it
-// is evaluated in FP64 and only the entry is rounded to complex64.
+//   term_{m-1} / term_m = -|mu|^2 q_m,  q_m = m / ((s-m+1)(t-m+1)),
+// so D[s][t] = g c_st lead(mu) S with the leading power lead = mu^(s-t) (s >= t) or (-mu^*)^(t-s),
+// c_st = sqrt(max(s,t)! / min(s,t)!) / |s-t|!, and the real alternating series
+// S = 1 + sum_{m=min(s,t)}^{1} prod_{m' >= m} (-|mu|^2 q_m').  For large d and |mu| the series
+// cancels heavily (terms of order 10^3, sum of order 1 at d = 16, |mu| = 2.5), so S is summed in
+// FP64 with the FP64 constants c_st and q_m of a host-built table; g and the leading power, which
+// multiply the whole entry, are taken in FP32.  GB300's FP64 pipes are narrow: the table leaves
+// three FP64 operations per series term and no FP64 division, square root or exponential.
+//
+// Table layout (host-built by build_displacement_table): entry (s, t) at tab[(s*d + t) * (d + 1)]:
+// [c_st, q_1, ..., q_min(s,t)].
 // ---------------------------------------------------------------------------
-__device__ float2 displacement_entry(float2 mu, int s, int t) {
-    const double mr = mu.x, mi = mu.y;
-    const double x = mr * mr + mi * mi;
-    const int j = min(s, t), hi = max(s, t);
-    // leading term: mu^(s-t) sqrt(s!/t!)/(s-t)! for s >= t, (-mu^*)^(t-s) sqrt(t!/s!)/(t-s)! for t > s
-    const double br = s >= t ? mr : -mr, bi = mi;  // mu, or -mu^* = (-Re mu, Im mu)
-    double lr = 1.0, li = 0.0, c = 1.0;
-    for (int q = j + 1; q <= hi; ++q) {
-        const double nr = lr * br - li * bi;
-        li = lr * bi + li * br;
-        lr = nr;
-        c *= sqrt((double)q) / (double)(q - j);
-    }
-    double r = 1.0, sum = 1.0;
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ float2 displacement_entry(float2 mu, int s, int t, int d, const double *__restrict__ tab, float g) {
+    const double *e = tab + (s * d + t) * (d + 1);
+    const int j = min(s, t), p = max(s, t) - j;
+    const float2 base = s >= t ? mu : make_float2(-mu.x, mu.y);  // mu, or -mu^*
+    float2 lead = make_float2(1.f, 0.f);
+    for (int q = 0; q < p; ++q) lead = cmulf(lead, base);
+    const double mx = -((double)mu.x * (double)mu.x + (double)mu.y * (double)mu.y);
+    double r = 1.0, S = 1.0;
     for (int m = j; m >= 1; --m) {
-        r *= -x * (double)m / ((double)(s - m + 1) * (double)(t - m + 1));
-        sum += r;
+        r *= mx * e[m];
+        S += r;
     }
-    const double f = exp(-0.5 * x) * c * sum;
-    return make_float2((float)(f * lr), (float)(f * li));
+    const float f = g * (float)(e[0] * S);
+    return make_float2(f * lead.x, f * lead.y);
 }
 
 // D[(s*d + t) * N + n] for every sample n (batch index last)
-__global__ void displacement_kernel(const float2 *__restrict__ mu, int64_t N, int d, float2 *__restrict__ D) {
+__global__ void displacement_kernel(const float2 *__restrict__ mu, int64_t N, int d, const double *__restrict__ tab,
+                                    float2 *__restrict__ D) {
     const int st = blockIdx.y;  // s * d + t
     const int s = st / d, t = st % d;
-    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x)
-        D[(int64_t)st * N + n] = displacement_entry(mu[n], s, t);
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        const float2 m = mu[n];
+        const float g = expf(-0.5f * (m.x * m.x + m.y * m.y));
+        D[(int64_t)st * N + n] = displacement_entry(m, s, t, d, tab, g);
+    }
 }
 
-void launch_displacement(const float2 *mu, int64_t N, int d, float2 *D, cudaStream_t st) {
+void launch_displacement(const float2 *mu, int64_t N, int d, const double *tab, float2 *D, cudaStream_t st) {
     if (N <= 0) return;
     const int threads = 256;
     const int64_t bx = std::min<int64_t>((N + threads - 1) / threads, 4096);
     dim3 grid((unsigned)bx, (unsigned)(d * d));
-    displacement_kernel<<<grid, threads, 0, st>>>(mu, N, d, D);
+    displacement_kernel<<<grid, threads, 0, st>>>(mu, N, d, tab, D);
 }
 
 // ---------------------------------------------------------------------------
@@ -136,7 +146,8 @@ __global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(cons
     const int64_t Cs = a.Cs;
     float2 *D = Dsh[warp];
     const float2 mu = a.mu[row];
-    for (int e = lane; e < d * d; e += 32) D[e] = displacement_entry(mu, e / d, e % d);
+    const float g = expf(-0.5f * (mu.x * mu.x + mu.y * mu.y));
+    for (int e = lane; e < d * d; e += 32) D[e] = displacement_entry(mu, e / d, e % d, d, a.disp_tab, g);
     __syncwarp();
     const float *yrow = a.Y + (int64_t)row * a.ldY;
 
@@ -236,6 +247,23 @@ void launch_measure_displaced(const MeasureArgs &a, cudaStream_t st) {
     if (a.d <= 4) measure_displaced_kernel<4><<<grid, DISP_WARPS * 32, 0, st>>>(a);
     else if (a.d <= 8) measure_displaced_kernel<8><<<grid, DISP_WARPS * 32, 0, st>>>(a);
     else measure_displaced_kernel<kMaxDisplacedD><<<grid, DISP_WARPS * 32, 0, st>>>(a);
+}
+
+}  // namespace fastmps
+
+namespace fastmps {
+
+void build_displacement_table(int d, double *tab) {
+    for (int s = 0; s < d; ++s)
+        for (int t = 0; t < d; ++t) {
+            double *e = tab + (s * d + t) * (d + 1);
+            const int j = s < t ? s : t, hi = s < t ? t : s;
+            double c = 1.0;
+            for (int q = j + 1; q <= hi; ++q) c *= std::sqrt((double)q) / (double)(q - j);
+            e[0] = c;
+            for (int m = 1; m <= d; ++m)
+                e[m] = m <= j ? (double)m / ((double)(s - m + 1) * (double)(t - m + 1)) : 0.0;
+        }
 }
 
 }  // namespace fastmps
