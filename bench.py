@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="precision",
-                    choices=["precision", "plain", "tiny", "batching", "streaming"])
+                    choices=["precision", "plain", "tiny", "batching", "streaming", "displacement"])
     ap.add_argument("--rows-cap", type=int, default=1024, help="batching: rows sampled per job")
     ap.add_argument("--jobs", type=int, default=64, help="batching: number of MPS")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4", "fp8x1"])
@@ -570,9 +570,72 @@ def run_batching(args, rank, ws, local):
     return line
 
 
+def run_displacement(args, rank, ws, local):
+    """Batched Zassenhaus displacement matrices (Sec. 3.4.1) through fastmps_displacement: 2^24 amplitudes
+    per step (d = 4 by default; --sites overrides d), device arrays, batch index last."""
+    import torch
+
+    import paper_2512_20064_gb300 as F
+
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    d = args.sites or 4
+    N = args.macro or (1 << 24)
+    g = torch.Generator(device=device)
+    g.manual_seed(77 + rank)
+    mu = torch.complex(torch.randn(N, generator=g, device=device), torch.randn(N, generator=g, device=device)) * 0.3
+    out = torch.empty((d, d, N), dtype=torch.complex64, device=device)
+    stream = torch.cuda.Stream(device=local)
+    s = F.Sampler(device=local, stream=stream)
+
+    def step():
+        F.fastmps_displacement(s.h, mu, d, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    with torch.cuda.stream(stream):
+        ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, ws)
+    peaks, src = measured_peaks()
+    bytes_step = N * 8 + N * d * d * 8
+    gbs = bytes_step * args.steps / (ms / 1e3) / 1e9
+    s.close()
+    return {
+        "metric": "displacement matrices/s", "value": N * args.steps * ws / (ms_max / 1e3), "unit": "matrices/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (series in f64)",
+        "data": "synthetic (complex Gaussian amplitudes, E|mu|^2 = 0.18)",
+        "config": {"workload": f"batched Zassenhaus displacement, N = {N} amplitudes, d = {d}, batch index last",
+                   "l2": "outputs larger than L2"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": float(peaks.get("hbm_gbs", 6800.0)), "unit": "GB/s",
+                     "frac": gbs / float(peaks.get("hbm_gbs", 6800.0)), "traffic": None,
+                     "peak_source": f"{src} hbm_gbs", "kernel": "displacement_kernel",
+                     "bytes_per_launch_algorithmic": bytes_step},
+        "gpu_launches": args.steps, "clocks": clk,
+    }
+
+
 def main():
     args = parse()
     rank, ws, local = dist_setup()
+    if args.workload == "displacement" and args.impl == "ours":
+        line = run_displacement(args, rank, ws, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     if args.workload == "batching" and args.impl == "ours":
         line = run_batching(args, rank, ws, local)
         if rank == 0:

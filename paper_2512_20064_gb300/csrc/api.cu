@@ -609,6 +609,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         // (128 rows x SMs) so that every block gets the same number of m-tiles
         const int64_t wave = (int64_t)128 * h->num_sms;
         if (bf16 && h->opt.fused_measure && !mu_dev && N2 >= wave && N_pad > N2) N2 = N2 / wave * wave;
+        // the displaced measurement reads whole scratch rows and takes a large share of a site: with at
+        // least two micro-batches it overlaps the next micro-batch's contraction on the second stream
+        if (mu_dev && N2 >= N_pad && N_pad >= 2 * wave) N2 = roundup((N_pad + 1) / 2, 128);
     }
     N2 = std::min(N2, N_pad);
     const int64_t J = (N + N2 - 1) / N2;  // micro-batches per site

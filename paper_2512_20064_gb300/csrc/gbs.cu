@@ -136,20 +136,39 @@ __device__ __forceinline__ void store_next(const MeasureArgs &a, int64_t grow, i
     if (a.nplanes > 2) a.Vp[2][grow * a.ld_next + i] = h2;
 }
 
-template <int DMAX>
-__global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(const MeasureArgs a) {
+// kStaged: the warp first copies its whole scratch row (d * Cs floats) into shared memory with
+// cp.async (16-byte copies, all in flight at once), so both passes read shared memory and the row
+// crosses HBM once.  Otherwise (rows too large for shared memory) both passes read global memory and
+// the second relies on L2.
+template <int DMAX, bool kStaged>
+__global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(const MeasureArgs a, int rows_per_block) {
     __shared__ float2 Dsh[DISP_WARPS][DMAX * DMAX];
+    extern __shared__ __align__(16) float staged[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * DISP_WARPS + warp;
+    const int row = blockIdx.x * rows_per_block + warp;
     if (row >= a.rows) return;  // whole warps only: no block-level barrier below
     const int d = a.d, chi_r = a.chi_r;
     const int64_t Cs = a.Cs;
+    const float *yrow = a.Y + (int64_t)row * a.ldY;
+    if (kStaged) {
+        const int nf = d * (int)Cs;  // multiple of 32 floats; the row start is 128-byte aligned
+        float *srow = staged + (size_t)warp * nf;
+        const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(srow);
+        for (int i = lane * 4; i < nf; i += 128)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 4u * (uint32_t)i), "l"(yrow + i)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     float2 *D = Dsh[warp];
     const float2 mu = a.mu[row];
     const float g = expf(-0.5f * (mu.x * mu.x + mu.y * mu.y));
     for (int e = lane; e < d * d; e += 32) D[e] = displacement_entry(mu, e / d, e % d, d, a.disp_tab, g);
+    if (kStaged) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        yrow = staged + (size_t)warp * d * (int)Cs;
+    }
     __syncwarp();
-    const float *yrow = a.Y + (int64_t)row * a.ldY;
+    auto ld = [&](int64_t i) -> float { return kStaged ? yrow[i] : __ldcg(yrow + i); };
 
     // pass 1: w_s = sum_b |sum_t D[s][t] y_t[b]|^2, FP32 per lane, FP64 across lanes
     float w[DMAX];
@@ -159,8 +178,7 @@ __global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(cons
         float2 y[DMAX];
 #pragma unroll
         for (int t = 0; t < DMAX; ++t)
-            y[t] = t < d ? make_float2(__ldcg(yrow + t * Cs + b), __ldcg(yrow + t * Cs + chi_r + b))
-                         : make_float2(0.f, 0.f);
+            y[t] = t < d ? make_float2(ld(t * Cs + b), ld(t * Cs + chi_r + b)) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int s = 0; s < DMAX; ++s) {
             if (s >= d) break;
@@ -231,7 +249,7 @@ __global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(cons
 #pragma unroll
         for (int t = 0; t < DMAX; ++t) {
             if (t >= d) break;
-            const float yr = __ldcg(yrow + t * Cs + b), yi = __ldcg(yrow + t * Cs + chi_r + b);
+            const float yr = ld(t * Cs + b), yi = ld(t * Cs + chi_r + b);
             zr = fmaf(c[t].x, yr, fmaf(-c[t].y, yi, zr));
             zi = fmaf(c[t].x, yi, fmaf(c[t].y, yr, zi));
         }
@@ -241,12 +259,36 @@ __global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(cons
     for (int i = 2 * chi_r + lane; i < a.K_next; i += 32) store_next(a, grow, i, 0.f);
 }
 
+// Shared memory of the staged variant: at most 96 KB of rows per block (two blocks per SM),
+// rows above 200 KB (e.g. d = 3, chi = 10^4) use the unstaged variant.
+constexpr int kStageBudget = 96 * 1024;
+constexpr int kStageMaxRow = 200 * 1024;
+
+template <int DMAX>
+void launch_displaced_variant(const MeasureArgs &a, cudaStream_t st) {
+    const size_t row_bytes = (size_t)a.d * a.Cs * sizeof(float);
+    if (row_bytes > (size_t)kStageMaxRow || (int64_t)a.d * a.Cs > a.ldY) {
+        const int grid = (a.rows + DISP_WARPS - 1) / DISP_WARPS;
+        measure_displaced_kernel<DMAX, false><<<grid, DISP_WARPS * 32, 0, st>>>(a, DISP_WARPS);
+        return;
+    }
+    const int rpb = (int)std::max<size_t>(1, std::min<size_t>(DISP_WARPS, kStageBudget / row_bytes));
+    const size_t smem = (size_t)rpb * row_bytes;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(measure_displaced_kernel<DMAX, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStageMaxRow + 1024);
+        attr_set = true;
+    }
+    const int grid = (a.rows + rpb - 1) / rpb;
+    measure_displaced_kernel<DMAX, true><<<grid, rpb * 32, smem, st>>>(a, rpb);
+}
+
 void launch_measure_displaced(const MeasureArgs &a, cudaStream_t st) {
     if (a.rows <= 0) return;
-    const int grid = (a.rows + DISP_WARPS - 1) / DISP_WARPS;
-    if (a.d <= 4) measure_displaced_kernel<4><<<grid, DISP_WARPS * 32, 0, st>>>(a);
-    else if (a.d <= 8) measure_displaced_kernel<8><<<grid, DISP_WARPS * 32, 0, st>>>(a);
-    else measure_displaced_kernel<kMaxDisplacedD><<<grid, DISP_WARPS * 32, 0, st>>>(a);
+    if (a.d <= 4) launch_displaced_variant<4>(a, st);
+    else if (a.d <= 8) launch_displaced_variant<8>(a, st);
+    else launch_displaced_variant<kMaxDisplacedD>(a, st);
 }
 
 }  // namespace fastmps

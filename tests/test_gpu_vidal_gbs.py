@@ -145,6 +145,21 @@ def test_displaced_parity(lib, precision, d, chi):
     assert rep["prob_rows"] == N
 
 
+def test_displaced_large_rows_unstaged(lib):
+    """d = 16 with a 2048-wide bond: the scratch rows of site 2 (16 x 4096 floats = 256 KB) exceed the
+    shared-memory staging limit and take the unstaged kernel; the other sites are staged."""
+    M, d, N, seed = 6, 16, 512, 12
+    b, ts, _ = gen.mps_tensors(M, d, 2048, base_seed=70, skew=4.0)
+    assert max(b) == 2048
+    mu = gen.gbs_amplitudes(M, N, sigma=0.5, seed=3)
+    with lib.Sampler(precision="fp32") as s:
+        s.load_chain(ts)
+        smp, lp, tr = s.sample(b, d, N, seed, trace_rows=64, mu=mu)
+    rows = np.arange(0, N, 4)
+    rep = parity.check(b, ts, seed, rows, smp[rows], lp[rows], TOL["fp32"], dev_trace=tr, trace_rows=64, mu=mu)
+    print(rep)
+
+
 def test_displaced_device_amplitudes_and_strided(lib):
     """Device-resident amplitudes, and host amplitudes with a leading dimension above N, give the
     same result as contiguous host amplitudes."""
