@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="precision",
-                    choices=["precision", "plain", "tiny", "batching", "streaming", "displacement"])
+                    choices=["precision", "plain", "tiny", "batching", "streaming", "displacement", "knee"])
     ap.add_argument("--rows-cap", type=int, default=1024, help="batching: rows sampled per job")
     ap.add_argument("--jobs", type=int, default=64, help="batching: number of MPS")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4", "fp8x1"])
@@ -628,9 +628,52 @@ def run_displacement(args, rank, ws, local):
     }
 
 
+def run_knee(args, rank, ws, local):
+    """Micro-batch sweep (the paper's Sec. 4 parameter study, chi = 2000, d = 3): contraction throughput
+    of one macro-batch of 2^16 rows as a function of the rows per contraction launch N2.  Shows where
+    the per-site GEMM stops being too narrow for the tensor cores on one GB300 (the paper found the knee
+    at N = 5000 on an A100), and that no split of K is needed to fill the 152 SMs."""
+    import torch
+
+    import paper_2512_20064_gb300 as F
+
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    M, d, chi, N = 24, 3, 2000, 1 << 16
+    b, ts, idx = gen.mps_tensors(M, d, chi, base_seed=5150, skew=1.5, pool=4, device=device)
+    out_s = torch.empty((N, M), dtype=torch.uint8, device=device)
+    out_l = torch.empty(N, dtype=torch.float64, device=device)
+    points = []
+    for n2 in (128, 256, 512, 1024, 2048, 4096, 8192, 16384, 32768, 65536):
+        with F.Sampler(device=local, precision=args.precision or "bf16x2", max_microbatch=n2) as s:
+            s.load_chain(ts, site_index=idx)
+            for _ in range(max(1, args.warmup)):
+                s.sample(b, d, N, 1, out_samples=out_s, out_logprob=out_l)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.sample(b, d, N, 2, out_samples=out_s, out_logprob=out_l)
+            wall = time.perf_counter() - t0
+            st = s.stats()
+        points.append({"rows_per_launch": n2, "launches": int(st["contract_launches"]),
+                       "contract_tflops_issued": st["flops_issued"] / (st["ms_contract"] / 1e3) / 1e12,
+                       "ms_contract": st["ms_contract"], "ms_total": wall * 1e3,
+                       "m_tiles_x_n_tiles_per_launch": (n2 // 128) * ((2 * chi + 255) // 256) * d})
+    peaks, src = measured_peaks()
+    return {"metric": "contraction TFLOP/s (issued) vs rows per launch", "unit": "TFLOP/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"M={M} d={d} chi={chi} (pool of 4 interior isometries), N={N}",
+                       "precision": args.precision or "bf16x2"},
+            "peak": float(peaks.get("bf16_tflops_sustained", 1700.0)), "peak_source": src, "points": points}
+
+
 def main():
     args = parse()
     rank, ws, local = dist_setup()
+    if args.workload == "knee" and args.impl == "ours":
+        line = run_knee(args, rank, ws, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     if args.workload == "displacement" and args.impl == "ours":
         line = run_displacement(args, rank, ws, local)
         if rank == 0:

@@ -145,7 +145,7 @@ struct fastmps_ctx {
     DevBuf trunc;    // device gather of the leading block of a truncated Vidal-form site
     DevBuf disp_tab; // constants of the displacement entries for dimension disp_tab_d
     int disp_tab_d = 0;
-    std::vector<double> disp_tab_host;
+    std::vector<float> disp_tab_host;
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
     cudaEvent_t copy_done[2] = {nullptr, nullptr}, slot_free[2] = {nullptr, nullptr};
     cudaEvent_t contract_done[2] = {nullptr, nullptr}, measure_done[2] = {nullptr, nullptr};
@@ -542,17 +542,17 @@ struct EventTimer {
 };
 
 // Device table of the displacement constants for dimension d (built and uploaded once per d).
-const double *displacement_table(fastmps_handle h, int d) {
-    if (h->disp_tab_d == d) return h->disp_tab.as<double>();
-    const size_t n = (size_t)d * d * (d + 1);
-    h->disp_tab_host.assign(n, 0.0);
+const float *displacement_table(fastmps_handle h, int d) {
+    if (h->disp_tab_d == d) return h->disp_tab.as<float>();
+    const size_t n = (size_t)d * d * (2 * d + 1);
+    h->disp_tab_host.assign(n, 0.f);
     build_displacement_table(d, h->disp_tab_host.data());
-    if (!h->disp_tab.ensure(n * sizeof(double))) return nullptr;
-    if (cudaMemcpyAsync(h->disp_tab.p, h->disp_tab_host.data(), n * sizeof(double), cudaMemcpyHostToDevice,
+    if (!h->disp_tab.ensure(n * sizeof(float))) return nullptr;
+    if (cudaMemcpyAsync(h->disp_tab.p, h->disp_tab_host.data(), n * sizeof(float), cudaMemcpyHostToDevice,
                         h->stream) != cudaSuccess)
         return nullptr;
     h->disp_tab_d = d;
-    return h->disp_tab.as<double>();
+    return h->disp_tab.as<float>();
 }
 
 // mu_dev (nullable, device): displaced sampling, amplitude of call row i at site k at mu_dev[k * ld_mu + i].
@@ -659,7 +659,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             return fail(h, FASTMPS_ERR_OOM, "streaming slot allocation failed");
     }
 
-    const double *disp_tab = nullptr;
+    const float *disp_tab = nullptr;
     if (mu_dev && !(disp_tab = displacement_table(h, d)))
         return fail(h, FASTMPS_ERR_OOM, "displacement table allocation failed");
     int *d_err = h->err.as<int>();
@@ -818,7 +818,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 cudaEventRecord(h->contract_done[yb], st);
                 cudaStreamWaitEvent(ms, h->contract_done[yb], 0);
                 cudaEventRecord(m0, ms);
-                if (ma.mu) launch_measure_displaced(ma, ms);
+                if (ma.mu) launch_measure_displaced(ma, h->num_sms, ms);
                 else launch_measure(ma, ms);
                 h->stats.launches += 1;
                 cudaEventRecord(m1, ms);
@@ -1151,9 +1151,9 @@ int fastmps_displacement(fastmps_handle h, int64_t N, int d, const float *mu, fl
     }
     float2 *D_d = D_dev ? reinterpret_cast<float2 *>(D)
                         : reinterpret_cast<float2 *>(static_cast<char *>(h->disp_io.p) + off);
-    const double *tab = displacement_table(h, d);
+    const float *tab = displacement_table(h, d);
     if (!tab) return fail(h, FASTMPS_ERR_OOM, "displacement table allocation failed");
-    launch_displacement(mu_d, N, d, tab, D_d, st);
+    launch_displacement(mu_d, N, d, tab, D_d, h->num_sms, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "displacement launch");
     if (!D_dev) {

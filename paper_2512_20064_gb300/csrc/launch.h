@@ -102,7 +102,7 @@ struct MeasureArgs {
     int nplanes;              // 2 or 3
     uint8_t *V8 = nullptr;    // FP8 path: E4M3 row scaled by a per-row power of two
     const float2 *mu = nullptr;  // displaced measurement: amplitude of each row of this micro-batch
-    const double *disp_tab = nullptr;  // displaced measurement: constants of the displacement entries
+    const float *disp_tab = nullptr;   // displaced measurement: constants of the displacement entries
     uint8_t *outcomes;        // [rows] outcome bytes of this site (site-major buffer slice)
     double *logp;             // [rows] accumulated log-probability
     double *trace;            // nullable: [trace_rows][d] normalised conditionals of this site
@@ -115,14 +115,16 @@ void launch_measure(const MeasureArgs &a, cudaStream_t st);
 constexpr int kMaxDisplacedD = 16;
 // A[a][s][b] *= lam[b] on an interleaved complex tensor (float or double, lam of the same type).
 void launch_scale_columns(void *A, int is_f64, int64_t n_complex, int chi_r, const void *lam, cudaStream_t st);
-// Constants of the displacement entries for dimension d: (s, t) at [(s*d + t) * (d + 1)]:
-// c_st = sqrt(max! / min!) / |s-t|!, then q_m = m / ((s-m+1)(t-m+1)) for m = 1 .. min(s, t).
-void build_displacement_table(int d, double *tab /* d * d * (d + 1) */);
+// Constants of the displacement entries for dimension d: (s, t) at [(s*d + t) * (2d + 1)]:
+// c_st = sqrt(max! / min!) / |s-t|!, then q_m = m / ((s-m+1)(t-m+1)) for m = 1 .. d (0 above
+// min(s, t)) as float-float pairs (hi, lo).
+void build_displacement_table(int d, float *tab /* d * d * (2d + 1) */);
 // D[(s*d + t) * N + n] = Zassenhaus displacement matrix of mu[n] (complex64, batch index last).
-void launch_displacement(const float2 *mu, int64_t N, int d, const double *tab, float2 *D, cudaStream_t st);
+void launch_displacement(const float2 *mu, int64_t N, int d, const float *tab, float2 *D, int num_sms,
+                         cudaStream_t st);
 // Measurement with the physical index of each row mixed by D(a.mu[row]) first (a.mu != nullptr,
 // d <= kMaxDisplacedD, FP32 or BF16-plane next rows).
-void launch_measure_displaced(const MeasureArgs &a, cudaStream_t st);
+void launch_measure_displaced(const MeasureArgs &a, int num_sms, cudaStream_t st);
 
 // Self-test: one bounded mbarrier wait that nothing completes (status, device time waited).
 void launch_bounded_wait_selftest(uint64_t limit_ns, int *status, unsigned long long *waited_ns, cudaStream_t st);
