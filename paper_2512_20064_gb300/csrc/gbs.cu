@@ -19,9 +19,9 @@
 //   probabilities w_s = ||z_s||^2 are formed; the draw is Algorithm 2's, and the
 //   next left vector is z_{s*} / sqrt(w_{s*}).  The mixing couples all d blocks
 //   of a row, which no contraction tile holds together (a tile covers columns
-//   of one outcome), so this kernel reads the whole FP32 scratch row (staged in
-//   shared memory, so that it crosses HBM once) to form the probabilities and
-//   the selected combination.
+//   of one outcome), so this kernel reads the whole FP32 scratch row (held in
+//   registers by one small thread block per row, so that it crosses HBM once)
+//   to form the probabilities and the selected combination.
 // GB300's FP64 pipes are narrow (a warp-wide FP64 instruction costs an SM
 // about 16 issue cycles): FP64 is kept to the draw itself; the displacement
 // series uses float-float (error-free FP32 transformations) and the lane sums
@@ -176,13 +176,6 @@ __device__ __forceinline__ void store_next(const MeasureArgs &a, int64_t grow, i
     if (a.nplanes > 2) a.Vp[2][grow * a.ld_next + i] = h2;
 }
 
-__device__ __forceinline__ void stage_row(float *dst, const float *src, int nf, int lane) {
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(dst);
-    for (int i = lane * 4; i < nf; i += 128)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 4u * (uint32_t)i), "l"(src + i)
-                     : "memory");
-}
-
 // The measurement of one row given the row's scratch values (global or shared memory) and D.
 template <int DMAX, bool kShared>
 __device__ __forceinline__ void displaced_row(const MeasureArgs &a, int row, const float *yrow, const float2 *D,
@@ -284,35 +277,8 @@ __device__ __forceinline__ void build_D(const MeasureArgs &a, int row, float2 *D
     for (int e = lane; e < d * d; e += 32) D[e] = displacement_entry(mu, mx, g, e / d, e % d, d, a.disp_tab);
 }
 
-// Persistent, staged: each warp walks rows r = gw, gw + W, ... (W warps in the grid), with two shared
-// buffers of one scratch row each: the row after next is copied (cp.async) while this one is measured.
-template <int DMAX>
-__global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_staged_kernel(const MeasureArgs a,
-                                                                                  int total_warps) {
-    __shared__ float2 Dsh[DISP_WARPS][DMAX * DMAX];
-    extern __shared__ __align__(16) float staged[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (gw >= a.rows) return;  // whole warps only: no block-level barrier below
-    const int nf = a.d * a.Cs;  // floats of one row; a multiple of 32, and each row starts 128-byte aligned
-    float *const mine = staged + (size_t)warp * 2 * nf;  // this warp's two row buffers
-    stage_row(mine, a.Y + (int64_t)gw * a.ldY, nf, lane);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    int cur = 0;
-    for (int row = gw; row < a.rows; row += total_warps, cur ^= 1) {
-        const int next = row + total_warps;
-        if (next < a.rows) stage_row(mine + (size_t)(cur ^ 1) * nf, a.Y + (int64_t)next * a.ldY, nf, lane);
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        build_D(a, row, Dsh[warp], lane);
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this row's copy (all but the newest group)
-        __syncwarp();
-        displaced_row<DMAX, true>(a, row, mine + (size_t)cur * nf, Dsh[warp], lane);
-        __syncwarp();  // this buffer and D are reused by the next iterations
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-}
-
-// Unstaged (rows above the shared-memory limit): one row per warp, the second pass relies on L2.
+// Unstaged fallback (rows wider than the register-resident kernel takes): one row per warp, the
+// second pass re-reads the row and relies on L2.
 template <int DMAX>
 __global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(const MeasureArgs a) {
     __shared__ float2 Dsh[DISP_WARPS][DMAX * DMAX];
@@ -324,40 +290,176 @@ __global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(cons
     displaced_row<DMAX, false>(a, row, a.Y + (int64_t)row * a.ldY, Dsh[warp], lane);
 }
 
-// Two row buffers per warp must fit: rows up to 48 KB are staged (4 warps x 2 x 48 KB would not fit
-// one SM, so the warps per block shrink with the row size).
-constexpr size_t kStageSmem = 200 * 1024;   // shared memory per block for staged rows
-constexpr size_t kStageMaxRow = 48 * 1024;
+// Register-resident: one thread block per sample row; thread j holds the columns b = j + T v
+// (v < VPT) of all d blocks in registers, so the row crosses HBM once and both passes read
+// registers.  Small blocks (T = 32 .. 256 threads) keep many rows in flight per SM.  The lane sums
+// are reduced in FP32 (warp shuffles, then across warps in shared memory); one thread takes the
+// FP64 draw.
+template <int DMAX, int VPT>
+__global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const MeasureArgs a) {
+    __shared__ float2 D[DMAX * DMAX];
+    __shared__ float red[8][DMAX];
+    __shared__ float2 coef[DMAX];
+    __shared__ int s_sstar;
+    const int row = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
+    const int d = a.d, chi_r = a.chi_r;
+    const int64_t Cs = a.Cs;
+    const float *yrow = a.Y + (int64_t)row * a.ldY;
+    // all loads of the row first (independent, coalesced across the block)
+    float2 y[VPT][DMAX];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int b = tid + T * v;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t)
+            y[v][t] = (t < d && b < chi_r) ? make_float2(__ldcs(yrow + t * Cs + b), __ldcs(yrow + t * Cs + chi_r + b))
+                                          : make_float2(0.f, 0.f);
+    }
+    if (tid < 32) build_D(a, row, D, lane);
+    __syncthreads();
+    // pass 1: partial w_s over this thread's columns
+    float w[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) w[s] = 0.f;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) {
+            if (s >= d) break;
+            float zr = 0.f, zi = 0.f;
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t) {
+                if (t >= d) break;
+                const float2 c = D[s * d + t];
+                zr = fmaf(c.x, y[v][t].x, fmaf(-c.y, y[v][t].y, zr));
+                zi = fmaf(c.x, y[v][t].y, fmaf(c.y, y[v][t].x, zi));
+            }
+            w[s] = fmaf(zr, zr, fmaf(zi, zi, w[s]));
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w[s] += __shfl_xor_sync(0xffffffffu, w[s], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) red[warp][s] = w[s];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int nw = T >> 5;
+        float ws32[DMAX];
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) {
+            float acc = 0.f;
+            for (int q = 0; q < nw; ++q) acc += red[q][s];
+            ws32[s] = acc;
+        }
+        // the draw in FP64: C_s in s order, s* = first s with C_s >= u Z, else d-1
+        double C[DMAX];
+        double acc = 0.0;
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) {
+            if (s < d) acc += (double)ws32[s];
+            C[s] = acc;
+        }
+        const double Z = acc;
+        const uint64_t n = a.n_base + (uint64_t)row;
+        const double thr = sample_uniform(a.seed, n, a.k, a.job) * Z;
+        int sstar = d - 1;
+#pragma unroll
+        for (int s = DMAX - 1; s >= 0; --s)
+            if (s < d - 1 && C[s] >= thr) sstar = s;
+        float wsel = 0.f;
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s)
+            if (s == sstar) wsel = ws32[s];
+        const bool ok = (Z > 0.0) && isfinite(Z) && (wsel > 0.f);
+        const int64_t grow = a.row0 + row;
+        a.outcomes[row] = (uint8_t)sstar;
+        if (ok) a.logp[grow] += (double)(logf(wsel) - logf((float)Z));
+        else atomicExch(a.err, (int)kDevNumeric);
+        if (a.trace && grow < a.trace_rows) {
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s)
+                if (s < d) a.trace[grow * d + s] = ok ? (double)ws32[s] / Z : 0.0;
+        }
+        const float scale = ok ? rsqrtf(wsel) : 0.f;
+        s_sstar = sstar;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) {
+            const float2 e = t < d ? D[sstar * d + t] : make_float2(0.f, 0.f);
+            coef[t] = make_float2(e.x * scale, e.y * scale);
+        }
+    }
+    __syncthreads();
+    // pass 2 from registers: next left row = (sum_t D[s*][t] y_t) / sqrt(w_{s*})
+    const int64_t grow = a.row0 + row;
+    float2 c[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) c[t] = coef[t];
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+        const int b = tid + T * v;
+        if (b >= chi_r) break;
+        float zr = 0.f, zi = 0.f;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) {
+            if (t >= d) break;
+            zr = fmaf(c[t].x, y[v][t].x, fmaf(-c[t].y, y[v][t].y, zr));
+            zi = fmaf(c[t].x, y[v][t].y, fmaf(c[t].y, y[v][t].x, zi));
+        }
+        store_next(a, grow, b, zr);
+        store_next(a, grow, chi_r + b, zi);
+    }
+    for (int i = 2 * chi_r + tid; i < a.K_next; i += T) store_next(a, grow, i, 0.f);
+    (void)s_sstar;
+}
+
+// Threads per block and columns per thread of the register-resident kernel: the fewest columns per
+// thread (VPT in {1, 2, 4, 8}) that cover chi_r with at most 128 threads (else 256), under a register
+// cap of VPT * DMAX <= 32 complex values; 0 if none fits (the unstaged kernel runs instead).
+template <int DMAX>
+bool launch_rows_variant(const MeasureArgs &a, cudaStream_t st) {
+    const int chi_r = a.chi_r;
+    for (int cap : {128, 256}) {
+        for (int vpt : {1, 2, 4, 8}) {
+            if (vpt * DMAX > 32) break;
+            const int need = (chi_r + vpt - 1) / vpt;
+            if (need > cap) continue;
+            const int T = std::max(32, (need + 31) / 32 * 32);
+            const dim3 grid((unsigned)a.rows);
+            switch (vpt) {
+                case 1: measure_displaced_rows_kernel<DMAX, 1><<<grid, T, 0, st>>>(a); break;
+                case 2: measure_displaced_rows_kernel<DMAX, 2><<<grid, T, 0, st>>>(a); break;
+                case 4:
+                    if constexpr (4 * DMAX <= 32) measure_displaced_rows_kernel<DMAX, 4><<<grid, T, 0, st>>>(a);
+                    break;
+                default:
+                    if constexpr (8 * DMAX <= 32) measure_displaced_rows_kernel<DMAX, 8><<<grid, T, 0, st>>>(a);
+                    break;
+            }
+            return true;
+        }
+    }
+    return false;
+}
 
 template <int DMAX>
-void launch_displaced_variant(const MeasureArgs &a, int num_sms, cudaStream_t st) {
-    const size_t row_bytes = (size_t)a.d * a.Cs * sizeof(float);
-    if (row_bytes > kStageMaxRow || (int64_t)a.d * a.Cs > a.ldY) {
-        const int grid = (a.rows + DISP_WARPS - 1) / DISP_WARPS;
-        measure_displaced_kernel<DMAX><<<grid, DISP_WARPS * 32, 0, st>>>(a);
-        return;
-    }
-    const int wpb = (int)std::max<size_t>(1, std::min<size_t>(DISP_WARPS, kStageSmem / (2 * row_bytes)));
-    const size_t smem = (size_t)wpb * 2 * row_bytes;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(measure_displaced_staged_kernel<DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kStageSmem);
-        attr_set = true;
-    }
-    // blocks resident per SM (227 KB of shared memory, DMAX^2 * 8 bytes static per warp)
-    const size_t per_block = smem + (size_t)DISP_WARPS * DMAX * DMAX * 8 + 1024;
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(8, (size_t)(227 * 1024) / per_block));
-    const int64_t want = ((int64_t)a.rows + wpb - 1) / wpb;
-    const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms * per_sm);
-    measure_displaced_staged_kernel<DMAX><<<grid, wpb * 32, smem, st>>>(a, grid * wpb);
+void launch_displaced_variant(const MeasureArgs &a, cudaStream_t st) {
+    if (launch_rows_variant<DMAX>(a, st)) return;
+    const int grid = (a.rows + DISP_WARPS - 1) / DISP_WARPS;
+    measure_displaced_kernel<DMAX><<<grid, DISP_WARPS * 32, 0, st>>>(a);
 }
 
 void launch_measure_displaced(const MeasureArgs &a, int num_sms, cudaStream_t st) {
+    (void)num_sms;
     if (a.rows <= 0) return;
-    if (a.d <= 4) launch_displaced_variant<4>(a, num_sms, st);
-    else if (a.d <= 8) launch_displaced_variant<8>(a, num_sms, st);
-    else launch_displaced_variant<kMaxDisplacedD>(a, num_sms, st);
+    if (a.d <= 4) launch_displaced_variant<4>(a, st);
+    else if (a.d <= 8) launch_displaced_variant<8>(a, st);
+    else launch_displaced_variant<kMaxDisplacedD>(a, st);
 }
 
 }  // namespace fastmps
