@@ -144,6 +144,7 @@ struct fastmps_ctx {
     DevBuf disp_io;  // device staging of fastmps_displacement's host inputs / outputs
     DevBuf trunc;    // device gather of the leading block of a truncated Vidal-form site
     DevBuf disp_tab; // constants of the displacement entries for dimension disp_tab_d
+    DevBuf disp_D, disp_u;  // per-row matrices and uniforms of one displaced micro-batch
     int disp_tab_d = 0;
     std::vector<float> disp_tab_host;
     DevBuf slot_compact[2], slot_hi, slot_lo;  // streaming slots
@@ -660,8 +661,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     }
 
     const float *disp_tab = nullptr;
-    if (mu_dev && !(disp_tab = displacement_table(h, d)))
-        return fail(h, FASTMPS_ERR_OOM, "displacement table allocation failed");
+    if (mu_dev && (!(disp_tab = displacement_table(h, d)) || !h->disp_D.ensure((size_t)N2 * d * d * 8) ||
+                   !h->disp_u.ensure((size_t)N2 * 8)))
+        return fail(h, FASTMPS_ERR_OOM, "displacement buffers allocation failed");
     int *d_err = h->err.as<int>();
     e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
@@ -798,6 +800,8 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.err = d_err;
             ma.mu = mu_dev ? mu_dev + (int64_t)k * ld_mu + r0 : nullptr;
             ma.disp_tab = disp_tab;
+            ma.disp_D = mu_dev ? h->disp_D.as<float2>() : nullptr;
+            ma.disp_u = mu_dev ? h->disp_u.as<double>() : nullptr;
             cudaEvent_t c0 = timer.get(), c1 = timer.get();
             cudaEventRecord(c0, st);
             if (bf16) {
@@ -820,7 +824,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 cudaEventRecord(m0, ms);
                 if (ma.mu) launch_measure_displaced(ma, h->num_sms, ms);
                 else launch_measure(ma, ms);
-                h->stats.launches += 1;
+                h->stats.launches += ma.mu ? 2 : 1;  // the displaced measurement has a prep kernel
                 cudaEventRecord(m1, ms);
                 cudaEventRecord(h->measure_done[yb], ms);
                 timer.measure.push_back({m0, m1});

@@ -159,6 +159,22 @@ void launch_displacement(const float2 *mu, int64_t N, int d, const float *tab, f
     displacement_kernel<<<(unsigned)blocks, threads, 0, st>>>(mu, N, d, tab, D);
 }
 
+// Per-row inputs of the displaced measurement, one thread per row: the row's displacement matrix
+// D[row][s*d + t] and its uniform u = U(seed, n, k, job), so that the measurement kernel's
+// per-row serial section is only the draw.
+__global__ void __launch_bounds__(256) displaced_prep_kernel(const MeasureArgs a) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= a.rows) return;
+    const int d = a.d;
+    const float2 m = a.mu[row];
+    const ffloat mx = neg_abs2(m);
+    const float g = expf(0.5f * (mx.hi + mx.lo));
+    float2 *out = a.disp_D + (int64_t)row * d * d;
+    for (int s = 0; s < d; ++s)
+        for (int t = 0; t < d; ++t) out[s * d + t] = displacement_entry(m, mx, g, s, t, d, a.disp_tab);
+    a.disp_u[row] = sample_uniform(a.seed, a.n_base + (uint64_t)row, a.k, a.job);
+}
+
 // ---------------------------------------------------------------------------
 // Displaced measurement: one warp per sample row at a time
 // ---------------------------------------------------------------------------
@@ -217,8 +233,7 @@ __device__ __forceinline__ void displaced_row(const MeasureArgs &a, int row, con
 #pragma unroll
     for (int s = 0; s < DMAX; ++s)
         if (s < d) Z += (double)w[s];
-    const uint64_t n = a.n_base + (uint64_t)row;
-    const double thr = sample_uniform(a.seed, n, a.k, a.job) * Z;
+    const double thr = a.disp_u[row] * Z;
     int sstar = d - 1;
     float ws = 0.f;
     double C = 0.0;
@@ -269,12 +284,10 @@ __device__ __forceinline__ void displaced_row(const MeasureArgs &a, int row, con
     for (int i = 2 * chi_r + lane; i < a.K_next; i += 32) store_next(a, grow, i, 0.f);
 }
 
-__device__ __forceinline__ void build_D(const MeasureArgs &a, int row, float2 *D, int lane) {
-    const int d = a.d;
-    const float2 mu = a.mu[row];
-    const ffloat mx = neg_abs2(mu);
-    const float g = expf(0.5f * (mx.hi + mx.lo));
-    for (int e = lane; e < d * d; e += 32) D[e] = displacement_entry(mu, mx, g, e / d, e % d, d, a.disp_tab);
+__device__ __forceinline__ void load_D(const MeasureArgs &a, int row, float2 *D, int lane) {
+    const int dd = a.d * a.d;
+    const float2 *src = a.disp_D + (int64_t)row * dd;
+    for (int e = lane; e < dd; e += 32) D[e] = src[e];
 }
 
 // Unstaged fallback (rows wider than the register-resident kernel takes): one row per warp, the
@@ -285,7 +298,7 @@ __global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(cons
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row = blockIdx.x * DISP_WARPS + warp;
     if (row >= a.rows) return;
-    build_D(a, row, Dsh[warp], lane);
+    load_D(a, row, Dsh[warp], lane);
     __syncwarp();
     displaced_row<DMAX, false>(a, row, a.Y + (int64_t)row * a.ldY, Dsh[warp], lane);
 }
@@ -306,7 +319,16 @@ __global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const Measu
     const int d = a.d, chi_r = a.chi_r;
     const int64_t Cs = a.Cs;
     const float *yrow = a.Y + (int64_t)row * a.ldY;
-    // all loads of the row first (independent, coalesced across the block)
+    // this row's matrix entries and uniform (prep kernel), then all loads of the row (independent,
+    // coalesced across the block)
+    const int dd = d * d;
+    float2 Dmine[(DMAX * DMAX + 31) / 32];
+#pragma unroll
+    for (int q = 0; q < (DMAX * DMAX + 31) / 32; ++q) {
+        const int e = tid + 32 * q;
+        Dmine[q] = (tid < 32 && e < dd) ? a.disp_D[(int64_t)row * dd + e] : make_float2(0.f, 0.f);
+    }
+    const double u = tid == 0 ? a.disp_u[row] : 0.0;
     float2 y[VPT][DMAX];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -316,7 +338,11 @@ __global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const Measu
             y[v][t] = (t < d && b < chi_r) ? make_float2(__ldcs(yrow + t * Cs + b), __ldcs(yrow + t * Cs + chi_r + b))
                                           : make_float2(0.f, 0.f);
     }
-    if (tid < 32) build_D(a, row, D, lane);
+    if (tid < 32) {
+#pragma unroll
+        for (int q = 0; q < (DMAX * DMAX + 31) / 32; ++q)
+            if (tid + 32 * q < dd) D[tid + 32 * q] = Dmine[q];
+    }
     __syncthreads();
     // pass 1: partial w_s over this thread's columns
     float w[DMAX];
@@ -366,8 +392,7 @@ __global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const Measu
             C[s] = acc;
         }
         const double Z = acc;
-        const uint64_t n = a.n_base + (uint64_t)row;
-        const double thr = sample_uniform(a.seed, n, a.k, a.job) * Z;
+        const double thr = u * Z;
         int sstar = d - 1;
 #pragma unroll
         for (int s = DMAX - 1; s >= 0; --s)
@@ -457,6 +482,7 @@ void launch_displaced_variant(const MeasureArgs &a, cudaStream_t st) {
 void launch_measure_displaced(const MeasureArgs &a, int num_sms, cudaStream_t st) {
     (void)num_sms;
     if (a.rows <= 0) return;
+    displaced_prep_kernel<<<(a.rows + 255) / 256, 256, 0, st>>>(a);
     if (a.d <= 4) launch_displaced_variant<4>(a, st);
     else if (a.d <= 8) launch_displaced_variant<8>(a, st);
     else launch_displaced_variant<kMaxDisplacedD>(a, st);

@@ -103,6 +103,8 @@ struct MeasureArgs {
     uint8_t *V8 = nullptr;    // FP8 path: E4M3 row scaled by a per-row power of two
     const float2 *mu = nullptr;  // displaced measurement: amplitude of each row of this micro-batch
     const float *disp_tab = nullptr;   // displaced measurement: constants of the displacement entries
+    float2 *disp_D = nullptr;          // displaced measurement: per-row matrices [row][d*d] (prep kernel output)
+    double *disp_u = nullptr;          // displaced measurement: per-row uniforms (prep kernel output)
     uint8_t *outcomes;        // [rows] outcome bytes of this site (site-major buffer slice)
     double *logp;             // [rows] accumulated log-probability
     double *trace;            // nullable: [trace_rows][d] normalised conditionals of this site
@@ -123,7 +125,8 @@ void build_displacement_table(int d, float *tab /* d * d * (2d + 1) */);
 void launch_displacement(const float2 *mu, int64_t N, int d, const float *tab, float2 *D, int num_sms,
                          cudaStream_t st);
 // Measurement with the physical index of each row mixed by D(a.mu[row]) first (a.mu != nullptr,
-// d <= kMaxDisplacedD, FP32 or BF16-plane next rows).
+// d <= kMaxDisplacedD, FP32 or BF16-plane next rows).  Launches a prep kernel (one thread per row:
+// the row's matrix and uniform into a.disp_D / a.disp_u) and the measurement kernel.
 void launch_measure_displaced(const MeasureArgs &a, int num_sms, cudaStream_t st);
 
 // Self-test: one bounded mbarrier wait that nothing completes (status, device time waited).
