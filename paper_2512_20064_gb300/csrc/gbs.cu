@@ -443,6 +443,197 @@ __global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const Measu
     (void)s_sstar;
 }
 
+// Vectorised register-resident variant (chi_r a multiple of 4): thread j holds the four consecutive
+// columns b = 4g .. 4g+3 of groups g = j + T v (v < G) of all d blocks, loaded as 16-byte vectors,
+// and writes the next row with 16-byte (FP32) or 8-byte (BF16 plane) stores: four times fewer
+// memory and address instructions per byte than the scalar variant.
+__device__ __forceinline__ void store_next4(const MeasureArgs &a, int64_t grow, int i, float4 x) {
+    if (a.V32) {
+        *reinterpret_cast<float4 *>(a.V32 + grow * a.ld_next + i) = x;
+        return;
+    }
+    const float v[4] = {x.x, x.y, x.z, x.w};
+    __align__(8) __nv_bfloat16 p0[4], p1[4], p2[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) write_planes(v[e], a.nplanes, p0[e], p1[e], p2[e]);
+    const int64_t off = grow * a.ld_next + i;
+    *reinterpret_cast<uint2 *>(a.Vp[0] + off) = *reinterpret_cast<const uint2 *>(p0);
+    *reinterpret_cast<uint2 *>(a.Vp[1] + off) = *reinterpret_cast<const uint2 *>(p1);
+    if (a.nplanes > 2) *reinterpret_cast<uint2 *>(a.Vp[2] + off) = *reinterpret_cast<const uint2 *>(p2);
+}
+
+template <int DMAX, int G>
+__global__ void __launch_bounds__(256) measure_displaced_vec4_kernel(const MeasureArgs a) {
+    __shared__ float2 D[DMAX * DMAX];
+    __shared__ float red[8][DMAX];
+    __shared__ float2 coef[DMAX];
+    const int row = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
+    const int d = a.d, chi_r = a.chi_r, ngroups = chi_r >> 2;
+    const int64_t Cs = a.Cs;
+    const float *yrow = a.Y + (int64_t)row * a.ldY;
+    const int dd = d * d;
+    float2 Dmine[(DMAX * DMAX + 31) / 32];
+#pragma unroll
+    for (int q = 0; q < (DMAX * DMAX + 31) / 32; ++q) {
+        const int e = tid + 32 * q;
+        Dmine[q] = (tid < 32 && e < dd) ? a.disp_D[(int64_t)row * dd + e] : make_float2(0.f, 0.f);
+    }
+    const double u = tid == 0 ? a.disp_u[row] : 0.0;
+    float4 yr[G][DMAX], yi[G][DMAX];
+#pragma unroll
+    for (int v = 0; v < G; ++v) {
+        const int g = tid + T * v;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) {
+            if (t < d && g < ngroups) {
+                yr[v][t] = __ldcs(reinterpret_cast<const float4 *>(yrow + t * Cs) + g);
+                yi[v][t] = __ldcs(reinterpret_cast<const float4 *>(yrow + t * Cs + chi_r) + g);
+            } else {
+                yr[v][t] = make_float4(0.f, 0.f, 0.f, 0.f);
+                yi[v][t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    if (tid < 32) {
+#pragma unroll
+        for (int q = 0; q < (DMAX * DMAX + 31) / 32; ++q)
+            if (tid + 32 * q < dd) D[tid + 32 * q] = Dmine[q];
+    }
+    __syncthreads();
+    float w[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) w[s] = 0.f;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        if (s >= d) break;
+        float2 c[DMAX];
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) c[t] = t < d ? D[s * d + t] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int v = 0; v < G; ++v) {
+            float4 zr = make_float4(0.f, 0.f, 0.f, 0.f), zi = zr;
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t) {
+                if (t >= d) break;
+                zr.x = fmaf(c[t].x, yr[v][t].x, fmaf(-c[t].y, yi[v][t].x, zr.x));
+                zr.y = fmaf(c[t].x, yr[v][t].y, fmaf(-c[t].y, yi[v][t].y, zr.y));
+                zr.z = fmaf(c[t].x, yr[v][t].z, fmaf(-c[t].y, yi[v][t].z, zr.z));
+                zr.w = fmaf(c[t].x, yr[v][t].w, fmaf(-c[t].y, yi[v][t].w, zr.w));
+                zi.x = fmaf(c[t].x, yi[v][t].x, fmaf(c[t].y, yr[v][t].x, zi.x));
+                zi.y = fmaf(c[t].x, yi[v][t].y, fmaf(c[t].y, yr[v][t].y, zi.y));
+                zi.z = fmaf(c[t].x, yi[v][t].z, fmaf(c[t].y, yr[v][t].z, zi.z));
+                zi.w = fmaf(c[t].x, yi[v][t].w, fmaf(c[t].y, yr[v][t].w, zi.w));
+            }
+            w[s] += zr.x * zr.x + zr.y * zr.y + zr.z * zr.z + zr.w * zr.w + zi.x * zi.x + zi.y * zi.y +
+                    zi.z * zi.z + zi.w * zi.w;
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w[s] += __shfl_xor_sync(0xffffffffu, w[s], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) red[warp][s] = w[s];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int nw = T >> 5;
+        float ws32[DMAX];
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) {
+            float acc = 0.f;
+            for (int q = 0; q < nw; ++q) acc += red[q][s];
+            ws32[s] = acc;
+        }
+        double C[DMAX];
+        double acc = 0.0;
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) {
+            if (s < d) acc += (double)ws32[s];
+            C[s] = acc;
+        }
+        const double Z = acc;
+        const double thr = u * Z;
+        int sstar = d - 1;
+#pragma unroll
+        for (int s = DMAX - 1; s >= 0; --s)
+            if (s < d - 1 && C[s] >= thr) sstar = s;
+        float wsel = 0.f;
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s)
+            if (s == sstar) wsel = ws32[s];
+        const bool ok = (Z > 0.0) && isfinite(Z) && (wsel > 0.f);
+        const int64_t grow = a.row0 + row;
+        a.outcomes[row] = (uint8_t)sstar;
+        if (ok) a.logp[grow] += (double)(logf(wsel) - logf((float)Z));
+        else atomicExch(a.err, (int)kDevNumeric);
+        if (a.trace && grow < a.trace_rows) {
+#pragma unroll
+            for (int s = 0; s < DMAX; ++s)
+                if (s < d) a.trace[grow * d + s] = ok ? (double)ws32[s] / Z : 0.0;
+        }
+        const float scale = ok ? rsqrtf(wsel) : 0.f;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) {
+            const float2 e = t < d ? D[sstar * d + t] : make_float2(0.f, 0.f);
+            coef[t] = make_float2(e.x * scale, e.y * scale);
+        }
+    }
+    __syncthreads();
+    const int64_t grow = a.row0 + row;
+    float2 c[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) c[t] = coef[t];
+#pragma unroll
+    for (int v = 0; v < G; ++v) {
+        const int g = tid + T * v;
+        if (g >= ngroups) break;
+        float4 zr = make_float4(0.f, 0.f, 0.f, 0.f), zi = zr;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) {
+            if (t >= d) break;
+            zr.x = fmaf(c[t].x, yr[v][t].x, fmaf(-c[t].y, yi[v][t].x, zr.x));
+            zr.y = fmaf(c[t].x, yr[v][t].y, fmaf(-c[t].y, yi[v][t].y, zr.y));
+            zr.z = fmaf(c[t].x, yr[v][t].z, fmaf(-c[t].y, yi[v][t].z, zr.z));
+            zr.w = fmaf(c[t].x, yr[v][t].w, fmaf(-c[t].y, yi[v][t].w, zr.w));
+            zi.x = fmaf(c[t].x, yi[v][t].x, fmaf(c[t].y, yr[v][t].x, zi.x));
+            zi.y = fmaf(c[t].x, yi[v][t].y, fmaf(c[t].y, yr[v][t].y, zi.y));
+            zi.z = fmaf(c[t].x, yi[v][t].z, fmaf(c[t].y, yr[v][t].z, zi.z));
+            zi.w = fmaf(c[t].x, yi[v][t].w, fmaf(c[t].y, yr[v][t].w, zi.w));
+        }
+        store_next4(a, grow, 4 * g, zr);
+        store_next4(a, grow, chi_r + 4 * g, zi);
+    }
+    for (int i = 2 * chi_r + 4 * tid; i < a.K_next; i += 4 * T)
+        store_next4(a, grow, i, make_float4(0.f, 0.f, 0.f, 0.f));
+}
+
+template <int DMAX>
+bool launch_vec4_variant(const MeasureArgs &a, cudaStream_t st) {
+    if constexpr (DMAX > 8) {
+        return false;
+    } else {
+        if ((a.chi_r & 3) || (a.K_next & 3) || (a.ld_next & 3)) return false;
+        const int ngroups = a.chi_r >> 2;
+        for (int cap : {128, 256}) {
+            for (int G : {1, 2}) {
+                if (G * DMAX > 8) break;
+                const int need = (ngroups + G - 1) / G;
+                if (need > cap) continue;
+                const int T = std::max(32, (need + 31) / 32 * 32);
+                const dim3 grid((unsigned)a.rows);
+                if (G == 1) measure_displaced_vec4_kernel<DMAX, 1><<<grid, T, 0, st>>>(a);
+                else if constexpr (2 * DMAX <= 8) measure_displaced_vec4_kernel<DMAX, 2><<<grid, T, 0, st>>>(a);
+                return true;
+            }
+        }
+        return false;
+    }
+}
+
 // Threads per block and columns per thread of the register-resident kernel: the fewest columns per
 // thread (VPT in {1, 2, 4, 8}) that cover chi_r with at most 128 threads (else 256), under a register
 // cap of VPT * DMAX <= 32 complex values; 0 if none fits (the unstaged kernel runs instead).
@@ -474,6 +665,7 @@ bool launch_rows_variant(const MeasureArgs &a, cudaStream_t st) {
 
 template <int DMAX>
 void launch_displaced_variant(const MeasureArgs &a, cudaStream_t st) {
+    if (launch_vec4_variant<DMAX>(a, st)) return;
     if (launch_rows_variant<DMAX>(a, st)) return;
     const int grid = (a.rows + DISP_WARPS - 1) / DISP_WARPS;
     measure_displaced_kernel<DMAX><<<grid, DISP_WARPS * 32, 0, st>>>(a);
