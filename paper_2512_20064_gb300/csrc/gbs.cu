@@ -303,32 +303,111 @@ __global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(cons
     displaced_row<DMAX, false>(a, row, a.Y + (int64_t)row * a.ldY, Dsh[warp], lane);
 }
 
-// Register-resident: one thread block per sample row; thread j holds the columns b = j + T v
-// (v < VPT) of all d blocks in registers, so the row crosses HBM once and both passes read
-// registers.  Small blocks (T = 32 .. 256 threads) keep many rows in flight per SM.  The lane sums
-// are reduced in FP32 (warp shuffles, then across warps in shared memory); one thread takes the
-// FP64 draw.
+// ---------------------------------------------------------------------------
+// Register-resident displaced measurement: one thread block per sample row.  Thread j holds columns
+// of all d blocks of the row in registers (four consecutive columns per 16-byte load in the vector
+// variant, single columns in the scalar one), so the row crosses HBM once and both passes read
+// registers.  The d x d matrix of the row (prep kernel) is read by every thread through L1.
+// The lane sums are reduced in FP32 (shuffles, then across warps through shared memory: the only
+// block barrier), and every thread takes the same draw:
+//   * fast path in FP32: prefix sums C_s and threshold u Z.  Their rounding error is below
+//     16 * 2^-24 Z for d <= 16, so when every |C_s - u Z| exceeds 1e-5 Z the FP32 comparison
+//     decides exactly as the FP64 one on the same sums;
+//   * otherwise (about 2 d 1e-5 of the draws) the prefix sums and the threshold in FP64.
+// This keeps GB300's narrow FP64 pipes off the common path while the decision stays the FP64 one.
+// ---------------------------------------------------------------------------
+template <int DMAX>
+__device__ __forceinline__ int displaced_draw(const float (&w)[DMAX], int d, double u, float &wsel, float &Z32) {
+    float C32[DMAX];
+    float acc = 0.f;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        if (s < d) acc += w[s];
+        C32[s] = acc;
+    }
+    Z32 = acc;
+    const float thr32 = (float)u * acc;
+    const float band = 1e-5f * acc;
+    int sstar = d - 1;
+    bool near = false;
+#pragma unroll
+    for (int s = DMAX - 1; s >= 0; --s) {
+        if (s < d - 1) {
+            if (C32[s] >= thr32) sstar = s;
+            if (fabsf(C32[s] - thr32) <= band) near = true;
+        }
+    }
+    if (near) {
+        double C[DMAX];
+        double a64 = 0.0;
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) {
+            if (s < d) a64 += (double)w[s];
+            C[s] = a64;
+        }
+        const double thr = u * a64;
+        sstar = d - 1;
+#pragma unroll
+        for (int s = DMAX - 1; s >= 0; --s)
+            if (s < d - 1 && C[s] >= thr) sstar = s;
+    }
+    wsel = 0.f;
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s)
+        if (s == sstar) wsel = w[s];
+    return sstar;
+}
+
+// Block-wide FP32 reduction of w[DMAX] (same summation order in every thread, so every thread ends
+// with identical sums).
+template <int DMAX>
+__device__ __forceinline__ void block_reduce_w(float (&w)[DMAX], float (*red)[DMAX], int lane, int warp, int nw) {
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w[s] += __shfl_xor_sync(0xffffffffu, w[s], o);
+    }
+    if (nw == 1) return;
+    if (lane == 0) {
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) red[warp][s] = w[s];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        float acc = 0.f;
+        for (int q = 0; q < nw; ++q) acc += red[q][s];
+        w[s] = acc;
+    }
+}
+
+// Outcome, log-probability, trace (thread 0 of the block).
+template <int DMAX>
+__device__ __forceinline__ void displaced_outputs(const MeasureArgs &a, int row, int sstar, float wsel, float Z32,
+                                                  const float (&w)[DMAX]) {
+    const int d = a.d;
+    const bool ok = (Z32 > 0.f) && isfinite(Z32) && (wsel > 0.f);
+    const int64_t grow = a.row0 + row;
+    a.outcomes[row] = (uint8_t)sstar;
+    if (ok) a.logp[grow] += (double)(logf(wsel) - logf(Z32));
+    else atomicExch(a.err, (int)kDevNumeric);
+    if (a.trace && grow < a.trace_rows) {
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s)
+            if (s < d) a.trace[grow * d + s] = ok ? (double)w[s] / (double)Z32 : 0.0;
+    }
+}
+
 template <int DMAX, int VPT>
 __global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const MeasureArgs a) {
-    __shared__ float2 D[DMAX * DMAX];
     __shared__ float red[8][DMAX];
-    __shared__ float2 coef[DMAX];
-    __shared__ int s_sstar;
     const int row = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
-    const int d = a.d, chi_r = a.chi_r;
+    const int d = a.d, chi_r = a.chi_r, dd = d * d;
     const int64_t Cs = a.Cs;
     const float *yrow = a.Y + (int64_t)row * a.ldY;
-    // this row's matrix entries and uniform (prep kernel), then all loads of the row (independent,
-    // coalesced across the block)
-    const int dd = d * d;
-    float2 Dmine[(DMAX * DMAX + 31) / 32];
-#pragma unroll
-    for (int q = 0; q < (DMAX * DMAX + 31) / 32; ++q) {
-        const int e = tid + 32 * q;
-        Dmine[q] = (tid < 32 && e < dd) ? a.disp_D[(int64_t)row * dd + e] : make_float2(0.f, 0.f);
-    }
-    const double u = tid == 0 ? a.disp_u[row] : 0.0;
+    const float2 *Drow = a.disp_D + (int64_t)row * dd;
+    const double u = a.disp_u[row];
     float2 y[VPT][DMAX];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
@@ -338,93 +417,37 @@ __global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const Measu
             y[v][t] = (t < d && b < chi_r) ? make_float2(__ldcs(yrow + t * Cs + b), __ldcs(yrow + t * Cs + chi_r + b))
                                           : make_float2(0.f, 0.f);
     }
-    if (tid < 32) {
-#pragma unroll
-        for (int q = 0; q < (DMAX * DMAX + 31) / 32; ++q)
-            if (tid + 32 * q < dd) D[tid + 32 * q] = Dmine[q];
-    }
-    __syncthreads();
-    // pass 1: partial w_s over this thread's columns
     float w[DMAX];
 #pragma unroll
-    for (int s = 0; s < DMAX; ++s) w[s] = 0.f;
+    for (int s = 0; s < DMAX; ++s) {
+        w[s] = 0.f;
+        if (s >= d) continue;
+        float2 c[DMAX];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
+        for (int t = 0; t < DMAX; ++t) c[t] = t < d ? Drow[s * d + t] : make_float2(0.f, 0.f);
 #pragma unroll
-        for (int s = 0; s < DMAX; ++s) {
-            if (s >= d) break;
+        for (int v = 0; v < VPT; ++v) {
             float zr = 0.f, zi = 0.f;
 #pragma unroll
             for (int t = 0; t < DMAX; ++t) {
-                if (t >= d) break;
-                const float2 c = D[s * d + t];
-                zr = fmaf(c.x, y[v][t].x, fmaf(-c.y, y[v][t].y, zr));
-                zi = fmaf(c.x, y[v][t].y, fmaf(c.y, y[v][t].x, zi));
+                zr = fmaf(c[t].x, y[v][t].x, fmaf(-c[t].y, y[v][t].y, zr));
+                zi = fmaf(c[t].x, y[v][t].y, fmaf(c[t].y, y[v][t].x, zi));
             }
             w[s] = fmaf(zr, zr, fmaf(zi, zi, w[s]));
         }
     }
-#pragma unroll
-    for (int s = 0; s < DMAX; ++s) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w[s] += __shfl_xor_sync(0xffffffffu, w[s], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s) red[warp][s] = w[s];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const int nw = T >> 5;
-        float ws32[DMAX];
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s) {
-            float acc = 0.f;
-            for (int q = 0; q < nw; ++q) acc += red[q][s];
-            ws32[s] = acc;
-        }
-        // the draw in FP64: C_s in s order, s* = first s with C_s >= u Z, else d-1
-        double C[DMAX];
-        double acc = 0.0;
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s) {
-            if (s < d) acc += (double)ws32[s];
-            C[s] = acc;
-        }
-        const double Z = acc;
-        const double thr = u * Z;
-        int sstar = d - 1;
-#pragma unroll
-        for (int s = DMAX - 1; s >= 0; --s)
-            if (s < d - 1 && C[s] >= thr) sstar = s;
-        float wsel = 0.f;
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s)
-            if (s == sstar) wsel = ws32[s];
-        const bool ok = (Z > 0.0) && isfinite(Z) && (wsel > 0.f);
-        const int64_t grow = a.row0 + row;
-        a.outcomes[row] = (uint8_t)sstar;
-        if (ok) a.logp[grow] += (double)(logf(wsel) - logf((float)Z));
-        else atomicExch(a.err, (int)kDevNumeric);
-        if (a.trace && grow < a.trace_rows) {
-#pragma unroll
-            for (int s = 0; s < DMAX; ++s)
-                if (s < d) a.trace[grow * d + s] = ok ? (double)ws32[s] / Z : 0.0;
-        }
-        const float scale = ok ? rsqrtf(wsel) : 0.f;
-        s_sstar = sstar;
-#pragma unroll
-        for (int t = 0; t < DMAX; ++t) {
-            const float2 e = t < d ? D[sstar * d + t] : make_float2(0.f, 0.f);
-            coef[t] = make_float2(e.x * scale, e.y * scale);
-        }
-    }
-    __syncthreads();
-    // pass 2 from registers: next left row = (sum_t D[s*][t] y_t) / sqrt(w_{s*})
-    const int64_t grow = a.row0 + row;
+    block_reduce_w<DMAX>(w, red, lane, warp, T >> 5);
+    float wsel, Z32;
+    const int sstar = displaced_draw<DMAX>(w, d, u, wsel, Z32);
+    if (tid == 0) displaced_outputs<DMAX>(a, row, sstar, wsel, Z32, w);
+    const float scale = wsel > 0.f && Z32 > 0.f && isfinite(Z32) ? rsqrtf(wsel) : 0.f;
     float2 c[DMAX];
 #pragma unroll
-    for (int t = 0; t < DMAX; ++t) c[t] = coef[t];
+    for (int t = 0; t < DMAX; ++t) {
+        const float2 e = t < d ? Drow[sstar * d + t] : make_float2(0.f, 0.f);
+        c[t] = make_float2(e.x * scale, e.y * scale);
+    }
+    const int64_t grow = a.row0 + row;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
         const int b = tid + T * v;
@@ -432,7 +455,6 @@ __global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const Measu
         float zr = 0.f, zi = 0.f;
 #pragma unroll
         for (int t = 0; t < DMAX; ++t) {
-            if (t >= d) break;
             zr = fmaf(c[t].x, y[v][t].x, fmaf(-c[t].y, y[v][t].y, zr));
             zi = fmaf(c[t].x, y[v][t].y, fmaf(c[t].y, y[v][t].x, zi));
         }
@@ -440,13 +462,11 @@ __global__ void __launch_bounds__(256) measure_displaced_rows_kernel(const Measu
         store_next(a, grow, chi_r + b, zi);
     }
     for (int i = 2 * chi_r + tid; i < a.K_next; i += T) store_next(a, grow, i, 0.f);
-    (void)s_sstar;
 }
 
-// Vectorised register-resident variant (chi_r a multiple of 4): thread j holds the four consecutive
-// columns b = 4g .. 4g+3 of groups g = j + T v (v < G) of all d blocks, loaded as 16-byte vectors,
-// and writes the next row with 16-byte (FP32) or 8-byte (BF16 plane) stores: four times fewer
-// memory and address instructions per byte than the scalar variant.
+// Vectorised variant (chi_r a multiple of 4): thread j holds the four consecutive columns
+// b = 4g .. 4g+3 of groups g = j + T v (v < G), loaded as 16-byte vectors, and writes the next row
+// with 16-byte (FP32) or 8-byte (BF16 plane) stores.
 __device__ __forceinline__ void store_next4(const MeasureArgs &a, int64_t grow, int i, float4 x) {
     if (a.V32) {
         *reinterpret_cast<float4 *>(a.V32 + grow * a.ld_next + i) = x;
@@ -462,24 +482,27 @@ __device__ __forceinline__ void store_next4(const MeasureArgs &a, int64_t grow, 
     if (a.nplanes > 2) *reinterpret_cast<uint2 *>(a.Vp[2] + off) = *reinterpret_cast<const uint2 *>(p2);
 }
 
+__device__ __forceinline__ void cmac4(float2 c, const float4 &yr, const float4 &yi, float4 &zr, float4 &zi) {
+    zr.x = fmaf(c.x, yr.x, fmaf(-c.y, yi.x, zr.x));
+    zr.y = fmaf(c.x, yr.y, fmaf(-c.y, yi.y, zr.y));
+    zr.z = fmaf(c.x, yr.z, fmaf(-c.y, yi.z, zr.z));
+    zr.w = fmaf(c.x, yr.w, fmaf(-c.y, yi.w, zr.w));
+    zi.x = fmaf(c.x, yi.x, fmaf(c.y, yr.x, zi.x));
+    zi.y = fmaf(c.x, yi.y, fmaf(c.y, yr.y, zi.y));
+    zi.z = fmaf(c.x, yi.z, fmaf(c.y, yr.z, zi.z));
+    zi.w = fmaf(c.x, yi.w, fmaf(c.y, yr.w, zi.w));
+}
+
 template <int DMAX, int G>
 __global__ void __launch_bounds__(256) measure_displaced_vec4_kernel(const MeasureArgs a) {
-    __shared__ float2 D[DMAX * DMAX];
     __shared__ float red[8][DMAX];
-    __shared__ float2 coef[DMAX];
     const int row = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = blockDim.x;
-    const int d = a.d, chi_r = a.chi_r, ngroups = chi_r >> 2;
+    const int d = a.d, chi_r = a.chi_r, ngroups = chi_r >> 2, dd = d * d;
     const int64_t Cs = a.Cs;
     const float *yrow = a.Y + (int64_t)row * a.ldY;
-    const int dd = d * d;
-    float2 Dmine[(DMAX * DMAX + 31) / 32];
-#pragma unroll
-    for (int q = 0; q < (DMAX * DMAX + 31) / 32; ++q) {
-        const int e = tid + 32 * q;
-        Dmine[q] = (tid < 32 && e < dd) ? a.disp_D[(int64_t)row * dd + e] : make_float2(0.f, 0.f);
-    }
-    const double u = tid == 0 ? a.disp_u[row] : 0.0;
+    const float2 *Drow = a.disp_D + (int64_t)row * dd;
+    const double u = a.disp_u[row];
     float4 yr[G][DMAX], yi[G][DMAX];
 #pragma unroll
     for (int v = 0; v < G; ++v) {
@@ -495,115 +518,41 @@ __global__ void __launch_bounds__(256) measure_displaced_vec4_kernel(const Measu
             }
         }
     }
-    if (tid < 32) {
-#pragma unroll
-        for (int q = 0; q < (DMAX * DMAX + 31) / 32; ++q)
-            if (tid + 32 * q < dd) D[tid + 32 * q] = Dmine[q];
-    }
-    __syncthreads();
     float w[DMAX];
 #pragma unroll
-    for (int s = 0; s < DMAX; ++s) w[s] = 0.f;
-#pragma unroll
     for (int s = 0; s < DMAX; ++s) {
-        if (s >= d) break;
-        float2 c[DMAX];
-#pragma unroll
-        for (int t = 0; t < DMAX; ++t) c[t] = t < d ? D[s * d + t] : make_float2(0.f, 0.f);
+        w[s] = 0.f;
+        if (s >= d) continue;
 #pragma unroll
         for (int v = 0; v < G; ++v) {
             float4 zr = make_float4(0.f, 0.f, 0.f, 0.f), zi = zr;
 #pragma unroll
-            for (int t = 0; t < DMAX; ++t) {
-                if (t >= d) break;
-                zr.x = fmaf(c[t].x, yr[v][t].x, fmaf(-c[t].y, yi[v][t].x, zr.x));
-                zr.y = fmaf(c[t].x, yr[v][t].y, fmaf(-c[t].y, yi[v][t].y, zr.y));
-                zr.z = fmaf(c[t].x, yr[v][t].z, fmaf(-c[t].y, yi[v][t].z, zr.z));
-                zr.w = fmaf(c[t].x, yr[v][t].w, fmaf(-c[t].y, yi[v][t].w, zr.w));
-                zi.x = fmaf(c[t].x, yi[v][t].x, fmaf(c[t].y, yr[v][t].x, zi.x));
-                zi.y = fmaf(c[t].x, yi[v][t].y, fmaf(c[t].y, yr[v][t].y, zi.y));
-                zi.z = fmaf(c[t].x, yi[v][t].z, fmaf(c[t].y, yr[v][t].z, zi.z));
-                zi.w = fmaf(c[t].x, yi[v][t].w, fmaf(c[t].y, yr[v][t].w, zi.w));
-            }
+            for (int t = 0; t < DMAX; ++t)
+                if (t < d) cmac4(Drow[s * d + t], yr[v][t], yi[v][t], zr, zi);
             w[s] += zr.x * zr.x + zr.y * zr.y + zr.z * zr.z + zr.w * zr.w + zi.x * zi.x + zi.y * zi.y +
                     zi.z * zi.z + zi.w * zi.w;
         }
     }
-#pragma unroll
-    for (int s = 0; s < DMAX; ++s) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w[s] += __shfl_xor_sync(0xffffffffu, w[s], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s) red[warp][s] = w[s];
-    }
-    __syncthreads();
-    if (tid == 0) {
-        const int nw = T >> 5;
-        float ws32[DMAX];
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s) {
-            float acc = 0.f;
-            for (int q = 0; q < nw; ++q) acc += red[q][s];
-            ws32[s] = acc;
-        }
-        double C[DMAX];
-        double acc = 0.0;
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s) {
-            if (s < d) acc += (double)ws32[s];
-            C[s] = acc;
-        }
-        const double Z = acc;
-        const double thr = u * Z;
-        int sstar = d - 1;
-#pragma unroll
-        for (int s = DMAX - 1; s >= 0; --s)
-            if (s < d - 1 && C[s] >= thr) sstar = s;
-        float wsel = 0.f;
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s)
-            if (s == sstar) wsel = ws32[s];
-        const bool ok = (Z > 0.0) && isfinite(Z) && (wsel > 0.f);
-        const int64_t grow = a.row0 + row;
-        a.outcomes[row] = (uint8_t)sstar;
-        if (ok) a.logp[grow] += (double)(logf(wsel) - logf((float)Z));
-        else atomicExch(a.err, (int)kDevNumeric);
-        if (a.trace && grow < a.trace_rows) {
-#pragma unroll
-            for (int s = 0; s < DMAX; ++s)
-                if (s < d) a.trace[grow * d + s] = ok ? (double)ws32[s] / Z : 0.0;
-        }
-        const float scale = ok ? rsqrtf(wsel) : 0.f;
-#pragma unroll
-        for (int t = 0; t < DMAX; ++t) {
-            const float2 e = t < d ? D[sstar * d + t] : make_float2(0.f, 0.f);
-            coef[t] = make_float2(e.x * scale, e.y * scale);
-        }
-    }
-    __syncthreads();
-    const int64_t grow = a.row0 + row;
+    block_reduce_w<DMAX>(w, red, lane, warp, T >> 5);
+    float wsel, Z32;
+    const int sstar = displaced_draw<DMAX>(w, d, u, wsel, Z32);
+    if (tid == 0) displaced_outputs<DMAX>(a, row, sstar, wsel, Z32, w);
+    const float scale = wsel > 0.f && Z32 > 0.f && isfinite(Z32) ? rsqrtf(wsel) : 0.f;
     float2 c[DMAX];
 #pragma unroll
-    for (int t = 0; t < DMAX; ++t) c[t] = coef[t];
+    for (int t = 0; t < DMAX; ++t) {
+        const float2 e = t < d ? Drow[sstar * d + t] : make_float2(0.f, 0.f);
+        c[t] = make_float2(e.x * scale, e.y * scale);
+    }
+    const int64_t grow = a.row0 + row;
 #pragma unroll
     for (int v = 0; v < G; ++v) {
         const int g = tid + T * v;
         if (g >= ngroups) break;
         float4 zr = make_float4(0.f, 0.f, 0.f, 0.f), zi = zr;
 #pragma unroll
-        for (int t = 0; t < DMAX; ++t) {
-            if (t >= d) break;
-            zr.x = fmaf(c[t].x, yr[v][t].x, fmaf(-c[t].y, yi[v][t].x, zr.x));
-            zr.y = fmaf(c[t].x, yr[v][t].y, fmaf(-c[t].y, yi[v][t].y, zr.y));
-            zr.z = fmaf(c[t].x, yr[v][t].z, fmaf(-c[t].y, yi[v][t].z, zr.z));
-            zr.w = fmaf(c[t].x, yr[v][t].w, fmaf(-c[t].y, yi[v][t].w, zr.w));
-            zi.x = fmaf(c[t].x, yi[v][t].x, fmaf(c[t].y, yr[v][t].x, zi.x));
-            zi.y = fmaf(c[t].x, yi[v][t].y, fmaf(c[t].y, yr[v][t].y, zi.y));
-            zi.z = fmaf(c[t].x, yi[v][t].z, fmaf(c[t].y, yr[v][t].z, zi.z));
-            zi.w = fmaf(c[t].x, yi[v][t].w, fmaf(c[t].y, yr[v][t].w, zi.w));
-        }
+        for (int t = 0; t < DMAX; ++t)
+            if (t < d) cmac4(c[t], yr[v][t], yi[v][t], zr, zi);
         store_next4(a, grow, 4 * g, zr);
         store_next4(a, grow, chi_r + 4 * g, zi);
     }
@@ -618,7 +567,8 @@ bool launch_vec4_variant(const MeasureArgs &a, cudaStream_t st) {
     } else {
         if ((a.chi_r & 3) || (a.K_next & 3) || (a.ld_next & 3)) return false;
         const int ngroups = a.chi_r >> 2;
-        for (int cap : {128, 256}) {
+        // one warp per row when G groups per thread cover the row, else up to 256 threads
+        for (int cap : {32, 128, 256}) {
             for (int G : {1, 2}) {
                 if (G * DMAX > 8) break;
                 const int need = (ngroups + G - 1) / G;
@@ -634,9 +584,8 @@ bool launch_vec4_variant(const MeasureArgs &a, cudaStream_t st) {
     }
 }
 
-// Threads per block and columns per thread of the register-resident kernel: the fewest columns per
-// thread (VPT in {1, 2, 4, 8}) that cover chi_r with at most 128 threads (else 256), under a register
-// cap of VPT * DMAX <= 32 complex values; 0 if none fits (the unstaged kernel runs instead).
+// Scalar variant: the fewest columns per thread (VPT in {1, 2, 4, 8}) that cover chi_r with at most
+// 128 threads (else 256), under a register cap of VPT * DMAX <= 32 complex values; false if none fits.
 template <int DMAX>
 bool launch_rows_variant(const MeasureArgs &a, cudaStream_t st) {
     const int chi_r = a.chi_r;
