@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="precision",
-                    choices=["precision", "plain", "tiny", "batching", "streaming", "displacement", "knee"])
+                    choices=["precision", "plain", "tiny", "batching", "streaming", "displacement", "knee",
+                             "dynamic"])
     ap.add_argument("--rows-cap", type=int, default=1024, help="batching: rows sampled per job")
     ap.add_argument("--jobs", type=int, default=64, help="batching: number of MPS")
     ap.add_argument("--precision", default=None, choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4", "fp8x1"])
@@ -628,6 +629,62 @@ def run_displacement(args, rank, ws, local):
     }
 
 
+def run_dynamic(args, rank, ws, local):
+    """Dynamic bond dimensions (Sec. 3.4.2): a Vidal-form chain with area-law Schmidt spectra
+    (M = 128, d = 4, bonds up to 256) truncated (a) to a fixed chi = 128 everywhere and (b) to the
+    per-bond counts of fastmps_bond_filter with the same maximum discarded weight; both sampled
+    (N = 2^17 rows per step, BF16x2).  value = sample-sites/s of (b); the line also carries (a)."""
+    import torch
+
+    import paper_2512_20064_gb300 as F
+
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    precision = args.precision or "bf16x2"
+    M, d, chi_gen, chi, N = 128, 4, 256, 128, args.macro or (1 << 17)
+    t0 = time.perf_counter()
+    b, G, L = gen.area_law_vidal_chain(M, d, chi_gen, xi_max=40.0)
+    t_gen = time.perf_counter() - t0
+    dyn, disc = F.fastmps_bond_filter(b, L, d, chi)
+    fixed = [min(x, chi) for x in b]
+    out_s = torch.empty((N, M), dtype=torch.uint8, device=device)
+    out_l = torch.empty(N, dtype=torch.float64, device=device)
+    res = {}
+    for name, bonds in (("fixed", fixed), ("dynamic", dyn)):
+        stream = torch.cuda.Stream(device=local)
+        with F.Sampler(device=local, precision=precision, stream=stream) as s:
+            s.load_chain_vidal_truncated(G, L, bonds)
+            for i in range(args.warmup):
+                s.sample(bonds, d, N, 7, n0=(args.steps + i) * N, out_samples=out_s, out_logprob=out_l)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            flops = 0.0
+            with torch.cuda.stream(stream):
+                ev0.record(stream)
+            for i in range(args.steps):
+                s.sample(bonds, d, N, 7, n0=i * N, out_samples=out_s, out_logprob=out_l)
+                flops += s.stats()["flops_algorithmic"]
+            with torch.cuda.stream(stream):
+                ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+        res[name] = {"sample_sites_per_s": N * M * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "flops_algorithmic_per_step": flops / args.steps, "bond_sum": int(sum(bonds))}
+    fixed_err = max(float(np.sum(np.asarray(L[k][min(chi, len(L[k])):]) ** 2) / np.sum(np.asarray(L[k]) ** 2))
+                    for k in range(M - 1))
+    return {"metric": "sample-sites/s with dynamic bond dimensions", "value": res["dynamic"]["sample_sites_per_s"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["dynamic"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic (area-law Vidal chain)",
+            "config": {"workload": f"Vidal chain M={M} d={d}, bonds up to {chi_gen}, fixed chi={chi} vs "
+                                   f"fastmps_bond_filter, N={N} rows per step", "precision": precision},
+            "fixed_chi": res["fixed"], "dynamic": res["dynamic"],
+            "speedup_vs_fixed_chi": res["dynamic"]["sample_sites_per_s"] / res["fixed"]["sample_sites_per_s"],
+            "max_discarded_weight": {"fixed": fixed_err, "dynamic": float(max(disc))},
+            "setup_s": {"generate": t_gen}}
+
+
 def run_knee(args, rank, ws, local):
     """Micro-batch sweep (the paper's Sec. 4 parameter study, chi = 2000, d = 3): contraction throughput
     of one macro-batch of 2^16 rows as a function of the rows per contraction launch N2.  Shows where
@@ -669,8 +726,8 @@ def run_knee(args, rank, ws, local):
 def main():
     args = parse()
     rank, ws, local = dist_setup()
-    if args.workload == "knee" and args.impl == "ours":
-        line = run_knee(args, rank, ws, local)
+    if args.workload in ("knee", "dynamic") and args.impl == "ours":
+        line = (run_knee if args.workload == "knee" else run_dynamic)(args, rank, ws, local)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
