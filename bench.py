@@ -631,9 +631,10 @@ def run_displacement(args, rank, ws, local):
 
 def run_dynamic(args, rank, ws, local):
     """Dynamic bond dimensions (Sec. 3.4.2): a Vidal-form chain with area-law Schmidt spectra
-    (M = 128, d = 4, bonds up to 256) truncated (a) to a fixed chi = 128 everywhere and (b) to the
+    (M = 64, d = 4, bonds up to 1024) truncated (a) to a fixed chi = 512 everywhere and (b) to the
     per-bond counts of fastmps_bond_filter with the same maximum discarded weight; both sampled
-    (N = 2^17 rows per step, BF16x2).  value = sample-sites/s of (b); the line also carries (a)."""
+    (N = 2^16 rows per step, BF16x2; contraction-bound at these bonds).  value = sample-sites/s of (b);
+    the line also carries (a)."""
     import torch
 
     import paper_2512_20064_gb300 as F
@@ -641,10 +642,13 @@ def run_dynamic(args, rank, ws, local):
     torch.cuda.set_device(local)
     device = f"cuda:{local}"
     precision = args.precision or "bf16x2"
-    M, d, chi_gen, chi, N = 128, 4, 256, 128, args.macro or (1 << 17)
+    M, d, chi_gen, chi, N = 64, 4, 1024, 512, args.macro or (1 << 16)
     t0 = time.perf_counter()
-    b, G, L = gen.area_law_vidal_chain(M, d, chi_gen, xi_max=40.0)
+    b, G, L = gen.area_law_vidal_chain(M, d, chi_gen, xi_max=150.0, device=device if args.gen_device == "cuda"
+                                       else None)
+    torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
+    L = [l.cpu().numpy() if hasattr(l, "cpu") else l for l in L]
     dyn, disc = F.fastmps_bond_filter(b, L, d, chi)
     fixed = [min(x, chi) for x in b]
     out_s = torch.empty((N, M), dtype=torch.uint8, device=device)

@@ -329,16 +329,21 @@ def decaying_vidal_chain(M: int, d: int, chi: int, decay: float = 0.35, seed: in
     return bonds, gammas, lams
 
 
-def area_law_vidal_chain(M: int, d: int, chi: int, xi_max: float = 10.0, seed: int = 314):
+def area_law_vidal_chain(M: int, d: int, chi: int, xi_max: float = 10.0, seed: int = 314,
+                         device: str | None = None):
     """A chain in Vidal form whose Schmidt spectra decay fastest at the edges (Sec. 3.4.2: entanglement
     grows from the edges to the centre).
 
     Site k is a right-canonical isometry whose Gaussian is damped along the right bond index,
     ``exp(-b / xi_k)`` with ``xi_k = 1 + xi_max sin(pi (k+1) / M)``, before the QR; the Vidal form
-    (true Schmidt coefficients, descending) then comes from ``vidal_form``.  Returns
-    ``(bonds, Gammas, Lambdas)`` with ``bonds = bond_dims(M, d, chi)``.
+    (true Schmidt coefficients, descending) then comes from the SVD sweep of ``vidal_form``.  Returns
+    ``(bonds, Gammas, Lambdas)`` with ``bonds = bond_dims(M, d, chi)``.  ``device='cuda'`` draws the
+    Gaussians with a seeded torch generator and runs the QR and SVD sweep there (complex64 torch
+    tensors out) for chains whose host SVDs would take minutes.
     """
     bonds = bond_dims(M, d, chi)
+    if device is not None:
+        return bonds, *_area_law_vidal_torch(M, d, bonds, xi_max, seed, device)
     As = []
     for k in range(M):
         cl, cr = bonds[k], bonds[k + 1]
@@ -351,3 +356,37 @@ def area_law_vidal_chain(M: int, d: int, chi: int, xi_max: float = 10.0, seed: i
         As.append(np.ascontiguousarray(q.T.reshape(cl, d, cr)))
     gammas, lams = vidal_form(bonds, As)
     return bonds, gammas, lams
+
+
+def _area_law_vidal_torch(M, d, bonds, xi_max, seed, device):
+    """The same construction with torch on ``device``: damped Gaussian, QR, then the left-to-right SVD
+    sweep of ``vidal_form`` (complex64 Gammas, float64 Lambdas on the device)."""
+    import torch
+
+    R = torch.ones((1, 1), dtype=torch.complex128, device=device)
+    lam_prev = torch.ones(1, dtype=torch.float64, device=device)
+    gammas, lams = [], []
+    for k in range(M):
+        cl, cr = bonds[k], bonds[k + 1]
+        gen_ = torch.Generator(device=device)
+        gen_.manual_seed(int(seed + k))
+        g = torch.complex(torch.randn((d * cr, cl), generator=gen_, device=device, dtype=torch.float64),
+                          torch.randn((d * cr, cl), generator=gen_, device=device, dtype=torch.float64))
+        xi = 1.0 + xi_max * math.sin(math.pi * (k + 1) / M)
+        w = torch.exp(-torch.arange(cr, device=device, dtype=torch.float64) / xi).repeat(d)
+        q, r = torch.linalg.qr(g * w[:, None], mode="reduced")
+        dg = torch.diagonal(r)
+        q = q * (dg / dg.abs())[None, :]
+        A = q.transpose(0, 1).reshape(cl, d, cr)
+        T = torch.einsum("xa,asb->xsb", R, A).reshape(cl * d, cr)
+        U, S, Vh = torch.linalg.svd(T, full_matrices=False)
+        j = torch.argmax(Vh.abs(), dim=1)
+        ph = Vh[torch.arange(cr, device=device), j]
+        ph = ph / ph.abs()
+        U = U * ph[None, :]
+        Vh = Vh * ph.conj()[:, None]
+        gammas.append((U.reshape(cl, d, cr) / lam_prev[:, None, None]).to(torch.complex64).contiguous())
+        lams.append(S.clone())
+        R = S[:, None].to(torch.complex128) * Vh
+        lam_prev = S
+    return gammas, lams
