@@ -650,11 +650,12 @@ def run_dynamic(args, rank, ws, local):
     t_gen = time.perf_counter() - t0
     L = [l.cpu().numpy() if hasattr(l, "cpu") else l for l in L]
     dyn, disc = F.fastmps_bond_filter(b, L, d, chi)
+    dyn_al, disc_al = F.fastmps_bond_filter(b, L, d, chi, align=64)
     fixed = [min(x, chi) for x in b]
     out_s = torch.empty((N, M), dtype=torch.uint8, device=device)
     out_l = torch.empty(N, dtype=torch.float64, device=device)
     res = {}
-    for name, bonds in (("fixed", fixed), ("dynamic", dyn)):
+    for name, bonds in (("fixed", fixed), ("dynamic", dyn), ("dynamic_aligned", dyn_al)):
         stream = torch.cuda.Stream(device=local)
         with F.Sampler(device=local, precision=precision, stream=stream) as s:
             s.load_chain_vidal_truncated(G, L, bonds)
@@ -674,18 +675,22 @@ def run_dynamic(args, rank, ws, local):
             torch.cuda.synchronize()
             ms = ev0.elapsed_time(ev1)
         res[name] = {"sample_sites_per_s": N * M * args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
-                     "flops_algorithmic_per_step": flops / args.steps, "bond_sum": int(sum(bonds))}
+                     "flops_algorithmic_per_step": flops / args.steps, "bonds": [int(x) for x in bonds]}
     fixed_err = max(float(np.sum(np.asarray(L[k][min(chi, len(L[k])):]) ** 2) / np.sum(np.asarray(L[k]) ** 2))
                     for k in range(M - 1))
-    return {"metric": "sample-sites/s with dynamic bond dimensions", "value": res["dynamic"]["sample_sites_per_s"],
+    best = max(("dynamic", "dynamic_aligned"), key=lambda k: res[k]["sample_sites_per_s"])
+    return {"metric": "sample-sites/s with dynamic bond dimensions", "value": res[best]["sample_sites_per_s"],
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": res["dynamic"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": res[best]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic (area-law Vidal chain)",
             "config": {"workload": f"Vidal chain M={M} d={d}, bonds up to {chi_gen}, fixed chi={chi} vs "
                                    f"fastmps_bond_filter, N={N} rows per step", "precision": precision},
-            "fixed_chi": res["fixed"], "dynamic": res["dynamic"],
-            "speedup_vs_fixed_chi": res["dynamic"]["sample_sites_per_s"] / res["fixed"]["sample_sites_per_s"],
-            "max_discarded_weight": {"fixed": fixed_err, "dynamic": float(max(disc))},
+            "fixed_chi": res["fixed"], "dynamic": res["dynamic"], "dynamic_aligned_64": res["dynamic_aligned"],
+            "value_is": best,
+            "speedup_vs_fixed_chi": {k: res[k]["sample_sites_per_s"] / res["fixed"]["sample_sites_per_s"]
+                                     for k in ("dynamic", "dynamic_aligned")},
+            "max_discarded_weight": {"fixed": fixed_err, "dynamic": float(max(disc)),
+                                     "dynamic_aligned": float(max(disc_al))},
             "setup_s": {"generate": t_gen}}
 
 

@@ -292,17 +292,19 @@ int fastmps_sample_displaced(fastmps_handle h, int M, int d, const int *bond_dim
  *   chi       the fixed bond dimension of the reference filter (keep at most chi per bond).
  *   eps       discarded-weight budget per bond; eps <= 0 selects the largest discarded weight
  *             that keeping min(chi, n) coefficients incurs on any bond of this chain.
+ *   align     >= 1; kept counts are rounded up to a multiple of align (capped at min(chi, n)) --
+ *             1 keeps the least counts; a multiple of the contraction tile (e.g. 64) avoids padding.
  *   bond_out  M+1 ints: bond_out[k+1] = the least c in [1, min(chi, n)] whose discarded weight
  *             T_c / T_0 (T_c = sum_{j >= c} lambda_j^2, summed in FP64 from the last index down)
- *             is <= the budget (min(chi, n) if none), then raised left to right to
- *             ceil(bond_out[k] / d) so that d * chi_r >= chi_l holds at every site.
+ *             is <= the budget (min(chi, n) if none), rounded up to the alignment, then raised
+ *             left to right to ceil(bond_out[k] / d) so that d * chi_r >= chi_l holds at every site.
  *   discarded_out (nullable) M+1 doubles: the discarded weight of each bond (0 at the ends).
  * Returns FASTMPS_OK, FASTMPS_ERR_INVALID_ARG (null pointer, bad size, all-zero spectrum) or
  * FASTMPS_ERR_SHAPE (ends not 1).  Keeping the leading coefficients assumes each spectrum is
  * sorted in descending order, as Schmidt coefficients are.
  */
 int fastmps_bond_filter(int M, int d, const int *bond_in, const double *const *lambdas, int chi, double eps,
-                        int *bond_out, double *discarded_out);
+                        int align, int *bond_out, double *discarded_out);
 
 /*
  * Load the leading block Gamma[:keep_l, :, :keep_r], Lambda[:keep_r] of a Vidal-form site whose

@@ -21,6 +21,9 @@ summation order):
 * budget eps* = max over bonds of eps(min(chi, n)), or a given eps > 0;
 * kept count chi_b = the least c in [1, min(chi, n)] with eps(c) <= eps*
   (min(chi, n) if there is none);
+* alignment (optional, align > 1): chi_b is rounded up to a multiple of align,
+  capped at min(chi, n) -- keeping more coefficients only lowers the discarded
+  weight, and tile-aligned bonds waste no tensor-core work on padding;
 * isometry shapes: a left-to-right sweep raises chi_b to ceil(chi_{b-1} / d)
   (chi_0 = 1) so that d * chi_r >= chi_l holds at every site.
 """
@@ -45,7 +48,7 @@ def discarded_weight(lam, c: int) -> float:
     return T[c] / T[0]
 
 
-def filter_bonds(lams, d: int, chi: int, eps: float | None = None):
+def filter_bonds(lams, d: int, chi: int, eps: float | None = None, align: int = 1):
     """lams[k]: Schmidt coefficients right of site k (k = 0..M-1; the last is ignored).
 
     Returns (bonds[M+1], discarded[M+1], eps_star)."""
@@ -68,6 +71,8 @@ def filter_bonds(lams, d: int, chi: int, eps: float | None = None):
             if T[c] / T[0] <= eps_star:
                 keep = c
                 break
+        if align > 1:
+            keep = min(-(-keep // align) * align, caps[k])
         bonds[k + 1] = keep
     for k in range(M - 1):
         need = -(-bonds[k] // d)          # ceil(bonds[k] / d)

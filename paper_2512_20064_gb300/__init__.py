@@ -102,7 +102,8 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
                                                           ctypes.c_int, ctypes.c_int]
         lib.fastmps_load_site_vidal_truncated.restype = ctypes.c_int
         lib.fastmps_bond_filter.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p),
-                                            ctypes.c_int, ctypes.c_double, P(ctypes.c_int), ctypes.c_void_p]
+                                            ctypes.c_int, ctypes.c_double, ctypes.c_int, P(ctypes.c_int),
+                                            ctypes.c_void_p]
         lib.fastmps_bond_filter.restype = ctypes.c_int
         lib.fastmps_displacement.argtypes = [H, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
         lib.fastmps_displacement.restype = ctypes.c_int
@@ -257,7 +258,7 @@ def fastmps_load_site_vidal_truncated(h, k: int, Gamma, Lam, keep_l: int, keep_r
     del keep, lkeep
 
 
-def fastmps_bond_filter(bonds, lams, d: int, chi: int, eps: float = 0.0):
+def fastmps_bond_filter(bonds, lams, d: int, chi: int, eps: float = 0.0, align: int = 1):
     """Dynamic bond dimensions from the Schmidt spectra ``lams[k]`` (right of site k; host code, no GPU).
 
     Returns ``(bonds_out[M+1], discarded[M+1])``."""
@@ -268,7 +269,7 @@ def fastmps_bond_filter(bonds, lams, d: int, chi: int, eps: float = 0.0):
     ptrs = (ctypes.c_void_p * max(1, M - 1))(*[a.ctypes.data for a in keep])
     bo = (ctypes.c_int * (M + 1))()
     disc = np.zeros(M + 1, np.float64)
-    rc = lib.fastmps_bond_filter(M, d, bi, ptrs, int(chi), float(eps), bo, disc.ctypes.data)
+    rc = lib.fastmps_bond_filter(M, d, bi, ptrs, int(chi), float(eps), int(align), bo, disc.ctypes.data)
     _check(lib, None, rc)
     return [int(x) for x in bo], disc
 

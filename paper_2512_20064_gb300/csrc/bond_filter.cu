@@ -8,6 +8,10 @@
 // error over the bonds is unchanged while the edge bonds shrink, and with them
 // the per-site contraction cost 8 chi_l d chi_r.
 //
+// With align > 1 the kept counts are rounded up to a multiple of align (capped by chi and the
+// spectrum length): more coefficients only lower the discarded weight, and bond dimensions that are
+// multiples of the contraction tiles waste no tensor-core work on padding.
+//
 // Decisions are taken in FP64: T_c = sum_{j >= c} Lambda_j^2 is accumulated
 // from the last coefficient towards c, and the discarded weight of keeping c
 // of n coefficients is T_c / T_0.
@@ -19,8 +23,9 @@
 #include "../../include/fastmps.h"
 
 extern "C" int fastmps_bond_filter(int M, int d, const int *bond_in, const double *const *lambdas, int chi,
-                                   double eps, int *bond_out, double *discarded_out) {
-    if (M < 1 || d < 2 || chi < 1 || !bond_in || !bond_out || (M > 1 && !lambdas)) return FASTMPS_ERR_INVALID_ARG;
+                                   double eps, int align, int *bond_out, double *discarded_out) {
+    if (M < 1 || d < 2 || chi < 1 || align < 1 || !bond_in || !bond_out || (M > 1 && !lambdas))
+        return FASTMPS_ERR_INVALID_ARG;
     if (bond_in[0] != 1 || bond_in[M] != 1) return FASTMPS_ERR_SHAPE;
     for (int k = 1; k < M; ++k)
         if (bond_in[k] < 1 || !lambdas[k - 1]) return FASTMPS_ERR_INVALID_ARG;
@@ -55,6 +60,7 @@ extern "C" int fastmps_bond_filter(int M, int d, const int *bond_in, const doubl
                 keep = c;
                 break;
             }
+        if (align > 1) keep = std::min((keep + align - 1) / align * align, cap[k]);
         bond_out[k + 1] = keep;
     }
     // isometry shapes: d * chi_r >= chi_l at every site (left-to-right sweep)

@@ -19,12 +19,14 @@ def F():
     return F
 
 
-@pytest.mark.parametrize("M,d,chi_gen,chi,eps", [(40, 3, 64, 24, 0.0), (40, 3, 64, 64, 1e-4), (30, 4, 48, 8, 0.0),
-                                                  (25, 2, 32, 32, 0.0), (60, 3, 27, 20, 1e-6), (3, 5, 5, 2, 0.0)])
-def test_filter_matches_oracle(F, M, d, chi_gen, chi, eps):
+@pytest.mark.parametrize("M,d,chi_gen,chi,eps,align", [(40, 3, 64, 24, 0.0, 1), (40, 3, 64, 64, 1e-4, 1),
+                                                        (30, 4, 48, 8, 0.0, 1), (25, 2, 32, 32, 0.0, 1),
+                                                        (60, 3, 27, 20, 1e-6, 1), (3, 5, 5, 2, 0.0, 1),
+                                                        (40, 3, 64, 48, 0.0, 16), (30, 4, 48, 40, 1e-5, 8)])
+def test_filter_matches_oracle(F, M, d, chi_gen, chi, eps, align):
     b, G, L = gen.area_law_vidal_chain(M, d, chi_gen, seed=M + d)
-    got, disc = F.fastmps_bond_filter(b, L, d, chi, eps)
-    want, wdisc, es = BF.filter_bonds(L, d, chi, eps)
+    got, disc = F.fastmps_bond_filter(b, L, d, chi, eps, align)
+    want, wdisc, es = BF.filter_bonds(L, d, chi, eps, align)
     assert got == want
     assert np.array_equal(disc, np.asarray(wdisc))
     for k in range(M):
@@ -43,8 +45,9 @@ def test_filter_random_spectra(F):
             L[0] = np.ones(b[1])                        # flat spectrum
         chi = int(rng.integers(1, 35))
         eps = [0.0, 1e-9, 1e-3, 0.3][trial % 4]
-        got, disc = F.fastmps_bond_filter(b, L, d, chi, eps)
-        want, wdisc, _ = BF.filter_bonds(L, d, chi, eps)
+        align = [1, 4, 7, 32][(trial // 4) % 4]
+        got, disc = F.fastmps_bond_filter(b, L, d, chi, eps, align)
+        want, wdisc, _ = BF.filter_bonds(L, d, chi, eps, align)
         assert got == want, (trial, got, want)
         assert np.array_equal(disc, np.asarray(wdisc))
 

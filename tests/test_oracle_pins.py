@@ -227,6 +227,22 @@ def test_bond_filter_invariants():
             assert BF.discarded_weight(L[k], c - 1) > es
 
 
+def test_bond_filter_alignment():
+    """Aligned counts: multiples of the alignment except where capped or raised for the isometry shape;
+    never below the unaligned counts; discarded weights within the budget."""
+    from oracle import bond_filter as BF
+
+    M, d, chi = 40, 3, 48
+    b, G, L = gen.area_law_vidal_chain(M, d, 64)
+    plain, _, es = BF.filter_bonds(L, d, chi)
+    al, disc, es2 = BF.filter_bonds(L, d, chi, align=16)
+    assert es == es2
+    for k in range(1, M):
+        cap = min(chi, len(L[k - 1]))
+        assert al[k] >= plain[k] and disc[k] <= es
+        assert al[k] % 16 == 0 or al[k] == cap or al[k] == -(-al[k - 1] // d)
+
+
 def test_truncated_vidal_sampling_error_bounded():
     """The Born law of the truncated chain stays within total-variation distance 2 sqrt(sum of discarded
     weights) of the full chain's (norm bound of Schmidt truncation; tiny chain, exact laws by brute
