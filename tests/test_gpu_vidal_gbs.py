@@ -305,3 +305,23 @@ def test_truncated_load_from_device_arrays(lib, area_law):
                                      [torch.from_numpy(l).cuda() for l in L], bonds)
         d_s, d_l = s.sample(bonds, 3, 1500, 8)
     assert np.array_equal(h_s, d_s) and np.array_equal(h_l, d_l)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16x2"])
+def test_displaced_microbatch_and_offsets_are_exact(lib, precision):
+    """Displaced results depend only on (seed, n, mu[:, n]): micro-batch splits, ragged tails and n0
+    offsets reproduce them bitwise (every row's reduction order is fixed by chi_r alone)."""
+    M, d, N = 18, 4, 1000
+    b, ts, _ = gen.mps_tensors(M, d, 64, base_seed=41, skew=1.5)
+    mu = gen.gbs_amplitudes(M, N, sigma=0.5, seed=6)
+    with lib.Sampler(precision=precision) as s:
+        s.load_chain(ts)
+        a_s, a_l = s.sample(b, d, N, 9, mu=mu)
+    with lib.Sampler(precision=precision, max_microbatch=256) as s:
+        s.load_chain(ts)
+        b_s, b_l = s.sample(b, d, N, 9, mu=mu)
+        c_s, c_l = s.sample(b, d, 100, 9, n0=333, mu=np.ascontiguousarray(mu[:, 333:433]))
+        one_s, one_l = s.sample(b, d, 1, 9, n0=999, mu=np.ascontiguousarray(mu[:, 999:]))
+    assert np.array_equal(a_s, b_s) and np.array_equal(a_l, b_l)
+    assert np.array_equal(a_s[333:433], c_s) and np.array_equal(a_l[333:433], c_l)
+    assert np.array_equal(a_s[999:], one_s) and np.array_equal(a_l[999:], one_l)
