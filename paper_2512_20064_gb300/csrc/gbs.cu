@@ -560,6 +560,84 @@ __global__ void __launch_bounds__(256) measure_displaced_vec4_kernel(const Measu
         store_next4(a, grow, i, make_float4(0.f, 0.f, 0.f, 0.f));
 }
 
+// Narrow rows (d * chi_r <= 2048, chi_r a multiple of 4): one warp per row, the row's d blocks
+// copied to shared memory with cp.async (16-byte chunks, all in flight at once) instead of registers,
+// so that about 28 rows per SM are in flight (shared memory bounds it, not registers).
+template <int DMAX>
+__global__ void __launch_bounds__(32) measure_displaced_smem_kernel(const MeasureArgs a) {
+    extern __shared__ __align__(16) float srow[];  // d blocks of [Re (chi_r) | Im (chi_r)]
+    const int row = blockIdx.x, lane = threadIdx.x;
+    const int d = a.d, chi_r = a.chi_r, nf2 = 2 * chi_r, ngroups = chi_r >> 2, dd = d * d;
+    const int64_t Cs = a.Cs;
+    const float *yrow = a.Y + (int64_t)row * a.ldY;
+    {
+        const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(srow);
+        for (int t = 0; t < d; ++t)
+            for (int i = lane * 4; i < nf2; i += 128)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sbase + 4u * (uint32_t)(t * nf2 + i)),
+                             "l"(yrow + t * Cs + i)
+                             : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    const float2 *Drow = a.disp_D + (int64_t)row * dd;
+    const double u = a.disp_u[row];
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    const float4 *s4 = reinterpret_cast<const float4 *>(srow);
+    const int q = nf2 >> 2;  // float4 per block
+    float w[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        w[s] = 0.f;
+        if (s >= d) continue;
+        float2 c[DMAX];
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) c[t] = t < d ? Drow[s * d + t] : make_float2(0.f, 0.f);
+        for (int g = lane; g < ngroups; g += 32) {
+            float4 zr = make_float4(0.f, 0.f, 0.f, 0.f), zi = zr;
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t)
+                if (t < d) cmac4(c[t], s4[t * q + g], s4[t * q + ngroups + g], zr, zi);
+            w[s] += zr.x * zr.x + zr.y * zr.y + zr.z * zr.z + zr.w * zr.w + zi.x * zi.x + zi.y * zi.y +
+                    zi.z * zi.z + zi.w * zi.w;
+        }
+    }
+    block_reduce_w<DMAX>(w, nullptr, lane, 0, 1);
+    float wsel, Z32;
+    const int sstar = displaced_draw<DMAX>(w, d, u, wsel, Z32);
+    if (lane == 0) displaced_outputs<DMAX>(a, row, sstar, wsel, Z32, w);
+    const float scale = wsel > 0.f && Z32 > 0.f && isfinite(Z32) ? rsqrtf(wsel) : 0.f;
+    float2 c[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) {
+        const float2 e = t < d ? Drow[sstar * d + t] : make_float2(0.f, 0.f);
+        c[t] = make_float2(e.x * scale, e.y * scale);
+    }
+    const int64_t grow = a.row0 + row;
+    for (int g = lane; g < ngroups; g += 32) {
+        float4 zr = make_float4(0.f, 0.f, 0.f, 0.f), zi = zr;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t)
+            if (t < d) cmac4(c[t], s4[t * q + g], s4[t * q + ngroups + g], zr, zi);
+        store_next4(a, grow, 4 * g, zr);
+        store_next4(a, grow, chi_r + 4 * g, zi);
+    }
+    for (int i = 2 * chi_r + 4 * lane; i < a.K_next; i += 128)
+        store_next4(a, grow, i, make_float4(0.f, 0.f, 0.f, 0.f));
+}
+
+template <int DMAX>
+bool launch_smem_variant(const MeasureArgs &a, cudaStream_t st) {
+    if constexpr (DMAX > 8) {
+        return false;
+    } else {
+        if ((a.chi_r & 3) || (a.K_next & 3) || (a.ld_next & 3) || a.d * a.chi_r > 2048) return false;
+        const size_t smem = (size_t)a.d * 2 * a.chi_r * sizeof(float);
+        measure_displaced_smem_kernel<DMAX><<<(unsigned)a.rows, 32, smem, st>>>(a);
+        return true;
+    }
+}
+
 template <int DMAX>
 bool launch_vec4_variant(const MeasureArgs &a, cudaStream_t st) {
     if constexpr (DMAX > 8) {
@@ -614,6 +692,7 @@ bool launch_rows_variant(const MeasureArgs &a, cudaStream_t st) {
 
 template <int DMAX>
 void launch_displaced_variant(const MeasureArgs &a, cudaStream_t st) {
+    if (launch_smem_variant<DMAX>(a, st)) return;
     if (launch_vec4_variant<DMAX>(a, st)) return;
     if (launch_rows_variant<DMAX>(a, st)) return;
     const int grid = (a.rows + DISP_WARPS - 1) / DISP_WARPS;
