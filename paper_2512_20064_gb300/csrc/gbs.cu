@@ -192,117 +192,6 @@ __device__ __forceinline__ void store_next(const MeasureArgs &a, int64_t grow, i
     if (a.nplanes > 2) a.Vp[2][grow * a.ld_next + i] = h2;
 }
 
-// The measurement of one row given the row's scratch values (global or shared memory) and D.
-template <int DMAX, bool kShared>
-__device__ __forceinline__ void displaced_row(const MeasureArgs &a, int row, const float *yrow, const float2 *D,
-                                              int lane) {
-    const int d = a.d, chi_r = a.chi_r;
-    const int64_t Cs = a.Cs;
-    auto ld = [&](int64_t i) -> float { return kShared ? yrow[i] : __ldcg(yrow + i); };
-    // pass 1: w_s = sum_b |sum_t D[s][t] y_t[b]|^2 (FP32; the lane sums are reduced in FP32)
-    float w[DMAX];
-#pragma unroll
-    for (int s = 0; s < DMAX; ++s) w[s] = 0.f;
-    for (int b = lane; b < chi_r; b += 32) {
-        float2 y[DMAX];
-#pragma unroll
-        for (int t = 0; t < DMAX; ++t)
-            y[t] = t < d ? make_float2(ld(t * Cs + b), ld(t * Cs + chi_r + b)) : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int s = 0; s < DMAX; ++s) {
-            if (s >= d) break;
-            float zr = 0.f, zi = 0.f;
-#pragma unroll
-            for (int t = 0; t < DMAX; ++t) {
-                if (t >= d) break;
-                const float2 c = D[s * d + t];
-                zr = fmaf(c.x, y[t].x, fmaf(-c.y, y[t].y, zr));
-                zi = fmaf(c.x, y[t].y, fmaf(c.y, y[t].x, zi));
-            }
-            w[s] = fmaf(zr, zr, fmaf(zi, zi, w[s]));
-        }
-    }
-#pragma unroll
-    for (int s = 0; s < DMAX; ++s) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w[s] += __shfl_xor_sync(0xffffffffu, w[s], o);
-    }
-    // the draw in FP64 on the reduced sums (every lane holds them): C_s in s order,
-    // s* = first s with C_s >= u Z, else d-1
-    double Z = 0.0;
-#pragma unroll
-    for (int s = 0; s < DMAX; ++s)
-        if (s < d) Z += (double)w[s];
-    const double thr = a.disp_u[row] * Z;
-    int sstar = d - 1;
-    float ws = 0.f;
-    double C = 0.0;
-    bool found = false;
-#pragma unroll
-    for (int s = 0; s < DMAX; ++s) {
-        if (s < d && !found) {
-            C += (double)w[s];
-            if (s == d - 1 || C >= thr) {
-                sstar = s;
-                ws = w[s];
-                found = true;
-            }
-        }
-    }
-    const bool ok = (Z > 0.0) && isfinite(Z) && (ws > 0.f);
-    const int64_t grow = a.row0 + row;
-    if (lane == 0) {
-        a.outcomes[row] = (uint8_t)sstar;
-        if (ok) a.logp[grow] += (double)(logf(ws) - logf((float)Z));
-        else atomicExch(a.err, (int)kDevNumeric);
-        if (a.trace && grow < a.trace_rows) {
-#pragma unroll
-            for (int s = 0; s < DMAX; ++s)
-                if (s < d) a.trace[grow * d + s] = ok ? (double)w[s] / Z : 0.0;
-        }
-    }
-    // pass 2: next left row = (sum_t D[s*][t] y_t) / sqrt(w_{s*}), written as [Re | Im | zero padding]
-    const float scale = ok ? rsqrtf(ws) : 0.f;
-    float2 c[DMAX];
-#pragma unroll
-    for (int t = 0; t < DMAX; ++t) {
-        const float2 e = t < d ? D[sstar * d + t] : make_float2(0.f, 0.f);
-        c[t] = make_float2(e.x * scale, e.y * scale);
-    }
-    for (int b = lane; b < chi_r; b += 32) {
-        float zr = 0.f, zi = 0.f;
-#pragma unroll
-        for (int t = 0; t < DMAX; ++t) {
-            if (t >= d) break;
-            const float yr = ld(t * Cs + b), yi = ld(t * Cs + chi_r + b);
-            zr = fmaf(c[t].x, yr, fmaf(-c[t].y, yi, zr));
-            zi = fmaf(c[t].x, yi, fmaf(c[t].y, yr, zi));
-        }
-        store_next(a, grow, b, zr);
-        store_next(a, grow, chi_r + b, zi);
-    }
-    for (int i = 2 * chi_r + lane; i < a.K_next; i += 32) store_next(a, grow, i, 0.f);
-}
-
-__device__ __forceinline__ void load_D(const MeasureArgs &a, int row, float2 *D, int lane) {
-    const int dd = a.d * a.d;
-    const float2 *src = a.disp_D + (int64_t)row * dd;
-    for (int e = lane; e < dd; e += 32) D[e] = src[e];
-}
-
-// Unstaged fallback (rows wider than the register-resident kernel takes): one row per warp, the
-// second pass re-reads the row and relies on L2.
-template <int DMAX>
-__global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(const MeasureArgs a) {
-    __shared__ float2 Dsh[DISP_WARPS][DMAX * DMAX];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * DISP_WARPS + warp;
-    if (row >= a.rows) return;
-    load_D(a, row, Dsh[warp], lane);
-    __syncwarp();
-    displaced_row<DMAX, false>(a, row, a.Y + (int64_t)row * a.ldY, Dsh[warp], lane);
-}
-
 // ---------------------------------------------------------------------------
 // Register-resident displaced measurement: one thread block per sample row.  Thread j holds columns
 // of all d blocks of the row in registers (four consecutive columns per 16-byte load in the vector
@@ -396,6 +285,70 @@ __device__ __forceinline__ void displaced_outputs(const MeasureArgs &a, int row,
         for (int s = 0; s < DMAX; ++s)
             if (s < d) a.trace[grow * d + s] = ok ? (double)w[s] / (double)Z32 : 0.0;
     }
+}
+
+// Unstaged fallback (rows too wide for the register-resident and shared-memory variants, e.g.
+// chi = 10^4): one warp per row, two passes over the row in global memory (the second from L2).
+template <int DMAX>
+__global__ void __launch_bounds__(DISP_WARPS * 32) measure_displaced_kernel(const MeasureArgs a) {
+    __shared__ float2 Dsh[DISP_WARPS][DMAX * DMAX];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * DISP_WARPS + warp;
+    if (row >= a.rows) return;
+    const int d = a.d, chi_r = a.chi_r, dd = d * d;
+    const int64_t Cs = a.Cs;
+    float2 *D = Dsh[warp];
+    for (int e = lane; e < dd; e += 32) D[e] = a.disp_D[(int64_t)row * dd + e];
+    __syncwarp();
+    const float *yrow = a.Y + (int64_t)row * a.ldY;
+    float w[DMAX];
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) w[s] = 0.f;
+    for (int b = lane; b < chi_r; b += 32) {
+        float2 y[DMAX];
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t)
+            y[t] = t < d ? make_float2(__ldcg(yrow + t * Cs + b), __ldcg(yrow + t * Cs + chi_r + b))
+                         : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int s = 0; s < DMAX; ++s) {
+            if (s >= d) break;
+            float zr = 0.f, zi = 0.f;
+#pragma unroll
+            for (int t = 0; t < DMAX; ++t) {
+                if (t >= d) break;
+                const float2 c = D[s * d + t];
+                zr = fmaf(c.x, y[t].x, fmaf(-c.y, y[t].y, zr));
+                zi = fmaf(c.x, y[t].y, fmaf(c.y, y[t].x, zi));
+            }
+            w[s] = fmaf(zr, zr, fmaf(zi, zi, w[s]));
+        }
+    }
+    block_reduce_w<DMAX>(w, nullptr, lane, 0, 1);
+    float wsel, Z32;
+    const int sstar = displaced_draw<DMAX>(w, d, a.disp_u[row], wsel, Z32);
+    if (lane == 0) displaced_outputs<DMAX>(a, row, sstar, wsel, Z32, w);
+    const float scale = wsel > 0.f && Z32 > 0.f && isfinite(Z32) ? rsqrtf(wsel) : 0.f;
+    float2 c[DMAX];
+#pragma unroll
+    for (int t = 0; t < DMAX; ++t) {
+        const float2 e = t < d ? D[sstar * d + t] : make_float2(0.f, 0.f);
+        c[t] = make_float2(e.x * scale, e.y * scale);
+    }
+    const int64_t grow = a.row0 + row;
+    for (int b = lane; b < chi_r; b += 32) {
+        float zr = 0.f, zi = 0.f;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) {
+            if (t >= d) break;
+            const float yr = __ldcg(yrow + t * Cs + b), yi = __ldcg(yrow + t * Cs + chi_r + b);
+            zr = fmaf(c[t].x, yr, fmaf(-c[t].y, yi, zr));
+            zi = fmaf(c[t].x, yi, fmaf(c[t].y, yr, zi));
+        }
+        store_next(a, grow, b, zr);
+        store_next(a, grow, chi_r + b, zi);
+    }
+    for (int i = 2 * chi_r + lane; i < a.K_next; i += 32) store_next(a, grow, i, 0.f);
 }
 
 template <int DMAX, int VPT>
