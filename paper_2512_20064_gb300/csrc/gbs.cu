@@ -151,27 +151,76 @@ __global__ void __launch_bounds__(256) displacement_kernel(const float2 *__restr
     }
 }
 
+// The d*d entries of one sample for d <= DMAX, loops unrolled at compile time: the powers mu^k and
+// (-mu^*)^k are formed once per sample and each entry's series has a fixed length.  out(e, value)
+// receives entry e = s*d + t.
+template <int DMAX, class Out>
+__device__ __forceinline__ void displacement_matrix(float2 mu, int d, const float *__restrict__ tab, Out out) {
+    const ffloat mx = neg_abs2(mu);
+    const float g = expf(0.5f * (mx.hi + mx.lo));
+    float2 pw[DMAX], pc[DMAX];  // mu^k and (-mu^*)^k
+    pw[0] = pc[0] = make_float2(1.f, 0.f);
+    const float2 nmc = make_float2(-mu.x, mu.y);
+#pragma unroll
+    for (int k = 1; k < DMAX; ++k) {
+        pw[k] = cmulf(pw[k - 1], mu);
+        pc[k] = cmulf(pc[k - 1], nmc);
+    }
+#pragma unroll
+    for (int s = 0; s < DMAX; ++s) {
+        if (s >= d) break;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t) {
+            if (t >= d) break;
+            const float *e = tab + (s * d + t) * (2 * d + 1);
+            const int j = s < t ? s : t;
+            ffloat r = {1.f, 0.f}, S = {1.f, 0.f};
+#pragma unroll
+            for (int m = DMAX - 1; m >= 1; --m) {
+                if (m > j) continue;
+                r = ff_mul(r, ff_mul(mx, ffloat{e[2 * m - 1], e[2 * m]}));
+                S = ff_add(S, r);
+            }
+            const float f = g * e[0] * (S.hi + S.lo);
+            const float2 lead = s >= t ? pw[s - t] : pc[t - s];
+            out(s * d + t, make_float2(f * lead.x, f * lead.y));
+        }
+    }
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(256) displacement_small_kernel(const float2 *__restrict__ mu, int64_t N, int d,
+                                                                 const float *tab, float2 *D) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < N; n += (int64_t)gridDim.x * blockDim.x) {
+        // entries arrive in order e = 0, 1, ...: a running pointer (stride N) instead of e * N per entry
+        float2 *q = D + n;
+        displacement_matrix<DMAX>(mu[n], d, tab, [&](int, float2 v) {
+            *q = v;
+            q += N;
+        });
+    }
+}
+
 void launch_displacement(const float2 *mu, int64_t N, int d, const float *tab, float2 *D, int num_sms,
                          cudaStream_t st) {
     if (N <= 0) return;
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((N + threads - 1) / threads, (int64_t)num_sms * 8);
-    displacement_kernel<<<(unsigned)blocks, threads, 0, st>>>(mu, N, d, tab, D);
+    // (a fully unrolled 16 x 16 matrix no longer fits the register file: d > 8 takes the loop form)
+    if (d <= 4) displacement_small_kernel<4><<<(unsigned)blocks, threads, 0, st>>>(mu, N, d, tab, D);
+    else if (d <= 8) displacement_small_kernel<8><<<(unsigned)blocks, threads, 0, st>>>(mu, N, d, tab, D);
+    else displacement_kernel<<<(unsigned)blocks, threads, 0, st>>>(mu, N, d, tab, D);
 }
 
 // Per-row inputs of the displaced measurement, one thread per row: the row's displacement matrix
 // D[row][s*d + t] and its uniform u = U(seed, n, k, job), so that the measurement kernel's
 // per-row serial section is only the draw.
+template <int DMAX>
 __global__ void __launch_bounds__(256) displaced_prep_kernel(const MeasureArgs a) {
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.rows) return;
-    const int d = a.d;
-    const float2 m = a.mu[row];
-    const ffloat mx = neg_abs2(m);
-    const float g = expf(0.5f * (mx.hi + mx.lo));
-    float2 *out = a.disp_D + (int64_t)row * d * d;
-    for (int s = 0; s < d; ++s)
-        for (int t = 0; t < d; ++t) out[s * d + t] = displacement_entry(m, mx, g, s, t, d, a.disp_tab);
+    float2 *out = a.disp_D + (int64_t)row * a.d * a.d;
+    displacement_matrix<DMAX>(a.mu[row], a.d, a.disp_tab, [&](int e, float2 v) { out[e] = v; });
     a.disp_u[row] = sample_uniform(a.seed, a.n_base + (uint64_t)row, a.k, a.job);
 }
 
@@ -655,7 +704,10 @@ void launch_displaced_variant(const MeasureArgs &a, cudaStream_t st) {
 void launch_measure_displaced(const MeasureArgs &a, int num_sms, cudaStream_t st) {
     (void)num_sms;
     if (a.rows <= 0) return;
-    displaced_prep_kernel<<<(a.rows + 255) / 256, 256, 0, st>>>(a);
+    const unsigned pg = (unsigned)((a.rows + 255) / 256);
+    if (a.d <= 4) displaced_prep_kernel<4><<<pg, 256, 0, st>>>(a);
+    else if (a.d <= 8) displaced_prep_kernel<8><<<pg, 256, 0, st>>>(a);
+    else displaced_prep_kernel<kMaxDisplacedD><<<pg, 256, 0, st>>>(a);
     if (a.d <= 4) launch_displaced_variant<4>(a, st);
     else if (a.d <= 8) launch_displaced_variant<8>(a, st);
     else launch_displaced_variant<kMaxDisplacedD>(a, st);
