@@ -325,3 +325,32 @@ def test_displaced_microbatch_and_offsets_are_exact(lib, precision):
     assert np.array_equal(a_s, b_s) and np.array_equal(a_l, b_l)
     assert np.array_equal(a_s[333:433], c_s) and np.array_equal(a_l[333:433], c_l)
     assert np.array_equal(a_s[999:], one_s) and np.array_equal(a_l[999:], one_l)
+
+
+def test_displaced_host_stream_equals_resident(lib):
+    """Host-streamed BF16 site tensors give the same displaced samples as resident ones."""
+    M, d, N = 16, 4, 1500
+    b, ts, _ = gen.mps_tensors(M, d, 32, base_seed=77, skew=1.5)
+    mu = gen.gbs_amplitudes(M, N, sigma=0.4, seed=8)
+    with lib.Sampler(precision="bf16x2") as s:
+        s.load_chain(ts)
+        r_s, r_l = s.sample(b, d, N, 5, mu=mu)
+    with lib.Sampler(precision="bf16x2", residency="host_stream") as s:
+        s.load_chain(ts)
+        h_s, h_l = s.sample(b, d, N, 5, mu=mu)
+    assert np.array_equal(r_s, h_s) and np.array_equal(r_l, h_l)
+
+
+def test_vidal_pool_equals_sites(lib, vidal_chain):
+    """Vidal-form pool entries mapped to sites sample exactly like the same tensors loaded per site."""
+    b, G, L = vidal_chain
+    M = len(G)
+    with lib.Sampler(precision="bf16x2") as s:
+        s.load_chain_vidal(G, L)
+        a_s, a_l = s.sample(b, 3, 1000, 2)
+    with lib.Sampler(precision="bf16x2") as s:
+        for k in range(M):
+            lib.fastmps_load_pool_vidal(s.h, k, G[k], L[k])
+            lib.fastmps_map_site(s.h, k, k)
+        p_s, p_l = s.sample(b, 3, 1000, 2)
+    assert np.array_equal(a_s, p_s) and np.array_equal(a_l, p_l)

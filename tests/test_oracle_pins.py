@@ -259,3 +259,18 @@ def test_truncated_vidal_sampling_error_bounded():
     assert sum(bonds) < sum(b)
     tv = 0.5 * np.abs(full - trunc).sum()
     assert tv < 2 * math.sqrt(sum(disc)), (tv, sum(disc))
+
+
+def test_displacement_special_cases():
+    """mu = 0: D is the identity and displaced sampling is plain sampling (bitwise); for a large
+    truncation the leading block of D^dagger D is the identity (unitarity of the untruncated operator)."""
+    for n in (2, 5, 9):
+        assert np.array_equal(oracle.displacement(0.0, n), np.eye(n))
+    b, ts, _ = gen.mps_tensors(10, 3, 9, base_seed=2, skew=1.5)
+    s0, l0, p0 = oracle.sample(b, ts, 4, 200, want_probs=True)
+    s1, l1, p1 = oracle.sample(b, ts, 4, 200, want_probs=True, mu=np.zeros((10, 200), np.complex128))
+    assert np.array_equal(s0, s1) and np.array_equal(l0, l1) and np.array_equal(p0, p1)
+    for mu in (0.3 + 0.1j, -0.5j, 0.8):
+        D = oracle.displacement(mu, 60)
+        G = (D.conj().T @ D)[:10, :10]
+        assert np.abs(G - np.eye(10)).max() < 1e-12
