@@ -65,6 +65,9 @@ extern "C" {
  * each left row e4m3(v * 2^r) with a per-row power of two likewise; one kind::f8f6f4 product.
  * Both scales cancel in w / Z.  Resident residency only. */
 #define FASTMPS_FP8X1 5
+/* Experiment: as FP8X1, with the left row split into two E4M3 residual planes at the same per-row
+ * scale (V = V0 + V1, V1 = e4m3(v 2^r - V0)); two kind::f8f6f4 products V0 B + V1 B. */
+#define FASTMPS_FP8X2 6
 
 /* Where site tensors live between uses (Sec. 3.1: I/O overlapped by a double buffer). */
 #define FASTMPS_RESIDENT_HBM 0    /* repacked once at load time, kept in device memory */
@@ -77,7 +80,7 @@ extern "C" {
 #define FASTMPS_C128 1  /* interleaved complex double (re, im) */
 
 typedef struct fastmps_options {
-    int precision;          /* FASTMPS_FP32 | FASTMPS_BF16X2 | _BF16X3 | _BF16X3L | _BF16X4 | _FP8X1 */
+    int precision;          /* FASTMPS_FP32 | FASTMPS_BF16X2 | _BF16X3 | _BF16X3L | _BF16X4 | _FP8X1 | _FP8X2 */
     int residency;          /* FASTMPS_RESIDENT_HBM | FASTMPS_HOST_STREAM (BF16 modes only) */
     int64_t max_microbatch; /* rows per contraction launch; 0 = chosen from free memory */
     int autotune;           /* 1: time the candidate tile shapes once per new shape */

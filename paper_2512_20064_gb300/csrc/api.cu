@@ -168,7 +168,7 @@ int cuda_fail(fastmps_handle h, cudaError_t e, const char *what) {
 
 // Tensor-core precision modes (BF16 split planes or FP8); FP32 is the SIMT path.
 bool is_bf16(const fastmps_handle h) { return h->opt.precision != FASTMPS_FP32; }
-bool is_fp8(const fastmps_handle h) { return h->opt.precision == FASTMPS_FP8X1; }
+bool is_fp8(const fastmps_handle h) { return h->opt.precision == FASTMPS_FP8X1 || h->opt.precision == FASTMPS_FP8X2; }
 
 // Planes of the split-precision operands and the products accumulated per precision mode.
 struct PrecisionPlan {
@@ -183,6 +183,7 @@ PrecisionPlan plan_of(int precision) {
         case FASTMPS_BF16X3L: return {3, 1, 3, {0, 1, 2, 0}, {0, 0, 0, 0}};
         case FASTMPS_BF16X4: return {3, 2, 4, {0, 1, 2, 0}, {0, 0, 0, 1}};
         case FASTMPS_FP8X1: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
+        case FASTMPS_FP8X2: return {2, 1, 2, {0, 1, 0, 0}, {0, 0, 0, 0}};
         default: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
     }
 }
@@ -193,7 +194,7 @@ SiteLayout make_layout(int precision, int chi_l, int d, int chi_r, int bn_overri
     L.chi_l = chi_l;
     L.d = d;
     L.chi_r = chi_r;
-    L.bk = precision == FASTMPS_FP8X1 ? 128 : 64;
+    L.bk = (precision == FASTMPS_FP8X1 || precision == FASTMPS_FP8X2) ? 128 : 64;
     L.K_pad = (int)roundup(2 * (int64_t)chi_l, L.bk);
     if (precision == FASTMPS_FP32) {
         L.bn = 128;
@@ -671,9 +672,10 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     __nv_bfloat16 *Vp[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     for (int x = 0; x < 2; ++x)
         for (int p = 0; p < planes && bf16 && !fp8; ++p) Vp[x][p] = h->V[x][p].as<__nv_bfloat16>();
-    if (fp8)
+    if (fp8) {
         launch_init_left_e4m3(h->V[0][0].as<uint8_t>(), N_pad, ldV, st);
-    else if (bf16)
+        if (planes > 1) cudaMemsetAsync(h->V[0][1].p, 0, (size_t)N_pad * ldV, st);  // residual plane of [1]
+    } else if (bf16)
         launch_init_left_bf16(Vp[0], planes, N_pad, ldV, st);
     else
         launch_init_left_f32(h->V[0][0].as<float>(), N_pad, ldV, st);
@@ -793,6 +795,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             for (int p = 0; p < 3; ++p) ma.Vp[p] = fp8 ? nullptr : Vp[nxt][p];
             ma.nplanes = planes;
             ma.V8 = fp8 ? h->V[nxt][0].as<uint8_t>() : nullptr;
+            ma.V8lo = (fp8 && planes > 1) ? h->V[nxt][1].as<uint8_t>() : nullptr;
             ma.outcomes = h->O.as<uint8_t>() + (int64_t)k * N_pad + r0;
             ma.logp = h->logp.as<double>();
             ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
@@ -898,7 +901,7 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
     fastmps_options o;
     fastmps_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_FP8X1) {
+    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_FP8X2) {
         g_create_error = "unknown precision";
         return FASTMPS_ERR_INVALID_ARG;
     }
@@ -906,7 +909,8 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
         g_create_error = "unknown residency";
         return FASTMPS_ERR_INVALID_ARG;
     }
-    if (o.residency == FASTMPS_HOST_STREAM && (o.precision == FASTMPS_FP32 || o.precision == FASTMPS_FP8X1)) {
+    if (o.residency == FASTMPS_HOST_STREAM &&
+        (o.precision == FASTMPS_FP32 || o.precision == FASTMPS_FP8X1 || o.precision == FASTMPS_FP8X2)) {
         g_create_error = "host streaming keeps BF16 tensors: use a BF16 precision";
         return FASTMPS_ERR_UNSUPPORTED;
     }

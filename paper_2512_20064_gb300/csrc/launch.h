@@ -101,6 +101,7 @@ struct MeasureArgs {
     __nv_bfloat16 *Vp[3];     // BF16 paths: planes of successive residuals
     int nplanes;              // 2 or 3
     uint8_t *V8 = nullptr;    // FP8 path: E4M3 row scaled by a per-row power of two
+    uint8_t *V8lo = nullptr;  // FP8X2: E4M3 residual plane at the same per-row scale (or nullptr)
     const float2 *mu = nullptr;  // displaced measurement: amplitude of each row of this micro-batch
     const float *disp_tab = nullptr;   // displaced measurement: constants of the displacement entries
     float2 *disp_D = nullptr;          // displaced measurement: per-row matrices [row][d*d] (prep kernel output)

@@ -75,9 +75,16 @@ __device__ __forceinline__ void measure_write_row(const MeasureArgs &a, int lane
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
         const float s8 = m > 0.f ? exp2f(floorf(log2f(448.f / m))) : 1.f;
         uint8_t *dst = a.V8 + grow * a.ld_next;
+        uint8_t *dlo = a.V8lo ? a.V8lo + grow * a.ld_next : nullptr;
         for (int i = lane; i < a.K_next; i += 32) {
             const float x = i < nreal ? __ldcg(ysrc + i) * scale * s8 : 0.f;
-            dst[i] = (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+            const __nv_fp8_storage_t h = __nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+            dst[i] = (uint8_t)h;
+            if (dlo) {
+                // residual at the same scale: the two planes' products add up to (V0 + V1) B
+                const float hv = __half2float(__half(__nv_cvt_fp8_to_halfraw(h, __NV_E4M3)));
+                dlo[i] = (uint8_t)__nv_cvt_float_to_fp8(x - hv, __NV_SATFINITE, __NV_E4M3);
+            }
         }
         return;
     }

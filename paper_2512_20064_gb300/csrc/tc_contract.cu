@@ -476,7 +476,7 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     }
     p.row0 = (int)a.row0;
     p.idesc = a.fp8 ? idesc_e4m3_f32(kBM, L.bn) : idesc_bf16_f32(kBM, L.bn);
-    if (a.fp8 && (fused || a.a_planes != 1 || a.b_planes != 1 || a.nprod != 1)) return cudaErrorInvalidValue;
+    if (a.fp8 && (fused || a.a_planes > 2 || a.b_planes != 1)) return cudaErrorInvalidValue;
     p.Y = o.Y;
     p.ldY = o.ldY;
     p.P = o.P;
