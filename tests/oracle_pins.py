@@ -337,3 +337,81 @@ def marginals_5sigma(samples: np.ndarray, bf: np.ndarray):
         if z.max() > worst:
             worst, where = float(z.max()), f"pair ({k},{k+1})"
     return worst, where
+
+
+# ---------------------------------------------------------------------------
+# Dynamic bond-dimension filter (Sec. 3.4.2): pins taking the filter module as an argument, so that
+# mutated copies can be checked too
+# ---------------------------------------------------------------------------
+
+def pin_bf_geometric(BF):
+    """Lambda_j^2 = q^j: eps(c) = (q^c - q^n) / (1 - q^n), least c with eps(c) <= e is
+    ceil(log(e (1 - q^n) + q^n) / log q); the discarded weight reported is that closed form."""
+    for q, n, e in ((0.5, 40, 1e-6), (0.9, 200, 1e-3), (0.99, 500, 0.05), (0.7, 10, 1e-2)):
+        lam = [math.sqrt(q ** j) for j in range(n)]
+        want = max(1, math.ceil(math.log(e * (1 - q ** n) + q ** n) / math.log(q) - 1e-9))
+        bonds, disc, _ = BF.filter_bonds([lam, [1.0]], d=n, chi=n, eps=e)
+        if bonds[1] != want:
+            return False, f"q={q} n={n} e={e}: kept {bonds[1]} != {want}"
+        if not abs(disc[1] - (q ** bonds[1] - q ** n) / (1 - q ** n)) < 1e-12:
+            return False, f"discarded weight {disc[1]!r} is not the closed form"
+    return True, ""
+
+
+def pin_bf_budget_and_minimality(BF):
+    """Default budget = the largest discarded weight of keeping min(chi, n) at any bond; every bond within
+    it and minimal (where the isometry rule did not raise it); isometry shapes hold."""
+    M, d, chi = 40, 3, 24
+    b, G, L = gen.area_law_vidal_chain(M, d, 64)
+    bonds, disc, es = BF.filter_bonds(L, d, chi)
+    fixed = []
+    for k in range(M - 1):
+        lam2 = np.asarray(L[k], np.float64) ** 2
+        c = min(chi, len(L[k]))
+        fixed.append(float(lam2[c:].sum() / lam2.sum()))
+    if not abs(es - max(fixed)) <= 1e-12 * max(fixed):
+        return False, f"budget {es!r} != largest fixed-chi discarded weight {max(fixed)!r}"
+    for k in range(M - 1):
+        c = bonds[k + 1]
+        lam2 = np.asarray(L[k], np.float64) ** 2
+        if not 1 <= c <= min(chi, len(L[k])):
+            return False, f"bond {k + 1}: {c} outside [1, cap]"
+        if not lam2[c:].sum() / lam2.sum() <= es * (1 + 1e-12):
+            return False, f"bond {k + 1}: discarded weight above the budget"
+        if bonds[k] > d * c:
+            return False, f"site {k}: d * chi_r < chi_l"
+        if c > 1 and c > -(-bonds[k] // d) and lam2[c - 1:].sum() / lam2.sum() <= es * (1 - 1e-12):
+            return False, f"bond {k + 1}: {c} is not the least count within the budget"
+    if not (bonds[2] < bonds[M // 2] and bonds[M - 2] < bonds[M // 2]):
+        return False, "edges do not keep fewer coefficients than the centre"
+    return True, ""
+
+
+def pin_bf_alignment(BF):
+    """Aligned counts are multiples of the alignment unless capped or raised for an isometry shape, and
+    never below the unaligned counts."""
+    M, d, chi = 40, 3, 48
+    b, G, L = gen.area_law_vidal_chain(M, d, 64)
+    plain, _, _ = BF.filter_bonds(L, d, chi)
+    al, _, _ = BF.filter_bonds(L, d, chi, align=16)
+    for k in range(1, M):
+        cap = min(chi, len(L[k - 1]))
+        if al[k] < plain[k]:
+            return False, f"bond {k}: aligned {al[k]} below unaligned {plain[k]}"
+        if not (al[k] % 16 == 0 or al[k] == cap or al[k] == -(-al[k - 1] // d)):
+            return False, f"bond {k}: {al[k]} is not aligned"
+    return True, ""
+
+
+def pin_bf_isometry_raise(BF):
+    """A flat spectrum followed by a peaked one: the threshold keeps 4 then 1, and the isometry rule must
+    raise the second count to ceil(4 / d) = 2 (d = 2), since a site needs d * chi_r >= chi_l."""
+    flat = [0.5] * 4
+    peaked = [1.0] + [1e-9] * 7
+    bonds, disc, _ = BF.filter_bonds([flat, peaked, [1.0]], d=2, chi=8, eps=1e-12)
+    if bonds != [1, 4, 2, 1]:
+        return False, f"bonds {bonds} != [1, 4, 2, 1]"
+    return True, ""
+
+
+BOND_FILTER_PINS = [pin_bf_geometric, pin_bf_budget_and_minimality, pin_bf_alignment, pin_bf_isometry_raise]

@@ -59,3 +59,12 @@ def test_filter_rejects_bad_input(F):
     with pytest.raises(F.FastMPSError) as e:
         F.fastmps_bond_filter([1, 3, 1], [np.zeros(3), np.ones(1)], 3, 4)
     assert e.value.code == -1
+
+
+def test_filter_isometry_raise(F):
+    """The library raises a count for the isometry shape exactly as the oracle does."""
+    b = [1, 4, 8, 1]
+    L = [np.full(4, 0.5), np.array([1.0] + [1e-9] * 7), np.ones(1)]
+    got, _ = F.fastmps_bond_filter(b, L, 2, 8, 1e-12)
+    want, _, _ = BF.filter_bonds(L, 2, 8, 1e-12)
+    assert got == want == [1, 4, 2, 1]

@@ -60,3 +60,41 @@ def test_mutant_is_caught(name, tmp_path):
         if not ok:
             failures.append(pin.__name__)
     assert failures, f"mutant {name} passed every pin"
+
+
+# ---------------------------------------------------------------------------
+# the bond-dimension filter's restatement (oracle/bond_filter.py)
+# ---------------------------------------------------------------------------
+BF_SRC = os.path.join(os.path.dirname(oracle.__file__), "bond_filter.py")
+
+BF_MUTANTS = {
+    "tail_sum_from_the_front": ("    for j in range(n - 1, -1, -1):", "    for j in range(0, n):"),
+    "kept_count_off_by_one": ("                keep = c\n", "                keep = c - 1 if c > 1 else c\n"),
+    "strict_budget_comparison": ("            if T[c] / T[0] <= eps_star:", "            if T[c] / T[0] < eps_star * 0.5:"),
+    "budget_from_first_bond_only": ("            if e > eps_star:\n                eps_star = e", "            if k == 0:\n                eps_star = e"),
+    "alignment_rounds_down": ("            keep = min(-(-keep // align) * align, caps[k])",
+                              "            keep = max(1, min(keep // align * align, caps[k]))"),
+    "no_isometry_sweep": ("        bonds[k + 1] = min(max(bonds[k + 1], need), caps[k])", "        pass"),
+    "discarded_not_normalised": ("        disc[k + 1] = tails[k][bonds[k + 1]] / tails[k][0]",
+                                 "        disc[k + 1] = tails[k][bonds[k + 1]]"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(BF_MUTANTS))
+def test_bond_filter_mutant_is_caught(name):
+    import types
+
+    find, repl = BF_MUTANTS[name]
+    src = open(BF_SRC).read()
+    assert src.count(find) == 1, f"mutation site for {name} not unique/absent"
+    mod = types.ModuleType(f"bf_mutant_{name}")
+    exec(compile(src.replace(find, repl), f"<mutant {name}>", "exec"), mod.__dict__)
+    failures = []
+    for pin in P.BOND_FILTER_PINS:
+        try:
+            ok, detail = pin(mod)
+        except Exception as e:  # a crash also counts as caught
+            ok, detail = False, repr(e)
+        if not ok:
+            failures.append(pin.__name__)
+    assert failures, f"mutant {name} passed every pin"

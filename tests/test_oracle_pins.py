@@ -15,6 +15,14 @@ def test_pin(pin):
     assert ok, detail
 
 
+@pytest.mark.parametrize("pin", P.BOND_FILTER_PINS, ids=lambda f: f.__name__)
+def test_bond_filter_pin(pin):
+    from oracle import bond_filter as BF
+
+    ok, detail = pin(BF)
+    assert ok, detail
+
+
 def test_uniform_range_and_uniformity():
     n = 200_000
     u = np.array([oracle.uniform(42, i, 7) for i in range(0, n)])
