@@ -282,3 +282,18 @@ def test_displacement_special_cases():
         D = oracle.displacement(mu, 60)
         G = (D.conj().T @ D)[:10, :10]
         assert np.abs(G - np.eye(10)).max() < 1e-12
+
+
+def test_area_law_chain_torch_route_is_a_vidal_form():
+    """The device route of the area-law generator (run here with torch on the CPU) yields a valid Vidal
+    form: Gamma_k Lambda_k right-canonical (complex64 rounding) and Lambda_k the chain's Schmidt
+    coefficients (an independent SVD sweep of Gamma Lambda reproduces them)."""
+    b, G, L = gen.area_law_vidal_chain(10, 3, 27, xi_max=3.0, seed=5, device="cpu")
+    Gs = [g.numpy().astype(np.complex128) for g in G]
+    Ls = [l.numpy() for l in L]
+    A = [Gs[k] * Ls[k][None, None, :] for k in range(10)]
+    for B in A:
+        E = np.einsum("asb,csb->ac", B, B.conj())
+        assert np.abs(E - np.eye(B.shape[0])).max() < 1e-6
+    _, L2 = gen.vidal_form(b, A)
+    assert max(float(np.abs(L2[k] - Ls[k]).max()) for k in range(10)) < 1e-6
