@@ -277,7 +277,11 @@ int fastmps_load_pool_vidal(fastmps_handle h, int j, int chi_l, int d, int chi_r
  * vector are then those of fastmps_sample_ex on the mixed blocks.  Needs
  * 2 <= d <= 16 and the FP32 or a BF16 precision (FASTMPS_ERR_SHAPE /
  * FASTMPS_ERR_UNSUPPORTED otherwise); the measurement runs as a separate kernel
- * (fused_measure is ignored).
+ * (fused_measure is ignored).  Host amplitudes are copied to a device buffer of
+ * M * N * 8 bytes owned by the handle at the start of the call; device
+ * amplitudes (8-byte aligned) are read in place.  The outcome draw is decided
+ * as in FP64 on the FP32 probability sums (an FP32 comparison, redone in FP64
+ * when the threshold lies within 1e-5 Z of a cumulative sum).
  */
 int fastmps_displacement(fastmps_handle h, int64_t N, int d, const float *mu, float *D);
 int fastmps_sample_displaced(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N,
