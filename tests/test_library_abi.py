@@ -50,3 +50,27 @@ def test_library_does_not_reference_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "orc_" not in text, f
+
+
+def test_every_exported_symbol_is_declared():
+    """The library exports no fastmps_* entry point that the header does not declare."""
+    import shutil
+    import subprocess
+
+    import paper_2512_20064_gb300 as F
+
+    if shutil.which("nm") is None:
+        pytest.skip("nm not available")
+    F.load_library()
+    out = subprocess.run(["nm", "-D", "--defined-only", F.native.LIB], capture_output=True, text=True).stdout
+    exported = sorted({ln.split()[-1] for ln in out.splitlines() if ln.split() and ln.split()[-1].startswith("fastmps_")})
+    undeclared = [n for n in exported if n not in declared_functions()]
+    assert exported and not undeclared, undeclared
+
+
+def test_binding_carries_the_c_names():
+    """The Python binding offers every declared entry point under its C name (argument marshalling only)."""
+    import paper_2512_20064_gb300 as F
+
+    missing = [n for n in declared_functions() if not callable(getattr(F, n, None))]
+    assert not missing, missing
