@@ -7,6 +7,11 @@ the tensors those stores represent.  This module restates the storage format
 from its definition (IEEE-754 binary32 -> bfloat16, round to nearest, ties to
 even) with integer operations on the float32 bit patterns; it shares nothing
 with the CUDA path.
+
+Pinned in ``tests/oracle_pins.py`` (``QUANT_PINS``): hand-derived rounding cases of
+both formats and an independent cross-check against torch's casts; planted
+mistakes (truncation, ties away from zero, no saturation, a wrong subnormal
+floor, a ceiling scale, ...) are each caught (``tests/test_oracle_mutants.py``).
 """
 from __future__ import annotations
 

@@ -37,6 +37,12 @@ What pins what
   (Gamma, Lambda) reproduces the brute-force Born law of the state
   Gamma_0 Lambda_0 Gamma_1 Lambda_1 ... for a converted chain and for a chain with
   decaying Schmidt spectra.
+* ``QUANT_PINS`` (oracle/quant.py) -- bfloat16 and E4M3 rounding on hand-derived cases
+  (ties to even of both parities, carries into the exponent, subnormal grids, the E4M3
+  2^-6 boundary and saturation at 448, signed zero), cross-checked against torch's
+  bfloat16 / float8_e4m3fn casts called as a library; the hi/lo split holds 16
+  significant bits; the FP8 site scale is the power of two that puts max|Re, Im| in
+  [224, 448].
 """
 from __future__ import annotations
 
@@ -415,3 +421,197 @@ def pin_bf_isometry_raise(BF):
 
 
 BOND_FILTER_PINS = [pin_bf_geometric, pin_bf_budget_and_minimality, pin_bf_alignment, pin_bf_isometry_raise]
+
+
+# ---------------------------------------------------------------------------
+# Low-precision storage formats (oracle/quant.py; Sec. 3.3.2 16-bit storage, the FP8 experiment):
+# pins taking the module as an argument, so that mutated copies can be checked too.  The expected
+# values are derived by hand from the format definitions (bfloat16: 8 significant bits, 8 exponent
+# bits, round to nearest, ties to even; E4M3FN: 4 significant bits, bias 7, subnormal spacing 2^-9,
+# largest finite 448, saturating stores) and, separately, from torch's casts called as a library.
+# ---------------------------------------------------------------------------
+
+def _f32(values):
+    return np.asarray(values, dtype=np.float32)
+
+
+def _same_bits(a, b):
+    a = np.ascontiguousarray(np.asarray(a, np.float32))
+    b = np.ascontiguousarray(np.asarray(b, np.float32))
+    return np.array_equal(a.view(np.uint32), b.view(np.uint32))
+
+
+def pin_bf16_hand_cases(Q):
+    """Ties to even (both parities), just above a tie, carry into the exponent, subnormals, signed zero."""
+    u = 2.0 ** -8  # half an ulp of bfloat16 at 1.0 (spacing 2^-7 in [1, 2))
+    cases = [
+        (1.0, 1.0),
+        (1.0 + u, 1.0),                          # tie, lower neighbour 1.0 has an even last bit
+        (1.0 + 3 * u, 1.0 + 4 * u),              # tie between 1+2^-7 (odd) and 1+2^-6 (even): up
+        (1.0 + u + 2.0 ** -20, 1.0 + 2 * u),     # just above the tie: up
+        (1.0 + u - 2.0 ** -20, 1.0),             # just below the tie: down
+        (2.0 - u, 2.0),                          # tie between 2-2^-7 (all ones, odd) and 2: carry
+        (2.0 - 2 * u, 2.0 - 2 * u),              # representable: unchanged
+        (-(1.0 + u), -1.0),                      # symmetric in the sign
+        (-(1.0 + 3 * u), -(1.0 + 4 * u)),
+        (3 * 2.0 ** -134, 2.0 ** -132),          # subnormal tie (spacing 2^-133): to the even neighbour
+        (2.0 ** -134, 0.0),                      # subnormal tie between 0 and 2^-133: to zero
+        (5 * 2.0 ** -135, 2.0 ** -133),          # below the tie 1.25 * 2^-133: down
+        (1.5 * 2.0 ** 100, 1.5 * 2.0 ** 100),
+    ]
+    x = _f32([c[0] for c in cases])
+    want = _f32([c[1] for c in cases])
+    got = Q.bf16_round(x)
+    if not _same_bits(got, want):
+        bad = [(float(a), float(g), float(w)) for a, g, w in zip(x, got, want) if float(g) != float(w)]
+        return False, f"bf16_round hand cases differ: {bad[:4]}"
+    z = Q.bf16_round(_f32([-0.0, 0.0]))
+    if not (np.signbit(z[0]) and not np.signbit(z[1])):
+        return False, "bf16_round loses the sign of zero"
+    return True, ""
+
+
+def pin_bf16_vs_torch(Q, n=200000, seed=1):
+    """bf16_round equals torch's float32 -> bfloat16 cast (round to nearest even) on random bit patterns
+    over the finite range and on values with 9 to 17 significant bits (dense in ties)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    bits = rng.integers(0, 2 ** 32, size=n, dtype=np.uint64).astype(np.uint32)
+    exp = (bits >> 23) & 0xFF
+    x = bits[exp != 0xFF].view(np.float32)
+    ties = (rng.integers(1 << 8, 1 << 17, size=n) * 2.0 ** rng.integers(-140, 100, size=n)).astype(np.float32)
+    for arr in (x, ties, -ties):
+        want = torch.from_numpy(arr.copy()).to(torch.bfloat16).float().numpy()
+        if not _same_bits(Q.bf16_round(arr), want):
+            return False, "bf16_round differs from torch's bfloat16 cast"
+    return True, ""
+
+
+def pin_bf16_split(Q, n=50000, seed=2):
+    """hi = bf16(x), lo = bf16(x - hi) (difference in float32): checked against torch's casts, and
+    |x - hi - lo| <= 2^-16 |x| (two 8-bit planes hold 16 significant bits) for normal x."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal(n) * 2.0 ** rng.integers(-30, 30, size=n)).astype(np.float32)
+    hi, lo = Q.bf16_split(x)
+    th = torch.from_numpy(x.copy()).to(torch.bfloat16)
+    tl = (torch.from_numpy(x.copy()) - th.float()).to(torch.bfloat16)
+    if not (_same_bits(hi, th.float().numpy()) and _same_bits(lo, tl.float().numpy())):
+        return False, "bf16_split planes differ from torch's casts"
+    err = np.abs(x.astype(np.float64) - hi.astype(np.float64) - lo.astype(np.float64))
+    if not (err <= 2.0 ** -16 * np.abs(x.astype(np.float64))).all():
+        return False, f"hi + lo misses x by {float((err / np.abs(x)).max()):.3e} relative"
+    # a value with exactly 16 significant bits is held exactly by the two planes
+    y = _f32([1.0 + 2.0 ** -15, -(3.0 + 2.0 ** -14)])
+    h, l = Q.bf16_split(y)
+    if not np.array_equal(h.astype(np.float64) + l.astype(np.float64), y.astype(np.float64)):
+        return False, "a 16-bit value is not held exactly by hi + lo"
+    return True, ""
+
+
+def pin_dequant_bf16(Q, seed=3):
+    """dequant_bf16: real and imaginary parts through float32 then the planes, for 1 and 2 planes."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((5, 3, 7)) + 1j * rng.standard_normal((5, 3, 7))
+    re = torch.from_numpy(A.real.astype(np.float32))
+    im = torch.from_numpy(A.imag.astype(np.float32))
+    one = re.to(torch.bfloat16).double().numpy() + 1j * im.to(torch.bfloat16).double().numpy()
+    if not np.array_equal(Q.dequant_bf16(A, 1), one):
+        return False, "dequant_bf16(planes=1) is not the bfloat16 cast of each part"
+    rl = (re - re.to(torch.bfloat16).float()).to(torch.bfloat16).double()
+    il = (im - im.to(torch.bfloat16).float()).to(torch.bfloat16).double()
+    two = (re.to(torch.bfloat16).double() + rl).numpy() + 1j * (im.to(torch.bfloat16).double() + il).numpy()
+    if not np.array_equal(Q.dequant_bf16(A, 2), two):
+        return False, "dequant_bf16(planes=2) is not hi + lo of each part"
+    return True, ""
+
+
+def pin_e4m3_hand_cases(Q):
+    """Subnormal grid 2^-9, ties to even on it and among normals, the 2^-6 boundary, saturation at 448."""
+    s = 2.0 ** -9
+    cases = [
+        (0.0, 0.0),
+        (s, s), (7 * s, 7 * s),                  # subnormals are exact multiples of 2^-9
+        (0.5 * s, 0.0),                          # tie between 0 and 2^-9: to zero (even)
+        (1.5 * s, 2 * s),                        # tie between 2^-9 (odd) and 2^-8 (even): up
+        (2.5 * s, 2 * s),                        # tie between 2^-8 (even) and 3 * 2^-9: down
+        (7.5 * s, 2.0 ** -6),                    # largest subnormal tie rounds into the normals
+        (2.0 ** -6, 2.0 ** -6),                  # least normal
+        (2.0 ** -6 + 0.5 * s, 2.0 ** -6),        # spacing stays 2^-9 in [2^-6, 2^-5): tie to even
+        (2.0 ** -6 + 1.5 * s, 2.0 ** -6 + 2 * s),
+        (1.0 + 2.0 ** -4, 1.0),                  # spacing 2^-3 in [1, 2): tie, down to the even 1.0
+        (1.0 + 3 * 2.0 ** -4, 1.25),             # tie, up to the even 1.25
+        (1.0 + 2.0 ** -4 + 2.0 ** -10, 1.125),   # above the tie
+        (240.0, 240.0), (256.0, 256.0), (416.0, 416.0), (448.0, 448.0),
+        (432.0, 448.0),                          # tie between 416 (odd last bit) and 448 (even): up
+        (400.0, 384.0), (420.0, 416.0),          # spacing 32 in [256, 512): 400 is a tie to even 384
+        (460.0, 448.0), (500.0, 448.0), (1e6, 448.0),  # saturating store
+        (-1.5 * s, -2 * s), (-1e6, -448.0),
+    ]
+    x = np.asarray([c[0] for c in cases], np.float64)
+    want = np.asarray([c[1] for c in cases], np.float64)
+    got = Q.e4m3_round(x)
+    if not np.array_equal(got, want):
+        bad = [(a, g, w) for a, g, w in zip(x, got, want) if g != w]
+        return False, f"e4m3_round hand cases differ: {bad[:4]}"
+    return True, ""
+
+
+def pin_e4m3_vs_torch(Q, n=200000, seed=4):
+    """e4m3_round equals torch's float32 -> float8_e4m3fn cast below the saturation region
+    (|x| < 464, where torch rounds to 448 too; above it torch gives NaN and the store saturates)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    x = (rng.uniform(-1, 1, size=n) * 2.0 ** rng.integers(-14, 9, size=n)).astype(np.float32)
+    x = x[np.abs(x) < 464.0]
+    grid = (np.arange(-3712, 3713) * 2.0 ** -13).astype(np.float32)  # every half-spacing tie up to 0.45
+    for arr in (x, grid):
+        want = torch.from_numpy(arr.copy()).to(torch.float8_e4m3fn).double().numpy()
+        if not np.array_equal(Q.e4m3_round(arr.astype(np.float64)), want):
+            return False, "e4m3_round differs from torch's float8_e4m3fn cast"
+    return True, ""
+
+
+def pin_e4m3_site_scale(Q, seed=5):
+    """The site scale is a power of two 2^j with max|Re, Im| * 2^j in [224, 448] (the largest such j)."""
+    rng = np.random.default_rng(seed)
+    for m in (448.0, 1.0, 1.75, 0.3, 3e-5, 1000.0, 224.0, 223.9):
+        A = rng.standard_normal((4, 2, 4)) + 1j * rng.standard_normal((4, 2, 4))
+        A *= m / max(np.abs(A.real).max(), np.abs(A.imag).max())
+        sc = Q.e4m3_site_scale(A)
+        mx = float(max(np.abs(A.real.astype(np.float32)).max(), np.abs(A.imag.astype(np.float32)).max()))
+        j = math.log2(sc)
+        if j != round(j):
+            return False, f"scale {sc} is not a power of two"
+        if not 224.0 <= mx * sc <= 448.0:
+            return False, f"max {mx} * scale {sc} = {mx * sc} outside [224, 448]"
+    if Q.e4m3_site_scale(np.zeros((2, 2, 2), complex)) != 1.0:
+        return False, "all-zero tensor must get scale 1"
+    return True, ""
+
+
+def pin_dequant_e4m3(Q, seed=6):
+    """dequant_e4m3 = e4m3(x * scale) / scale per part; values already on the scaled grid survive exactly."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((6, 2, 5)) + 1j * rng.standard_normal((6, 2, 5))
+    sc = Q.e4m3_site_scale(A)
+    D = Q.dequant_e4m3(A)
+    re = A.real.astype(np.float32).astype(np.float64)
+    im = A.imag.astype(np.float32).astype(np.float64)
+    if not np.array_equal(D, (Q.e4m3_round(re * sc) + 1j * Q.e4m3_round(im * sc)) / sc):
+        return False, "dequant_e4m3 is not the scaled rounding"
+    if not np.array_equal(Q.dequant_e4m3(D), D):
+        return False, "dequant_e4m3 is not idempotent"
+    rel = np.abs(D.real - re) / np.maximum(np.abs(re), 2.0 ** -6 / sc)
+    if rel.max() > 2.0 ** -4 * (1 + 1e-12):
+        return False, f"relative error {rel.max():.3e} above half a 3-bit ulp"
+    return True, ""
+
+
+QUANT_PINS = [pin_bf16_hand_cases, pin_bf16_vs_torch, pin_bf16_split, pin_dequant_bf16, pin_e4m3_hand_cases,
+              pin_e4m3_vs_torch, pin_e4m3_site_scale, pin_dequant_e4m3]

@@ -98,3 +98,52 @@ def test_bond_filter_mutant_is_caught(name):
         if not ok:
             failures.append(pin.__name__)
     assert failures, f"mutant {name} passed every pin"
+
+
+# ---------------------------------------------------------------------------
+# the low-precision storage formats (oracle/quant.py)
+# ---------------------------------------------------------------------------
+Q_SRC = os.path.join(os.path.dirname(oracle.__file__), "quant.py")
+
+QUANT_MUTANTS = {
+    "bf16_truncates": ("    u = (u + 0x7FFF + lsb) & 0xFFFF0000", "    u = u & 0xFFFF0000"),
+    "bf16_ties_away_from_zero": ("    u = (u + 0x7FFF + lsb) & 0xFFFF0000", "    u = (u + 0x8000) & 0xFFFF0000"),
+    "bf16_ties_to_odd": ("    u = (u + 0x7FFF + lsb) & 0xFFFF0000", "    u = (u + 0x8000 - lsb) & 0xFFFF0000"),
+    "bf16_lo_plane_unrounded": ("    lo = bf16_round((x - hi).astype(np.float32))", "    lo = (x - hi).astype(np.float32)"),
+    "bf16_lo_from_x": ("    lo = bf16_round((x - hi).astype(np.float32))", "    lo = bf16_round(x) * 0"),
+    "dequant_drops_lo_plane": ("    return (rh.astype(np.float64) + rl.astype(np.float64)) + 1j",
+                               "    return (rh.astype(np.float64) + 0.0 * rl.astype(np.float64)) + 1j"),
+    "dequant_imag_from_real": ("    return bf16_round(re).astype(np.float64) + 1j * bf16_round(im).astype(np.float64)",
+                               "    return bf16_round(re).astype(np.float64) + 1j * bf16_round(re).astype(np.float64)"),
+    "e4m3_no_saturation": ("    r = np.minimum(r, E4M3_MAX)", "    r = r"),
+    "e4m3_subnormal_floor_off_by_one": ("    e = np.maximum(ex - 1, -6)", "    e = np.maximum(ex - 1, -7)"),
+    "e4m3_four_mantissa_bits": ("    q = np.ldexp(1.0, (e - 3).astype(np.int64))", "    q = np.ldexp(1.0, (e - 4).astype(np.int64))"),
+    "e4m3_ties_away_from_zero": ("    r = np.round(a / q) * q", "    r = np.floor(a / q + 0.5) * q"),
+    "e4m3_truncates": ("    r = np.round(a / q) * q", "    r = np.floor(a / q) * q"),
+    "e4m3_scale_ceil": ("    return float(2.0 ** np.floor(np.log2(E4M3_MAX / m)))",
+                        "    return float(2.0 ** np.ceil(np.log2(E4M3_MAX / m)))"),
+    "e4m3_scale_one_too_small": ("    return float(2.0 ** np.floor(np.log2(E4M3_MAX / m)))",
+                                 "    return float(2.0 ** (np.floor(np.log2(E4M3_MAX / m)) - 1))"),
+    "dequant_e4m3_not_unscaled": ("    return (e4m3_round(re * s) + 1j * e4m3_round(im * s)) / s",
+                                  "    return (e4m3_round(re * s) + 1j * e4m3_round(im * s))"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(QUANT_MUTANTS))
+def test_quant_mutant_is_caught(name):
+    import types
+
+    find, repl = QUANT_MUTANTS[name]
+    src = open(Q_SRC).read()
+    assert src.count(find) == 1, f"mutation site for {name} not unique/absent"
+    mod = types.ModuleType(f"quant_mutant_{name}")
+    exec(compile(src.replace(find, repl), f"<mutant {name}>", "exec"), mod.__dict__)
+    failures = []
+    for pin in P.QUANT_PINS:
+        try:
+            ok, detail = pin(mod)
+        except Exception as e:  # a crash also counts as caught
+            ok, detail = False, repr(e)
+        if not ok:
+            failures.append(pin.__name__)
+    assert failures, f"mutant {name} passed every pin"

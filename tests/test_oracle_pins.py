@@ -15,6 +15,14 @@ def test_pin(pin):
     assert ok, detail
 
 
+@pytest.mark.parametrize("pin", P.QUANT_PINS, ids=lambda f: f.__name__)
+def test_quant_pin(pin):
+    from oracle import quant
+
+    ok, detail = pin(quant)
+    assert ok, detail
+
+
 @pytest.mark.parametrize("pin", P.BOND_FILTER_PINS, ids=lambda f: f.__name__)
 def test_bond_filter_pin(pin):
     from oracle import bond_filter as BF
