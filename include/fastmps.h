@@ -87,7 +87,14 @@ typedef struct fastmps_options {
     void *stream;           /* cudaStream_t to run on; NULL = a stream owned by the handle */
     int fused_measure;      /* BF16 modes: 0 (default) = separate measurement kernel, overlapped
                                on a second stream when there are several micro-batches;
-                               1 = measurement warps inside the contraction kernel */
+                               1 = measurement warps inside the contraction kernel;
+                               2 = single pass (Algorithm 2 fused into the contraction's
+                               epilogue): a thread-block cluster holds a sample's whole row in
+                               tensor memory, combines the per-tile sums of squares through
+                               distributed shared memory and writes only the selected,
+                               renormalised block -- no FP32 scratch.  Sites whose row does not
+                               fit one cluster (more than 32 column tiles, or column tiles not
+                               a multiple of 64 wide) take mode 0. */
 } fastmps_options;
 
 typedef struct fastmps_ctx *fastmps_handle;
@@ -107,21 +114,26 @@ typedef struct fastmps_stats {
 } fastmps_stats;
 
 /* Fill *opt with the defaults: FP32, resident, automatic micro-batch, no autotune, own stream,
- * separate measurement kernel. */
+ * separate measurement kernel.  (Precision: Sec. 3.3; residency: Sec. 3.1; micro-batch: the
+ * paper's N2 samples per contraction of Algorithm 2.) */
 void fastmps_default_options(fastmps_options *opt);
 
 /*
  * Create a handle on CUDA device `device`.  opt may be NULL (defaults).
+ * (Library plumbing: one handle holds one MPS on one device, the paper's
+ * per-process state of Sec. 3.1 reduced to a single GPU.)
  * Fails with FASTMPS_ERR_UNSUPPORTED if the device is not compute capability
  * 10.3 (the library is built for sm_103a only).  *out receives the handle
  * (NULL on failure).
  */
 int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt);
 
-/* Release every resource of the handle.  NULL is accepted; a handle must not be used afterwards. */
+/* Release every resource of the handle.  NULL is accepted; a handle must not be used afterwards.
+ * (Plumbing, no counterpart in the paper.) */
 void fastmps_destroy(fastmps_handle h);
 
 /*
+ * (Plumbing, no counterpart in the paper.)
  * Message of the last failure on h (empty string if none).  With h == NULL,
  * the message of the last failed fastmps_create in this process.
  * The pointer stays valid until the next call on the same handle.
@@ -129,7 +141,9 @@ void fastmps_destroy(fastmps_handle h);
 const char *fastmps_last_error(fastmps_handle h);
 
 /*
- * Load site k: A is host or device memory (detected with
+ * Load site k (Sec. 2.2: the site tensors of the MPS, here right-canonical
+ * A_k[chi_l][d][chi_r]; Sec. 3.3.2: kept in a compact low-precision format for
+ * storage and transfer in the BF16 modes): A is host or device memory (detected with
  * cudaPointerGetAttributes), shape [chi_l][d][chi_r] row-major, interleaved
  * complex of type dtype.  The tensor is copied and repacked into
  * the handle's arithmetic format (complex64, or BF16 planes of the real
@@ -141,7 +155,8 @@ const char *fastmps_last_error(fastmps_handle h);
 int fastmps_load_site(fastmps_handle h, int k, int chi_l, int d, int chi_r, const void *A, int dtype);
 
 /*
- * Pool extension for chains that reuse tensors (e.g. a pool of 16 interior
+ * Pool extension (Sec. 3.1: site tensors are loaded once and streamed to the
+ * compute while the previous site runs) for chains that reuse tensors (e.g. a pool of 16 interior
  * isometries shared by thousands of sites): load pool entry j (same layout
  * and rules as fastmps_load_site), then map site k to it.  A mapped site uses
  * the pool entry until it is mapped again or loaded with fastmps_load_site.
@@ -150,7 +165,10 @@ int fastmps_load_pool(fastmps_handle h, int j, int chi_l, int d, int chi_r, cons
 int fastmps_map_site(fastmps_handle h, int k, int j);
 
 /*
- * Draw N samples, rows n = 0 .. N-1.
+ * Draw N samples, rows n = 0 .. N-1 (Sec. 2.2 sampling workflow, Fig. 1: the
+ * site-by-site contraction of every sample's left environment; Algorithm 2:
+ * probabilities, cumulative sum, threshold draw and left-environment update;
+ * Sec. 3.3.1: per-sample rescaling, here the exact renormalisation).
  *   bond_dims   host array of M+1 ints with bond_dims[0] = bond_dims[M] = 1;
  *               site k must be loaded with shape (bond_dims[k], d, bond_dims[k+1]).
  *   out_samples N*M bytes, row n = sample n (out_samples[n*M + k] = s_k), or NULL.
@@ -161,6 +179,8 @@ int fastmps_sample(fastmps_handle h, int M, int d, const int *bond_dims, int64_t
                    uint8_t *out_samples, double *out_logprob);
 
 /*
+ * (Sec. 3.1 data parallelism: disjoint row ranges on different devices or calls
+ * give the rows of one large run, since the uniform is keyed by the global n.)
  * As fastmps_sample for rows n = n0 .. n0+N-1 (output row i is sample n0+i)
  * and Philox counter word `job`.  trace_rows > 0 with trace_probs != NULL
  * records the normalised conditionals w_s / Z of the first trace_rows rows at
@@ -172,15 +192,28 @@ int fastmps_sample_ex(fastmps_handle h, int M, int d, const int *bond_dims, int6
                       int64_t trace_rows, double *trace_probs);
 
 /*
+ * As fastmps_sample_ex, with the conditionals traced for an arbitrary list of
+ * call rows (for parity checks of rows anywhere in a large call, e.g. in
+ * every micro-batch).  trace_list: n_trace distinct call rows in [0, N), host
+ * memory; trace_probs[(k * n_trace + i) * d + s] = w_s / Z of call row
+ * trace_list[i] at site k (host or device, M * n_trace * d doubles).  The
+ * conditionals are those of Algorithm 2's probability line (Sec. 2.2); row
+ * lists with a repeated or out-of-range row give FASTMPS_ERR_INVALID_ARG.
+ */
+int fastmps_sample_traced(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N,
+                          uint64_t seed, uint32_t job, uint8_t *out_samples, double *out_logprob,
+                          const int64_t *trace_list, int64_t n_trace, double *trace_probs);
+
+/*
  * fastmps_sample_noalloc -- sampling that allocates no memory.  (An addition
  * of this library for callers that cannot allocate; the paper has no
  * counterpart.)
  *
  * Same result as fastmps_sample_ex for rows n0 .. n0+N-1 (no trace), for
- * callers that may not call cudaMalloc while they sample: code inside CUDA
- * stream capture, runtimes whose device memory belongs to their own caching
- * allocator or a fixed budget, services that forbid allocation after
- * start-up.  Every per-call buffer (left operands, contraction scratch,
+ * callers that may not call cudaMalloc while they sample: runtimes whose
+ * device memory belongs to their own caching allocator or a fixed budget,
+ * and services that allocate only at start-up so that their memory use
+ * cannot grow or fragment later.  Every per-call buffer (left operands, contraction scratch,
  * outcomes, log-probabilities, error word) is carved from one static device
  * array of 64 MiB that each device loading this library holds until the
  * process exits; the call makes no cudaMalloc, cudaFree or other allocating
@@ -202,8 +235,9 @@ int fastmps_sample_noalloc(fastmps_handle h, int M, int d, const int *bond_dims,
 
 /*
  * Batched sampling of many independent MPS in one engine call (the paper's
- * many-sample data parallelism extended to many chains; chains may differ in
- * M, d, bond dimensions and sample count).
+ * many-sample data parallelism of Sec. 3.1 extended to many chains; chains may
+ * differ in M, d, bond dimensions (Sec. 3.4.2: site-varying bond dimensions)
+ * and sample count).
  *
  * Each job names a handle `chain` whose sites hold that MPS (loaded with
  * fastmps_load_site / fastmps_load_pool); every chain must live on the
@@ -322,7 +356,7 @@ int fastmps_bond_filter(int M, int d, const int *bond_in, const double *const *l
 int fastmps_load_site_vidal_truncated(fastmps_handle h, int k, int chi_l, int d, int chi_r, const void *Gamma,
                                       const void *Lambda, int dtype, int keep_l, int keep_r);
 
-/* Statistics of the last fastmps_sample* call. */
+/* Statistics of the last fastmps_sample* call (measurement plumbing; the paper has no counterpart). */
 int fastmps_get_stats(fastmps_handle h, fastmps_stats *out);
 
 /*
@@ -336,7 +370,7 @@ int fastmps_get_stats(fastmps_handle h, fastmps_stats *out);
  */
 int fastmps_selftest_bounded_wait(int device, double limit_ms, int *status, double *waited_ms);
 
-/* Library version string (static storage). */
+/* Library version string (static storage; plumbing, no counterpart in the paper). */
 const char *fastmps_version(void);
 
 #ifdef __cplusplus

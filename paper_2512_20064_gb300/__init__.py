@@ -22,7 +22,7 @@ from .native import LIB, build
 __all__ = [
     "FastMPSError", "Sampler", "load_library", "build", "PRECISIONS", "RESIDENCIES",
     "fastmps_create", "fastmps_destroy", "fastmps_last_error", "fastmps_load_site", "fastmps_load_pool",
-    "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_sample_noalloc", "fastmps_sample_batch",
+    "fastmps_map_site", "fastmps_sample", "fastmps_sample_ex", "fastmps_sample_traced", "fastmps_sample_noalloc", "fastmps_sample_batch",
     "fastmps_get_stats", "fastmps_load_site_vidal", "fastmps_load_pool_vidal", "fastmps_displacement",
     "fastmps_sample_displaced", "fastmps_bond_filter", "fastmps_load_site_vidal_truncated",
     "fastmps_version",
@@ -34,6 +34,7 @@ ERR_NAMES = {-1: "INVALID_ARG", -2: "SHAPE", -3: "NOT_LOADED", -4: "OOM", -5: "C
              -7: "UNSUPPORTED", -8: "NUMERIC"}
 PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16x3": 2, "bf16x3l": 3, "bf16x4": 4, "fp8x1": 5, "fp8x2": 6}
 RESIDENCIES = {"hbm": 0, "host_stream": 1}
+MEASUREMENTS = {"separate": 0, "cta": 1, "cluster": 2}
 C64, C128 = 0, 1
 
 
@@ -121,6 +122,10 @@ def load_library(path: str | None = None, build_if_missing: bool = True) -> ctyp
                                           ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
         lib.fastmps_sample_ex.restype = ctypes.c_int
+        lib.fastmps_sample_traced.argtypes = [H, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
+                                              ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+        lib.fastmps_sample_traced.restype = ctypes.c_int
         lib.fastmps_sample_noalloc.argtypes = [H, ctypes.c_int, ctypes.c_int, P(ctypes.c_int), ctypes.c_int64,
                                                ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                                ctypes.c_void_p]
@@ -338,13 +343,24 @@ def fastmps_sample_ex(h, M: int, d: int, bonds, n0: int, N: int, seed: int, job:
                                          trace_rows, _ptr(trace_probs)))
 
 
+def fastmps_sample_traced(h, M: int, d: int, bonds, n0: int, N: int, seed: int, job: int, out_samples,
+                          out_logprob, trace_list, trace_probs) -> None:
+    """As ``fastmps_sample_ex``, tracing the conditionals of the listed call rows (any rows of the call)."""
+    lib = load_library()
+    b = (ctypes.c_int * (M + 1))(*[int(x) for x in bonds])
+    rows = np.ascontiguousarray(np.asarray(trace_list, dtype=np.int64))
+    _check(lib, h, lib.fastmps_sample_traced(h, M, d, b, n0, N, seed, job, _ptr(out_samples), _ptr(out_logprob),
+                                             rows.ctypes.data if rows.size else None, rows.size, _ptr(trace_probs)))
+
+
 def fastmps_sample_noalloc(h, M: int, d: int, bonds, n0: int, N: int, seed: int, job: int, out_samples,
                            out_logprob) -> None:
     """Sampling that allocates nothing (static 64 MiB device scratch); outputs must be device memory.
 
-    For callers that cannot allocate while sampling (inside CUDA stream capture, under a caching
-    allocator or a fixed memory budget).  Make the first call on a device before any stream capture;
-    calls that overlap on the GPU share the scratch and must be serialised."""
+    For callers that cannot allocate device memory while they sample (memory owned by their own
+    caching allocator, a fixed budget, a service that allocates only at start-up).  The first call on
+    a device looks up the scratch address and should come before any stream capture; calls that
+    overlap on the GPU share the scratch and must be serialised."""
     lib = load_library()
     b = (ctypes.c_int * (M + 1))(*[int(x) for x in bonds])
     _check(lib, h, lib.fastmps_sample_noalloc(h, M, d, b, n0, N, seed, job, _ptr(out_samples), _ptr(out_logprob)))
@@ -389,9 +405,12 @@ class Sampler:
     """A handle of the library: load site tensors once, then sample many times."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", residency: str = "hbm", max_microbatch: int = 0,
-                 stream=None, fused_measure: bool = False, autotune: bool = False):
+                 stream=None, fused_measure=False, autotune: bool = False):
+        """``fused_measure``: False / "separate" (measurement kernel after each contraction), True / "cta"
+        (measurement warps inside the contraction kernel), "cluster" (single-pass cluster kernel, no
+        scratch, where a site's row fits one cluster)."""
         o = fastmps_default_options()
-        o.fused_measure = int(bool(fused_measure))
+        o.fused_measure = MEASUREMENTS[fused_measure] if isinstance(fused_measure, str) else int(bool(fused_measure))
         o.autotune = int(bool(autotune))
         o.precision = PRECISIONS[precision]
         o.residency = RESIDENCIES[residency]
@@ -451,18 +470,23 @@ class Sampler:
         return fastmps_displacement(self.h, mu, d)
 
     def sample(self, bonds, d: int, N: int, seed: int, n0: int = 0, job: int = 0, out_samples=None,
-               out_logprob=None, trace_rows: int = 0, mu=None):
+               out_logprob=None, trace_rows: int = 0, mu=None, trace_list=None):
         """Draw rows ``n0 .. n0+N-1``.  Returns ``(samples[N, M] uint8, logprob[N] float64[, trace[M, R, d]])``.
 
         Outputs are numpy arrays unless ``out_samples`` / ``out_logprob`` are given
         (numpy arrays or torch tensors, host or CUDA).  ``mu`` (shape (M, N), complex):
-        per-sample GBS displacement amplitudes (Sec. 3.4.1).
+        per-sample GBS displacement amplitudes (Sec. 3.4.1).  The trace holds the conditionals
+        of call rows ``0 .. trace_rows-1``, or of the call rows in ``trace_list``.
         """
         M = len(bonds) - 1
         if out_samples is None:
             out_samples = np.empty((N, M), np.uint8)
         if out_logprob is None:
             out_logprob = np.empty(N, np.float64)
+        if trace_list is not None:
+            trace = np.empty((M, len(trace_list), d), np.float64)
+            fastmps_sample_traced(self.h, M, d, bonds, n0, N, seed, job, out_samples, out_logprob, trace_list, trace)
+            return out_samples, out_logprob, trace
         trace = np.empty((M, trace_rows, d), np.float64) if trace_rows > 0 else None
         if mu is not None:
             fastmps_sample_displaced(self.h, M, d, bonds, n0, N, seed, job, mu, out_samples, out_logprob,

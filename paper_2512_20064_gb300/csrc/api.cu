@@ -137,7 +137,7 @@ struct fastmps_ctx {
     std::map<int, int> site_pool;                        // site k -> pool entry j
     // work buffers (grow only)
     DevBuf V[2][3];  // [ping-pong][plane]  BF16 planes, or V[x][0] FP32
-    DevBuf Y[2], P[2], logp, O, Dout, Dlogp, trace, err;
+    DevBuf Y[2], P[2], logp, O, Dout, Dlogp, trace, trace_slot, err;
     DevBuf staging;  // device copy of a tensor being loaded
     DevBuf lam;      // device copy of the Schmidt coefficients of a Vidal-form site being loaded
     DevBuf mu;       // device copy of host displacement amplitudes (displaced sampling)
@@ -558,9 +558,10 @@ const float *displacement_table(fastmps_handle h, int d) {
 }
 
 // mu_dev (nullable, device): displaced sampling, amplitude of call row i at site k at mu_dev[k * ld_mu + i].
+// trace_list (nullable, host): the trace_rows call rows to trace, in place of rows 0 .. trace_rows-1.
 int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int64_t N, uint64_t seed, uint32_t job,
                uint8_t *out_samples, double *out_logprob, int64_t trace_rows, double *trace_probs,
-               const float2 *mu_dev = nullptr, int64_t ld_mu = 0) {
+               const float2 *mu_dev = nullptr, int64_t ld_mu = 0, const int64_t *trace_list = nullptr) {
     auto t_start = std::chrono::steady_clock::now();
     h->stats = fastmps_stats{};
     if (M < 1 || !bonds || N < 0 || n0 < 0) return fail(h, FASTMPS_ERR_INVALID_ARG, "need M >= 1, bonds, N >= 0, n0 >= 0");
@@ -569,6 +570,8 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     if (trace_rows < 0 || (trace_rows > 0 && !trace_probs))
         return fail(h, FASTMPS_ERR_INVALID_ARG, "trace_rows > 0 needs trace_probs");
     std::vector<Tensor *> ts(M);
+    std::vector<char> on_cluster(M, 0);  // single-pass cluster contraction + measurement at site k
+    const bool want_cluster = h->opt.fused_measure == 2 && is_bf16(h) && !is_fp8(h) && !mu_dev;
     int ldV = 64;
     int ncols_max = 0, ldP_max = 0;
     double flops = 0;
@@ -583,8 +586,14 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                                                   std::to_string(bonds[k + 1]) + ")");
         ts[k] = t;
         ldV = std::max(ldV, t->L.K_pad);
-        ncols_max = std::max(ncols_max, t->L.ncols);
-        ldP_max = std::max(ldP_max, t->L.ncols / t->L.bn);
+        int cC = 0, cT = 0;
+        on_cluster[k] = want_cluster && cluster_plan(t->L, &cC, &cT) &&
+                        cluster_capacity(plan_of(h->opt.precision).a_planes, plan_of(h->opt.precision).b_planes,
+                                         t->L) > 0;
+        if (!on_cluster[k]) {
+            ncols_max = std::max(ncols_max, t->L.ncols);
+            ldP_max = std::max(ldP_max, t->L.ncols / t->L.bn);
+        }
         flops += 8.0 * bonds[k] * d * bonds[k + 1];
     }
     const PrecisionPlan plan = plan_of(h->opt.precision);
@@ -600,7 +609,10 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     // ---- plan ---------------------------------------------------------------
     const int64_t N_pad = roundup(N, 128);
     int64_t N2;
-    if (h->opt.max_microbatch > 0) {
+    if (ncols_max == 0) {
+        // every site runs the single-pass cluster kernel: no scratch, all rows in one launch per site
+        N2 = h->opt.max_microbatch > 0 ? std::max<int64_t>(128, h->opt.max_microbatch / 128 * 128) : N_pad;
+    } else if (h->opt.max_microbatch > 0) {
         N2 = std::max<int64_t>(128, h->opt.max_microbatch / 128 * 128);
     } else {
         // FP32 scratch budget per micro-batch buffer; with several micro-batches per site the
@@ -628,12 +640,13 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             if (!h->V[x][p].ensure((size_t)N_pad * ldV * elem))
                 return fail(h, FASTMPS_ERR_OOM, "left-operand allocation failed");
     // BF16 modes measure inside the contraction kernel (no second launch, one scratch buffer)
-    const bool fused = bf16 && !fp8 && h->opt.fused_measure && !mu_dev;
+    const bool fused = bf16 && !fp8 && h->opt.fused_measure == 1 && !mu_dev;
     const int nybuf = (J > 1 && !fused) ? 2 : 1;
 
-    for (int b = 0; b < nybuf; ++b)
-        if (!h->Y[b].ensure((size_t)N2 * ncols_max * 4) || !h->P[b].ensure((size_t)N2 * ldP_max * 4))
-            return fail(h, FASTMPS_ERR_OOM, "scratch allocation failed");
+    if (ncols_max > 0)
+        for (int b = 0; b < nybuf; ++b)
+            if (!h->Y[b].ensure((size_t)N2 * ncols_max * 4) || !h->P[b].ensure((size_t)N2 * ldP_max * 4))
+                return fail(h, FASTMPS_ERR_OOM, "scratch allocation failed");
     if (!h->logp.ensure((size_t)N_pad * 8) || !h->O.ensure((size_t)M * N_pad) || !h->err.ensure(sizeof(int)))
         return fail(h, FASTMPS_ERR_OOM, "work-buffer allocation failed");
     const bool samples_dev = is_device_ptr(out_samples);
@@ -642,8 +655,24 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     if (out_samples && !samples_dev && !h->Dout.ensure((size_t)N * M))
         return fail(h, FASTMPS_ERR_OOM, "output staging allocation failed");
     double *trace_buf = nullptr;
+    const int *trace_slot = nullptr;
+    if (trace_list && trace_rows > 0) {
+        // per-row slot map of the listed rows (distinct, inside the call)
+        std::vector<int> slot((size_t)N, -1);
+        for (int64_t i = 0; i < trace_rows; ++i) {
+            const int64_t r = trace_list[i];
+            if (r < 0 || r >= N || slot[(size_t)r] >= 0)
+                return fail(h, FASTMPS_ERR_INVALID_ARG, "trace rows must be distinct call rows in [0, N)");
+            slot[(size_t)r] = (int)i;
+        }
+        if (!h->trace_slot.ensure((size_t)N * sizeof(int))) return fail(h, FASTMPS_ERR_OOM, "trace allocation failed");
+        e = cudaMemcpyAsync(h->trace_slot.p, slot.data(), (size_t)N * sizeof(int), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vector is released on return
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of the trace rows");
+        trace_slot = h->trace_slot.as<int>();
+    }
     if (trace_rows > 0) {
-        trace_rows = std::min(trace_rows, N);
+        if (!trace_list) trace_rows = std::min(trace_rows, N);
         if (trace_dev) trace_buf = trace_probs;
         else {
             if (!h->trace.ensure((size_t)M * trace_rows * d * 8)) return fail(h, FASTMPS_ERR_OOM, "trace allocation failed");
@@ -684,6 +713,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     EventTimer timer(h);
     cudaStream_t ms = h->measure_stream;
     int64_t g = 0;  // micro-batch counter over the whole call
+    int64_t last_measured = -1;  // micro-batch whose measurement ran last on the measurement stream
     // the measurement stream starts after everything queued so far on the compute stream
     {
         cudaEvent_t ev = timer.get();
@@ -764,6 +794,45 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             const int64_t rows = std::min<int64_t>(N2, N - r0);
             const int64_t rows_pad = roundup(rows, 128);
             const int yb = (int)(g % nybuf);
+            if (on_cluster[k]) {
+                // the rows come from the last measurement issued on the measurement stream, if any
+                if (last_measured >= 0) cudaStreamWaitEvent(st, h->measure_done[last_measured % nybuf], 0);
+                MeasureArgs ma{};
+                ma.d = d;
+                ma.chi_r = L.chi_r;
+                ma.Cs = L.Cs;
+                ma.tiles_per_s = L.tiles_per_s;
+                ma.rows = (int)rows;
+                ma.seed = seed;
+                ma.n_base = (uint64_t)(n0 + r0);
+                ma.k = (uint32_t)k;
+                ma.job = job;
+                ma.row0 = r0;
+                ma.ld_next = ldV;
+                ma.K_next = K_next;
+                ma.V32 = nullptr;
+                for (int p = 0; p < 3; ++p) ma.Vp[p] = Vp[nxt][p];
+                ma.nplanes = planes;
+                ma.outcomes = h->O.as<uint8_t>() + (int64_t)k * N_pad + r0;
+                ma.logp = h->logp.as<double>();
+                ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
+                ma.trace_rows = (int)trace_rows;
+                ma.trace_slot = trace_slot;
+                ma.err = d_err;
+                ta.row0 = r0;
+                ta.rows_pad = (int)rows_pad;
+                ta.has_tmY = false;
+                cudaEvent_t c0 = timer.get(), c1 = timer.get();
+                cudaEventRecord(c0, st);
+                e = launch_contract_tc_cluster(ta, L, (int)rows, d_err, st, ma);
+                if (e != cudaSuccess) return cuda_fail(h, e, "cluster contraction launch");
+                cudaEventRecord(c1, st);
+                timer.contract.push_back({c0, c1});
+                h->stats.launches += 1;
+                h->stats.contract_launches += 1;
+                last_measured = -1;
+                continue;
+            }
             // the scratch buffer is free once the measurement two micro-batches back is done; with one
             // micro-batch per site the left rows of this contraction come from the previous measurement
             if (!fused && g >= nybuf) cudaStreamWaitEvent(st, h->measure_done[yb], 0);
@@ -800,6 +869,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.logp = h->logp.as<double>();
             ma.trace = trace_buf ? trace_buf + (int64_t)k * trace_rows * d : nullptr;
             ma.trace_rows = (int)trace_rows;
+            ma.trace_slot = trace_slot;
             ma.err = d_err;
             ma.mu = mu_dev ? mu_dev + (int64_t)k * ld_mu + r0 : nullptr;
             ma.disp_tab = disp_tab;
@@ -831,13 +901,14 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 cudaEventRecord(m1, ms);
                 cudaEventRecord(h->measure_done[yb], ms);
                 timer.measure.push_back({m0, m1});
+                last_measured = g;
             }
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
         }
     }
     // the compute stream resumes after the last measurement
-    if (g > 0 && !fused) cudaStreamWaitEvent(st, h->measure_done[(g - 1) % nybuf], 0);
+    if (last_measured >= 0) cudaStreamWaitEvent(st, h->measure_done[last_measured % nybuf], 0);
 
     // ---- outputs -------------------------------------------------------------
     if (out_samples) {
@@ -1031,6 +1102,23 @@ int fastmps_sample_ex(fastmps_handle h, int M, int d, const int *bond_dims, int6
     cudaSetDevice(h->device);
     try {
         return run_sample(h, M, d, bond_dims, n0, N, seed, job, out_samples, out_logprob, trace_rows, trace_probs);
+    } catch (const std::bad_alloc &) {
+        return fail(h, FASTMPS_ERR_OOM, "out of host memory");
+    } catch (...) {
+        return fail(h, FASTMPS_ERR_CUDA, "unexpected host exception");
+    }
+}
+
+int fastmps_sample_traced(fastmps_handle h, int M, int d, const int *bond_dims, int64_t n0, int64_t N, uint64_t seed,
+                          uint32_t job, uint8_t *out_samples, double *out_logprob, const int64_t *trace_list,
+                          int64_t n_trace, double *trace_probs) {
+    if (!h) return FASTMPS_ERR_INVALID_ARG;
+    if (n_trace < 0 || (n_trace > 0 && (!trace_list || !trace_probs)))
+        return fail(h, FASTMPS_ERR_INVALID_ARG, "n_trace > 0 needs trace_list and trace_probs");
+    cudaSetDevice(h->device);
+    try {
+        return run_sample(h, M, d, bond_dims, n0, N, seed, job, out_samples, out_logprob, n_trace, trace_probs,
+                          nullptr, 0, n_trace > 0 ? trace_list : nullptr);
     } catch (const std::bad_alloc &) {
         return fail(h, FASTMPS_ERR_OOM, "out of host memory");
     } catch (...) {

@@ -327,12 +327,14 @@ __device__ __forceinline__ void displaced_outputs(const MeasureArgs &a, int row,
     const bool ok = (Z32 > 0.f) && isfinite(Z32) && (wsel > 0.f);
     const int64_t grow = a.row0 + row;
     a.outcomes[row] = (uint8_t)sstar;
-    if (ok) a.logp[grow] += (double)(logf(wsel) - logf(Z32));
+    if (ok) a.logp[grow] += log((double)wsel / (double)Z32);  // FP64 log of the FP32 sums' ratio
     else atomicExch(a.err, (int)kDevNumeric);
-    if (a.trace && grow < a.trace_rows) {
+    const int64_t slot = a.trace ? (a.trace_slot ? (int64_t)a.trace_slot[grow] : (grow < a.trace_rows ? grow : -1))
+                                 : -1;
+    if (slot >= 0) {
 #pragma unroll
         for (int s = 0; s < DMAX; ++s)
-            if (s < d) a.trace[grow * d + s] = ok ? (double)w[s] / (double)Z32 : 0.0;
+            if (s < d) a.trace[slot * d + s] = ok ? (double)w[s] / (double)Z32 : 0.0;
     }
 }
 

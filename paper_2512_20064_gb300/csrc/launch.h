@@ -81,6 +81,15 @@ struct MeasureArgs;
 // kernel (one thread block per m-tile at a time; grid = min(m-tiles, SMs)).
 cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int num_sms,
                                int *d_err, cudaStream_t st, const MeasureArgs *fused = nullptr);
+// Single-pass cluster variant (no scratch): true if the site's row fits one cluster's tensor memory
+// (C CTAs of T n-tiles each, C <= 16, the n-tile width a multiple of 64).
+bool cluster_plan(const SiteLayout &L, int *C, int *T);
+// Clusters of the site's plan that can be resident at once on the current device (0: not runnable).
+int cluster_capacity(int a_planes, int b_planes, const SiteLayout &L);
+// Contraction + measurement of rows_valid rows in one launch; m describes the draw and the next left
+// rows (BF16 planes; Y, P unused).  *clusters_out (nullable): clusters launched.
+cudaError_t launch_contract_tc_cluster(const TcArgs &a, const SiteLayout &L, int rows_valid, int *d_err,
+                                       cudaStream_t st, const MeasureArgs &m, int *clusters_out = nullptr);
 
 // ---- measurement (Algorithm 2) --------------------------------------------
 struct MeasureArgs {
@@ -109,7 +118,8 @@ struct MeasureArgs {
     uint8_t *outcomes;        // [rows] outcome bytes of this site (site-major buffer slice)
     double *logp;             // [rows] accumulated log-probability
     double *trace;            // nullable: [trace_rows][d] normalised conditionals of this site
-    int trace_rows;
+    int trace_rows;           // traced rows: call rows 0 .. trace_rows-1, or the rows trace_slot lists
+    const int *trace_slot = nullptr;  // nullable: per call row, its trace slot (-1: not traced)
     int *err;
 };
 void launch_measure(const MeasureArgs &a, cudaStream_t st);

@@ -19,9 +19,10 @@ namespace fastmps {
 //  * C_s = w_0 + ... + w_s in s order (FP64), Z = C_{d-1}, Philox uniform u,
 //    s* = #{s < d-1 : C_s < u Z}: the decision is taken in FP64 as in the
 //    oracle;
-//  * log p accumulates log w_{s*} - log Z in FP64; each logarithm is taken in
-//    FP32 (w and Z are O(1) because the left vector is renormalised at every
-//    site, so the absolute error per site is ~1e-7).
+//  * log p accumulates log(w_{s*} / Z) in FP64: the ratio and its logarithm
+//    are taken in FP64 (one log per sample per site, O(N M) work), since a
+//    rare outcome has w_{s*} << 1 and the absolute error of an FP32 log
+//    there would add up over thousands of sites.
 // Phase 2, a warp per sample (measure_write_row): the selected block y_{s*} is scaled
 // by 1/sqrt(w_{s*}) (FP32; the scale cancels in every later ratio w/Z) and
 // written as the next left row -- FP32, or BF16 planes of successive
@@ -162,13 +163,15 @@ __device__ __forceinline__ int measure_draw(const MeasureArgs &a, int row, float
         const bool ok = (Z > 0.0) && isfinite(Z) && (ws > 0.0);
         const int64_t grow = a.row0 + row;
         a.outcomes[row] = (uint8_t)sstar;
-        if (ok) a.logp[grow] += (double)(logf((float)ws) - logf((float)Z));
+        if (ok) a.logp[grow] += log(ws / Z);
         else atomicExch(a.err, (int)kDevNumeric);
-        if (a.trace && grow < a.trace_rows) {
+        const int64_t slot = a.trace ? (a.trace_slot ? (int64_t)a.trace_slot[grow] : (grow < a.trace_rows ? grow : -1))
+                                     : -1;
+        if (slot >= 0) {
             for (int s = 0; s < a.d; ++s) {
                 double acc = 0.0;
                 for (int j = 0; j < T; ++j) acc += (double)__ldcg(Prow + s * T + j);
-                a.trace[grow * a.d + s] = ok ? acc / Z : 0.0;
+                a.trace[slot * a.d + s] = ok ? acc / Z : 0.0;
             }
         }
         scale = ok ? rsqrtf((float)ws) : 0.f;

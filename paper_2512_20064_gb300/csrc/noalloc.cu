@@ -2,10 +2,9 @@
 // from one fixed device array instead of allocated memory.
 //
 // Who needs it: callers that may not call cudaMalloc while they sample --
-// code running inside CUDA stream capture (a graph that must not contain
-// allocations), runtimes whose device memory is owned by their own caching
-// allocator or a fixed budget, and long-running services that forbid
-// allocation after start-up so that memory use cannot grow or fragment.
+// runtimes whose device memory is owned by their own caching allocator or a
+// fixed budget, and long-running services that forbid allocation after
+// start-up so that memory use cannot grow or fragment.
 // fastmps_sample grows per-handle work buffers with cudaMalloc on demand;
 // this entry point instead uses kNoAllocScratchBytes of static device memory
 // that every device which loads this library holds until the process exits.

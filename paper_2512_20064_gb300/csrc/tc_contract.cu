@@ -27,6 +27,20 @@
 // outcomes and write the renormalised selected blocks as the next left rows
 // (Algorithm 2) while the tensor cores work on the next m-tile.
 //
+// Cluster variant (single pass, no scratch): a thread-block cluster of C CTAs
+// covers one m-tile's whole row, CTA rank r computing n-tiles r*T .. r*T+T-1
+// and keeping their accumulators in tensor memory.  The epilogue warps square
+// and sum their tiles per row, publish the 128 per-tile sums in shared memory
+// and signal every CTA of the cluster through a remote mbarrier arrive; each
+// CTA then reads all C*T partial sums of its rows through distributed shared
+// memory, combines them in FP64 in tile order (the same sums, in the same
+// order, as the two-pass measurement), draws the outcome -- identically in
+// every CTA -- and writes the columns of the selected block it holds,
+// scaled by 1/sqrt(w_{s*}), as BF16 planes of the next left row (Algorithm 2
+// fused after the contraction; Sec. 3.3.1 per-sample scaling).  Rank 0 writes
+// the outcome, log-probability and trace.  Nothing but the next left rows
+// leaves the chip.
+//
 // Every wait is bounded (common.cuh); on a timeout the kernel records an
 // error word, drains its own in-flight copies and MMAs, frees tensor memory
 // and returns.
@@ -56,6 +70,11 @@ constexpr uint32_t kAccStride = 256;
 constexpr uint32_t kATileBytes = kBM * kBK * 2;  // 16 KB
 constexpr int kMaxStages = 8;
 constexpr int kSmemLimit = 232448;           // 227 KB opt-in per block
+constexpr int kMaxClusterTiles = 32;         // cluster variant: n-tiles per m-tile (C * T)
+constexpr int kMaxClusterCTAs = 16;          // largest (non-portable) cluster
+constexpr uint32_t kClusterBytes = 64 + 4 * 128 * 4 * 2;  // 4 mbarriers + partial sums [2][T <= 4][128]
+
+enum TcMode : int { kTwoPass = 0, kFusedCta = 1, kClusterFused = 2 };
 
 struct TcParams {
     int num_m_tiles, num_n_tiles, num_k_blocks, bn;
@@ -71,6 +90,7 @@ struct TcParams {
     int ldP;
     int rows_valid;
     int *err;
+    int cl_T;  // cluster variant: n-tiles per CTA per m-tile (the cluster has num_n_tiles / cl_T CTAs)
     // fused measurement
     MeasureArgs m;
 };
@@ -114,10 +134,18 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity) 
 // The block's i-th tile.  Unfused: tiles are dealt round-robin in n-fastest
 // order.  Fused: the block owns m-tiles blockIdx.x, blockIdx.x + gridDim.x, ...
 // and visits all n-tiles of each (i % num_n_tiles == num_n_tiles - 1 ends an
-// m-tile).  Returns false past the last tile.
-template <bool kFused>
+// m-tile).  Cluster: the cluster owns m-tiles clusterid, clusterid + nclusters,
+// ... and CTA rank r visits n-tiles r*T .. r*T+T-1 of each.  Returns false past
+// the last tile.
+template <int kMode>
 __device__ __forceinline__ bool tile_of(const TcParams &p, int i, int &mt, int &nt) {
-    if (kFused) {
+    if (kMode == kClusterFused) {
+        const int q = i / p.cl_T;
+        nt = (int)cluster_ctarank() * p.cl_T + (i - q * p.cl_T);
+        mt = (int)cluster_id_x() + q * (int)cluster_count_x();
+        return mt < p.num_m_tiles;
+    }
+    if (kMode == kFusedCta) {
         const int q = i / p.num_n_tiles;
         nt = i - q * p.num_n_tiles;
         mt = blockIdx.x + q * gridDim.x;
@@ -129,12 +157,195 @@ __device__ __forceinline__ bool tile_of(const TcParams &p, int i, int &mt, int &
     return tile < p.num_m_tiles * p.num_n_tiles;
 }
 
-template <bool kFused, bool kFp8>
-__global__ void __launch_bounds__(kFused ? kThreadsFused : kThreads, 1)
+// ---------------------------------------------------------------------------
+// Cluster variant: draw of one row from the partial sums of squares of all
+// n-tiles of the row (pv[j] = sum over tile j, tiles in column order), exactly
+// as measure_draw does from the scratch P: w_s in FP64 in tile order, Z, the
+// Philox threshold, s* and log(w_{s*} / Z) in FP64.  The writer CTA (rank 0)
+// stores the outcome, the log-probability and the trace.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int cluster_draw(const MeasureArgs &a, int row, const float *pv, bool writer,
+                                            float *scale_out) {
+    const int T = a.tiles_per_s;
+    double Z = 0.0;
+    for (int s = 0; s < a.d; ++s) {
+        double acc = 0.0;
+        for (int j = 0; j < T; ++j) acc += (double)pv[s * T + j];
+        Z += acc;
+    }
+    const uint64_t n = a.n_base + (uint64_t)row;
+    const double t = sample_uniform(a.seed, n, a.k, a.job) * Z;
+    double C = 0.0, ws = 0.0;
+    int sstar = a.d - 1;
+    for (int s = 0; s < a.d; ++s) {
+        double acc = 0.0;
+        for (int j = 0; j < T; ++j) acc += (double)pv[s * T + j];
+        C += acc;
+        if (s == a.d - 1 || C >= t) {
+            sstar = s;
+            ws = acc;
+            break;
+        }
+    }
+    const bool ok = (Z > 0.0) && isfinite(Z) && (ws > 0.0);
+    if (writer) {
+        const int64_t grow = a.row0 + row;
+        a.outcomes[row] = (uint8_t)sstar;
+        if (ok) a.logp[grow] += log(ws / Z);
+        else atomicExch(a.err, (int)kDevNumeric);
+        const int64_t slot = a.trace ? (a.trace_slot ? (int64_t)a.trace_slot[grow] : (grow < a.trace_rows ? grow : -1))
+                                     : -1;
+        if (slot >= 0) {
+            for (int s = 0; s < a.d; ++s) {
+                double acc = 0.0;
+                for (int j = 0; j < T; ++j) acc += (double)pv[s * T + j];
+                a.trace[slot * a.d + s] = ok ? acc / Z : 0.0;
+            }
+        }
+    }
+    *scale_out = ok ? rsqrtf((float)ws) : 0.f;
+    return sstar;
+}
+
+// 32 consecutive entries (columns c0 .. c0+31 of the selected block, c0 a multiple of 32) of one next
+// left row: value * scale, zero at and beyond 2 chi_r, as BF16 planes of successive residuals.
+__device__ __forceinline__ void write_row_chunk(const MeasureArgs &a, int64_t grow, int c0, const uint32_t (&r)[32],
+                                                float scale) {
+    const int nreal = 2 * a.chi_r;
+    __nv_bfloat16 *d0 = a.Vp[0] + grow * a.ld_next + c0;
+    __nv_bfloat16 *d1 = a.Vp[1] + grow * a.ld_next + c0;
+    __nv_bfloat16 *d2 = a.nplanes > 2 ? a.Vp[2] + grow * a.ld_next + c0 : nullptr;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        __align__(16) __nv_bfloat16 p0[8], p1[8], p2[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int j = 8 * g + e;
+            const float x = (c0 + j < nreal) ? __uint_as_float(r[j]) * scale : 0.f;
+            write_planes(x, a.nplanes, p0[e], p1[e], p2[e]);
+        }
+        *reinterpret_cast<uint4 *>(d0 + 8 * g) = *reinterpret_cast<const uint4 *>(p0);
+        *reinterpret_cast<uint4 *>(d1 + 8 * g) = *reinterpret_cast<const uint4 *>(p1);
+        if (d2) *reinterpret_cast<uint4 *>(d2 + 8 * g) = *reinterpret_cast<const uint4 *>(p2);
+    }
+}
+
+// Epilogue warps (2..5) of the cluster variant.  part: [2][cl_T][128] partial sums of this CTA;
+// pready[b] / pfree[b]: count = cluster size, one remote arrive per CTA (b = m-tile parity).
+__device__ __forceinline__ void cluster_epilogue(const TcParams &p, uint32_t tmem_base, uint64_t *tfull,
+                                                 uint64_t *tempty, uint64_t *pready, uint64_t *pfree, float *part,
+                                                 volatile int *abort_flag, int warp, int lane) {
+    const int quad = warp & 3;  // tensor-memory lane quarter this warp may access
+    const int r = quad * 32 + lane;
+    const int T = p.cl_T;
+    const int NT = p.num_n_tiles;
+    const uint32_t C = (uint32_t)(NT / T);
+    const uint32_t rank = cluster_ctarank();
+    const int cid = (int)cluster_id_x(), ncl = (int)cluster_count_x();
+    const MeasureArgs &a = p.m;
+    const int tps = a.tiles_per_s;
+    const uint32_t part_addr = smem_u32(part);
+    int lt = 0;
+    for (int u = 0;; ++u) {
+        const int mt = cid + u * ncl;
+        if (mt >= p.num_m_tiles) break;
+        const int slot = u & 1;
+        const uint32_t use = (uint32_t)(u >> 1);
+        // this slot's partial sums may be overwritten once every CTA has read them (two m-tiles back)
+        if (use >= 1) {
+            const bool ok = mbar_wait_cluster_bounded(&pfree[slot], (use - 1) & 1u, abort_flag);
+            if (named_bar_any(1, 128, !ok)) {
+                record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                return;
+            }
+        }
+        // 1. sums of squares of this CTA's tiles, same order as the two-pass epilogue
+        for (int t = 0; t < T; ++t) {
+            const int buf = (lt + t) & 1;
+            const uint32_t tuse = (uint32_t)((lt + t) >> 1);
+            const bool ready = mbar_wait_bounded(&tfull[buf], tuse & 1u, abort_flag);
+            if (named_bar_any(1, 128, !ready)) {
+                record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                return;
+            }
+            tc_fence_after();
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)buf * kAccStride;
+            float ss = 0.f;
+            for (int ch = 0; ch < p.bn / 32; ++ch) {
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(taddr + (uint32_t)(ch * 32), v);
+                tc_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float x = __uint_as_float(v[j]);
+                    ss = fmaf(x, x, ss);
+                }
+            }
+            part[(slot * T + t) * 128 + r] = ss;
+        }
+        // 2. publish to every CTA of the cluster, then gather all partial sums of the row
+        named_bar_sync(1, 128);
+        if (threadIdx.x == 64) {
+            const uint32_t bar = smem_u32(&pready[slot]);
+            for (uint32_t c = 0; c < C; ++c) mbar_arrive_cluster(mapa_shared(bar, c));
+        }
+        const bool all = mbar_wait_cluster_bounded(&pready[slot], use & 1u, abort_flag);
+        if (named_bar_any(1, 128, !all)) {
+            record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+            return;
+        }
+        float pv[kMaxClusterTiles];
+#pragma unroll
+        for (int j = 0; j < kMaxClusterTiles; ++j) {
+            if (j < NT) {
+                const uint32_t owner = (uint32_t)(j / T);
+                const int t = j - (int)owner * T;
+                pv[j] = ld_shared_cluster_f32(mapa_shared(part_addr + (uint32_t)(((slot * T + t) * 128 + r) * 4), owner));
+            }
+        }
+        named_bar_sync(1, 128);
+        if (threadIdx.x == 64) {
+            const uint32_t bar = smem_u32(&pfree[slot]);
+            for (uint32_t c = 0; c < C; ++c) mbar_arrive_cluster(mapa_shared(bar, c));
+        }
+        // 3. the draw, identical in every CTA of the cluster
+        const int row = mt * kBM + r;
+        const bool valid = row < p.rows_valid;
+        int sstar = -1;
+        float scale = 0.f;
+        if (valid) sstar = cluster_draw(a, row, pv, rank == 0, &scale);
+        // 4. this CTA's columns of the selected block
+        for (int t = 0; t < T; ++t) {
+            const int j = (int)rank * T + t;
+            const int s_here = j / tps;
+            const int col0 = (j - s_here * tps) * p.bn;
+            const bool mine = valid && sstar == s_here;
+            if (!__any_sync(0xffffffffu, mine)) continue;  // tensor-memory loads are warp-collective
+            const int buf = (lt + t) & 1;
+            const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)buf * kAccStride;
+            for (int ch = 0; ch < p.bn / 32; ++ch) {
+                const int c0 = col0 + ch * 32;
+                if (c0 >= a.K_next) break;
+                uint32_t v[32];
+                tmem_ld_32x32b_x32(taddr + (uint32_t)(ch * 32), v);
+                tc_wait_ld();
+                if (mine) write_row_chunk(a, a.row0 + row, c0, v, scale);
+            }
+        }
+        tc_fence_before();
+        for (int t = 0; t < T; ++t) mbar_arrive(&tempty[(lt + t) & 1]);
+        lt += T;
+    }
+}
+
+template <int kMode, bool kFp8>
+__global__ void __launch_bounds__(kMode == kFusedCta ? kThreadsFused : kThreads, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
                    const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmY,
                    const TcParams p) {
+    constexpr bool kFused = kMode == kFusedCta;
+    constexpr bool kCluster = kMode == kClusterFused;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -152,6 +363,10 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *m_sstar = reinterpret_cast<int *>(tmem_slot + 4);   // [128]
     float *m_scale = reinterpret_cast<float *>(m_sstar + kBM);  // [128]
+    // cluster variant: behind the barrier region
+    uint64_t *pready = reinterpret_cast<uint64_t *>(reinterpret_cast<uint8_t *>(full) + kBarrierBytes);  // [2]
+    uint64_t *pfree = pready + 2;                                                                      // [2]
+    float *part = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(pready) + 64);  // [2][cl_T][128]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -169,6 +384,13 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             mbar_init(&mfull[r], 1);
             mbar_init(&mempty[r], kBM);
         }
+        if (kCluster) {
+            const uint32_t csize = (uint32_t)(p.num_n_tiles / p.cl_T);  // one arrive from every CTA
+            for (int b = 0; b < 2; ++b) {
+                mbar_init(&pready[b], csize);
+                mbar_init(&pfree[b], csize);
+            }
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -185,6 +407,8 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     }
     tc_fence_before();
     __syncthreads();
+    // cluster variant: every CTA's barriers are initialised before any remote arrive
+    if (kCluster) cluster_sync_all();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -197,7 +421,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             for (int s = 0; s < kMaxStages; ++s) last_parity[s] = -1;
             bool failed = false;
             int mt, nt;
-            for (int i = 0; !failed && tile_of<kFused>(p, i, mt, nt); ++i) {
+            for (int i = 0; !failed && tile_of<kMode>(p, i, mt, nt); ++i) {
                 const int y_a = p.row0 + mt * kBM;
                 const int y_b = nt * p.bn;
                 for (int kb = 0; kb < p.num_k_blocks; ++kb) {
@@ -238,7 +462,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             bool failed = false;
             bool issued = false;
             int mt, nt;
-            for (int i = 0; !failed && tile_of<kFused>(p, i, mt, nt); ++i, ++lt) {
+            for (int i = 0; !failed && tile_of<kMode>(p, i, mt, nt); ++i, ++lt) {
                 const int buf = lt & 1;
                 const uint32_t use = (uint32_t)(lt >> 1);
                 if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag)) {
@@ -293,6 +517,9 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             }
         }
         __syncwarp();
+    } else if (kCluster && warp < 6) {
+        // ---------------- cluster epilogue: warps 2..5 ----------------
+        cluster_epilogue(p, tmem_base, tfull, tempty, pready, pfree, part, abort_flag, warp, lane);
     } else if (warp < 6) {
         // ---------------- epilogue: warps 2..5 ----------------
         const int quad = warp & 3;  // tensor-memory lane quarter this warp may access
@@ -302,7 +529,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
         int mt, nt;
         int chunk = 0;  // chunks staged so far (alternating staging buffers)
         const bool group_sync = kFused || p.tma_store;
-        for (int i = 0; tile_of<kFused>(p, i, mt, nt); ++i, ++lt) {
+        for (int i = 0; tile_of<kMode>(p, i, mt, nt); ++i, ++lt) {
             const int buf = lt & 1;
             const uint32_t use = (uint32_t)(lt >> 1);
             const bool ready = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag);
@@ -421,6 +648,8 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
 
     tc_fence_before();
     __syncthreads();
+    // cluster variant: no CTA leaves while another may still read its partial sums or arrive on its barriers
+    if (kCluster) cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
@@ -497,21 +726,148 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     const CUtensorMap &ty = a.has_tmY ? a.tmY : a.tmA[0];  // unused when p.tma_store == 0
     cudaError_t e;
     if (a.fp8) {
-        e = cudaFuncSetAttribute(tc_contract_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc_contract_kernel<kTwoPass, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemLimit);
         if (e != cudaSuccess) return e;
-        tc_contract_kernel<false, true><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
+        tc_contract_kernel<kTwoPass, true><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
     } else if (fused) {
-        e = cudaFuncSetAttribute(tc_contract_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc_contract_kernel<kFusedCta, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemLimit);
         if (e != cudaSuccess) return e;
-        tc_contract_kernel<true, false><<<grid, kThreadsFused, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
+        tc_contract_kernel<kFusedCta, false><<<grid, kThreadsFused, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
     } else {
-        e = cudaFuncSetAttribute(tc_contract_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(tc_contract_kernel<kTwoPass, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kSmemLimit);
         if (e != cudaSuccess) return e;
-        tc_contract_kernel<false, false><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
+        tc_contract_kernel<kTwoPass, false><<<grid, kThreads, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, ty, p);
     }
+    return cudaGetLastError();
+}
+
+bool cluster_plan(const SiteLayout &L, int *C_out, int *T_out) {
+    if (L.bn % 64 != 0 || L.ncols % L.bn != 0) return false;
+    const int NT = L.ncols / L.bn;
+    if (NT > kMaxClusterTiles || L.K_pad < 64) return false;
+    // K_next <= Cs: the block's own columns cover the next row's padding up to its K extent
+    if ((int)(((2 * (int64_t)L.chi_r) + 63) / 64 * 64) > L.Cs) return false;
+    // the two 256-column accumulators hold all T tiles of an m-tile until its draw: T <= 2
+    for (int T = 1; T <= 2; ++T) {
+        if (NT % T != 0 || L.bn > (int)kAccStride || (T * 128 * 4 * 2) > (int)(kClusterBytes - 64)) continue;
+        const int C = NT / T;
+        if (C > kMaxClusterCTAs) continue;
+        *C_out = C;
+        *T_out = T;
+        return true;
+    }
+    return false;
+}
+
+namespace {
+
+// Launch configuration of the cluster kernel for a site layout and plane counts; returns the largest
+// number of clusters that can be resident at once (0: the configuration cannot run).
+int cluster_config(int a_planes, int b_planes, const SiteLayout &L, int C, cudaLaunchConfig_t &cfg,
+                   cudaLaunchAttribute *attr, size_t *smem_out, int *stages_out) {
+    const uint32_t stage_bytes = (uint32_t)a_planes * kATileBytes + (uint32_t)b_planes * (uint32_t)L.bn * 128;
+    const int stages = stages_for(stage_bytes, kClusterBytes);
+    if (stages < 2) return 0;
+    const size_t smem = (size_t)stages * stage_bytes + 1024 + kBarrierBytes + kClusterBytes;
+    auto kern = tc_contract_kernel<kClusterFused, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit) != cudaSuccess ||
+        (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+        cudaGetLastError();
+        return 0;
+    }
+    cfg = cudaLaunchConfig_t{};
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)C);
+    // resident clusters per (cluster size, shared-memory size), cached
+    static int cache[kMaxClusterCTAs + 1][8] = {};
+    const int sidx = (int)((smem >> 15) & 7);
+    if (cache[C][sidx] == 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        cache[C][sidx] = n > 0 ? n : -1;
+    }
+    *smem_out = smem;
+    *stages_out = stages;
+    return cache[C][sidx] > 0 ? cache[C][sidx] : 0;
+}
+
+}  // namespace
+
+int cluster_capacity(int a_planes, int b_planes, const SiteLayout &L) {
+    int C = 0, T = 0;
+    if (!cluster_plan(L, &C, &T)) return 0;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    size_t smem = 0;
+    int stages = 0;
+    return cluster_config(a_planes, b_planes, L, C, cfg, attr, &smem, &stages);
+}
+
+cudaError_t launch_contract_tc_cluster(const TcArgs &a, const SiteLayout &L, int rows_valid, int *d_err,
+                                       cudaStream_t st, const MeasureArgs &m, int *clusters_out) {
+    int C = 0, T = 0;
+    if (a.fp8 || !cluster_plan(L, &C, &T)) return cudaErrorInvalidConfiguration;
+    if (a.nprod < 1 || a.nprod > kMaxProducts || a.a_planes < 1 || a.a_planes > 3 || a.b_planes < 1 ||
+        a.b_planes > 2 || m.nplanes != a.a_planes)
+        return cudaErrorInvalidValue;
+    TcParams p;
+    p.num_m_tiles = a.rows_pad / kBM;
+    p.num_n_tiles = L.ncols / L.bn;
+    p.num_k_blocks = L.K_pad / L.bk;
+    p.bn = L.bn;
+    p.a_planes = a.a_planes;
+    p.b_planes = a.b_planes;
+    p.nprod = a.nprod;
+    p.prod_code = 0;
+    for (int q = 0; q < a.nprod; ++q) {
+        if (a.prod_a[q] < 0 || a.prod_a[q] >= a.a_planes || a.prod_b[q] < 0 || a.prod_b[q] >= a.b_planes)
+            return cudaErrorInvalidValue;
+        p.prod_code |= ((uint32_t)a.prod_a[q] | ((uint32_t)a.prod_b[q] << 2)) << (4 * q);
+    }
+    p.b_plane_bytes = (uint32_t)L.bn * 128;
+    p.stage_bytes = (uint32_t)a.a_planes * kATileBytes + (uint32_t)a.b_planes * p.b_plane_bytes;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    size_t smem = 0;
+    const int max_clusters = cluster_config(a.a_planes, a.b_planes, L, C, cfg, attr, &smem, &p.stages);
+    if (max_clusters <= 0) return cudaErrorInvalidConfiguration;
+    p.tma_store = 0;
+    p.row0 = (int)a.row0;
+    p.idesc = idesc_bf16_f32(kBM, L.bn);
+    p.Y = nullptr;
+    p.ldY = 0;
+    p.P = nullptr;
+    p.ldP = 0;
+    p.rows_valid = rows_valid;
+    p.err = d_err;
+    p.cl_T = T;
+    p.m = m;
+    if (p.num_m_tiles <= 0) return cudaSuccess;
+    (void)smem;
+    // persistent: as many clusters as can be resident at once (at most one per m-tile)
+    const int ncl = p.num_m_tiles < max_clusters ? p.num_m_tiles : max_clusters;
+    if (clusters_out) *clusters_out = ncl;
+    cfg.gridDim = dim3((unsigned)(ncl * C));
+    cfg.stream = st;
+    auto kern = tc_contract_kernel<kClusterFused, false>;
+    cudaError_t e;
+    const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
+    const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
+    e = cudaLaunchKernelEx(&cfg, kern, a.tmA[0], a1, a2, a.tmB[0], b1, a.tmA[0], p);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

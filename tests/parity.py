@@ -20,11 +20,15 @@ import oracle
 
 
 def check(bonds, tensors, seed, rows, dev_samples, dev_logprob, tol, dev_trace=None, trace_rows=0,
-          site_index=None, job=0, nthreads=0, site_chunk=None, lams=None, mu=None):
+          site_index=None, job=0, nthreads=0, site_chunk=None, lams=None, mu=None, dev_trace_list=None):
     """rows: sample indices checked; dev_samples[i], dev_logprob[i] belong to rows[i].
 
     dev_trace: [M, trace_rows, d] device conditionals of rows 0..trace_rows-1
-    (rows[i] < trace_rows are compared).  lams: Vidal form (tensors are Gamma_k).
+    (rows[i] < trace_rows are compared), or, with dev_trace_list, of the rows
+    dev_trace_list[j] (every checked row in that list is compared).  The report
+    carries the per-site maximum conditional error ("prob_err_by_site") and the
+    oracle's conditionals of the checked rows ("oracle_probs", [R, M, d]).
+    lams: Vidal form (tensors are Gamma_k).
     mu: displacement amplitudes of the device call, shape (M, N) with column n
     for sample n (the call started at n0 = 0).  Returns a report dict; raises
     AssertionError when a rule is broken.
@@ -54,12 +58,20 @@ def check(bonds, tensors, seed, rows, dev_samples, dev_logprob, tol, dev_trace=N
     report["logprob_max_err"] = float(lp_err.max())
     report["logprob_max_err_over_bound"] = float((lp_err / bound).max())
     assert (lp_err <= bound).all(), f"log-probability outside its bound: {report}"
-    if dev_trace is not None and trace_rows > 0:
+    report["oracle_probs"] = r["probs"]
+    sel = np.zeros(0, np.int64)
+    if dev_trace is not None and dev_trace_list is not None:
+        pos = {int(x): j for j, x in enumerate(np.asarray(dev_trace_list, np.int64))}
+        sel = np.asarray([i for i, x in enumerate(rows) if int(x) in pos], np.int64)
+        cols = np.asarray([pos[int(rows[i])] for i in sel], np.int64)
+    elif dev_trace is not None and trace_rows > 0:
         sel = np.nonzero(rows < trace_rows)[0]
-        if sel.size:
-            dev = np.transpose(dev_trace[:, rows[sel], :], (1, 0, 2))  # [R, M, d]
-            err = np.abs(dev - r["probs"][sel])
-            report["prob_max_err"] = float(err.max())
-            report["prob_rows"] = int(sel.size)
-            assert err.max() <= tol, f"conditional probabilities differ by {err.max():.3e} > {tol}: {report}"
+        cols = rows[sel]
+    if sel.size:
+        dev = np.transpose(dev_trace[:, cols, :], (1, 0, 2))  # [R, M, d]
+        err = np.abs(dev - r["probs"][sel])
+        report["prob_max_err"] = float(err.max())
+        report["prob_rows"] = int(sel.size)
+        report["prob_err_by_site"] = err.max(axis=(0, 2))
+        assert err.max() <= tol, f"conditional probabilities differ by {err.max():.3e} > {tol}: {report}"
     return report

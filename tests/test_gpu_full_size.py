@@ -1,20 +1,52 @@
 """Full-size parity of the precision workload (M=1024, d=4, chi=1024) in the benchmark's launch
-configuration: one macro-batch of 2^18 rows per call, site tensors generated on the device.
+configuration: site tensors generated on the device, one call of 2^18 rows (BF16 modes: four
+micro-batches of 65536 rows) or 2^17 rows (FP32: two micro-batches).
 
-The oracle replays sampled rows (the first 48, traced at every site, and the last 16) along the
-device's outcomes, 32 sites at a time, on the tensors the BF16 store represents.
+1024 rows per mode are replayed by the oracle along the device's outcomes, the same number in every
+micro-batch (256 of each of four, or 512 of each of two): spread over the micro-batch, including its
+last 32 rows.  The device traces exactly those rows, so every
+conditional of every replayed row at every site is compared (BF16 modes on the tensors the BF16
+store represents, tolerance 1e-4; FP32 on the complex64 tensors, tolerance 1e-5).  The printed
+report gives the per-site error profile; for the BF16 modes the oracle also replays 128 of the rows
+on the original tensors, which gives the storage error (BF16 store vs original, oracle vs oracle)
+and the device's total error against the original tensors (reported, not gated).
 """
 import numpy as np
 import pytest
 
 import gen
+import oracle
 import parity
 from oracle import quant
 
 pytestmark = pytest.mark.gpu
 
-ROWS_PER_CALL = 1 << 18
-TRACE = 48
+MICRO = 1 << 16
+CALL_ROWS = {"bf16x2": 1 << 18, "bf16x3": 1 << 18, "fp32": 1 << 17}
+TOL = {"bf16x2": 1e-4, "bf16x3": 1e-4, "fp32": 1e-5}
+PLANES = {"bf16x2": 1, "bf16x3": 2}
+STORAGE_ROWS = 128
+
+
+def spread_rows(N, total=1024, tail=32):
+    """total rows, the same number in every micro-batch: evenly spread over it, plus its last `tail` rows."""
+    out = []
+    nb = (N + MICRO - 1) // MICRO
+    per_batch = total // nb
+    for j in range(nb):
+        lo, hi = j * MICRO, min(N, (j + 1) * MICRO)
+        spread = np.linspace(lo, hi - tail - 1, per_batch - tail).round().astype(np.int64)
+        out.append(np.unique(np.concatenate([spread, np.arange(hi - tail, hi)])))
+    rows = np.unique(np.concatenate(out))
+    assert rows.size == per_batch * len(out)
+    return rows
+
+
+def profile(err_by_site):
+    e = np.asarray(err_by_site)
+    return {"first_64": float(e[:64].max()), "sites_64_to_M-64": float(e[64:-64].max()),
+            "last_64": float(e[-64:].max()), "last_8": [float(f"{x:.2e}") for x in e[-8:]],
+            "worst_site": int(e.argmax())}
 
 
 @pytest.fixture(scope="module")
@@ -24,29 +56,55 @@ def precision_chain():
     return w, b, ts
 
 
-@pytest.mark.parametrize("precision,planes", [("bf16x2", 1)])
-def test_precision_workload_sampled_rows(precision_chain, precision, planes):
+@pytest.mark.parametrize("precision", ["bf16x2", "bf16x3", "fp32"])
+def test_precision_workload_1024_rows(precision_chain, precision):
     import torch
 
     import paper_2512_20064_gb300 as F
 
     w, b, ts = precision_chain
-    N = ROWS_PER_CALL
+    N = CALL_ROWS[precision]
+    rows = spread_rows(N)
+    assert rows.size == 1024
     out_s = torch.empty((N, w.M), dtype=torch.uint8, device="cuda")
     out_l = torch.empty(N, dtype=torch.float64, device="cuda")
     with F.Sampler(precision=precision) as s:
         for k in range(w.M):
             s.load_site(k, ts[k])
-        _, _, tr = s.sample(b, w.d, N, w.sampler_seed, out_samples=out_s, out_logprob=out_l, trace_rows=TRACE)
+        _, _, tr = s.sample(b, w.d, N, w.sampler_seed, out_samples=out_s, out_logprob=out_l, trace_list=rows)
         st = s.stats()
-    rows = np.concatenate([np.arange(TRACE), np.arange(N - 16, N)])
-    smp = out_s[torch.as_tensor(rows, device="cuda")].cpu().numpy()
-    lp = out_l[torch.as_tensor(rows, device="cuda")].cpu().numpy()
-
-    def tensor(k):
-        return quant.dequant_bf16(ts[k].cpu().numpy(), planes).astype(np.complex64)
-
-    rep = parity.check(b, tensor, w.sampler_seed, rows, smp, lp, 1e-4, dev_trace=tr, trace_rows=TRACE,
-                       site_chunk=32)
-    print(precision, rep, {k: st[k] for k in ("ms_contract", "ms_measure", "launches")})
+    idx = torch.as_tensor(rows, device="cuda")
+    smp = out_s[idx].cpu().numpy()
+    lp = out_l[idx].cpu().numpy()
     assert np.isfinite(out_l.cpu().numpy()).all()
+
+    if precision == "fp32":
+        def tensor(k):
+            return ts[k].cpu().numpy()
+    else:
+        def tensor(k):
+            # what the BF16 store holds; hi + lo of a float32 fits a float32 again, so the complex64 copy
+            # handed to the oracle is exact (checked)
+            A = quant.dequant_bf16(ts[k].cpu().numpy(), PLANES[precision])
+            A32 = A.astype(np.complex64)
+            return A32 if np.array_equal(A32.astype(np.complex128), A) else A
+
+    rep = parity.check(b, tensor, w.sampler_seed, rows, smp, lp, TOL[precision], dev_trace=tr,
+                       dev_trace_list=rows, site_chunk=32)
+    assert rep["prob_rows"] == rows.size == 1024
+    summary = {k: v for k, v in rep.items() if not isinstance(v, np.ndarray)}
+    summary["profile"] = profile(rep["prob_err_by_site"])
+    summary["rows_per_microbatch"] = int(np.bincount(rows // MICRO).min())
+    summary.update({k: st[k] for k in ("ms_contract", "ms_measure", "launches")})
+    if precision != "fp32":
+        # storage error: the oracle on the original tensors along the same outcomes, for a row subset
+        sub = np.linspace(0, rows.size - 1, STORAGE_ROWS).round().astype(np.int64)
+        r0 = oracle.replay(b, lambda k: ts[k].cpu().numpy(), w.sampler_seed, rows[sub],
+                           np.ascontiguousarray(smp[sub]), site_chunk=32)
+        storage = np.abs(r0["probs"] - rep["oracle_probs"][sub])
+        dev = np.transpose(tr[:, sub, :], (1, 0, 2))
+        total = np.abs(r0["probs"] - dev)
+        summary["storage_error_max"] = float(storage.max())
+        summary["storage_error_last_64"] = float(storage[:, -64:].max())
+        summary["device_vs_original_max"] = float(total.max())
+    print(f"\nPRECISION_PARITY {precision} N={N} rows={rows.size} {summary}")
