@@ -50,7 +50,11 @@ def parse():
     ap.add_argument("--workload", default="precision",
                     choices=["precision", "plain", "tiny", "batching", "streaming", "displacement", "knee",
                              "dynamic"])
-    ap.add_argument("--rows-cap", type=int, default=1024, help="batching: rows sampled per job")
+    ap.add_argument("--rows-cap", type=int, default=None, help="batching: cap on the rows sampled per job")
+    ap.add_argument("--rows-scale", type=float, default=1 / 16,
+                    help="batching: each job's N (log-uniform in [1e3, 1e6]) is multiplied by this factor")
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="batching: skip running every job separately on the FP32 path")
     ap.add_argument("--jobs", type=int, default=64, help="batching: number of MPS")
     ap.add_argument("--precision", default=None,
                     choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4", "fp8x1", "fp8x2"])
@@ -60,8 +64,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
-    ap.add_argument("--fused-measure", action="store_true",
-                    help="BF16 modes: measurement warps inside the contraction kernel")
+    ap.add_argument("--measurement", default=None, choices=["separate", "cta", "cluster"],
+                    help="BF16 modes: separate measurement kernel, measurement warps inside the contraction "
+                         "kernel, or the single-pass cluster kernel (no scratch); default per workload")
     ap.add_argument("--gbs", type=float, default=None, metavar="SIGMA",
                     help="GBS random displacement (Sec. 3.4.1): every sample and site gets its own complex "
                          "amplitude, E|mu|^2 = SIGMA^2 (drawn once per run, resident on the device)")
@@ -70,11 +75,11 @@ def parse():
     return ap.parse_args()
 
 
-DEFAULTS = {  # workload -> (precision, macro-batch rows)
-    "streaming": ("bf16x2", 1 << 16),
-    "precision": ("bf16x2", 1 << 18),
-    "plain": ("fp32", 1 << 17),
-    "tiny": ("fp32", 10_000),
+DEFAULTS = {  # workload -> (precision, macro-batch rows, measurement)
+    "streaming": ("bf16x2", 1 << 16, "separate"),
+    "precision": ("bf16x2", 1 << 18, "separate"),
+    "plain": ("fp32", 1 << 17, "separate"),
+    "tiny": ("fp32", 10_000, "separate"),
 }
 
 
@@ -165,8 +170,8 @@ class ClockSampler:
 # DRAM bytes (read + write) of one contraction launch at an interior site, from the committed ncu
 # captures (scaled by rows to the bench's launch size); None where no capture of the current kernel exists.
 CONTRACT_TRAFFIC = {
-    ("precision", "bf16x2"): (2.89e9, "profiles/tc_contract_precision_bf16x2.md"),
-    ("plain", "bf16x2"): (1.287e9, "profiles/tc_contract_plain_bf16x2.md"),
+    ("precision", "bf16x2", "separate"): (2.89e9, "profiles/tc_contract_precision_bf16x2.md"),
+    ("plain", "bf16x2", "separate"): (1.287e9, "profiles/tc_contract_plain_bf16x2.md"),
 }
 
 
@@ -270,7 +275,8 @@ def run_ours(args, rank, ws, local):
 
     stream = torch.cuda.Stream(device=local)
     residency = "host_stream" if args.workload == "streaming" else "hbm"
-    s = F.Sampler(device=local, precision=precision, stream=stream, fused_measure=args.fused_measure,
+    measurement = args.measurement or (DEFAULTS[args.workload][2] if precision != "fp32" else "separate")
+    s = F.Sampler(device=local, precision=precision, stream=stream, fused_measure=measurement,
                   residency=residency)
     t_load = time.perf_counter()
     if residency == "host_stream":
@@ -345,7 +351,7 @@ def run_ours(args, rank, ws, local):
             peak_note += " x 2 (nominal FP8/BF16 ratio)"
         achieved = flops_alg / (contract_ms / 1e3) / 1e12
         achieved_issued = flops_iss / (contract_ms / 1e3) / 1e12
-        tr = CONTRACT_TRAFFIC.get((args.workload, precision)) if not args.sites and not args.fused_measure else None
+        tr = CONTRACT_TRAFFIC.get((args.workload, precision, measurement)) if not args.sites else None
         nominal = NOMINAL_TFLOPS["fp8" if precision in ("fp8x1", "fp8x2") else "bf16"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None,
@@ -370,7 +376,8 @@ def run_ours(args, rank, ws, local):
         "data": "synthetic (seeded skewed Haar isometries, GBS-shaped)",
         "config": {"workload": w.note, "M": w.M, "d": w.d, "chi": w.chi, "N": w.N, "rows_per_step": macro,
                    "precision": precision, "parallelism": f"replicas{ws}" if ws > 1 else "single",
-                   "measurement": "fused" if args.fused_measure and precision != "fp32" else "separate kernel",
+                   "measurement": {"separate": "separate kernel", "cta": "measurement warps in the contraction",
+                                   "cluster": "single-pass cluster kernel (no scratch)"}[measurement],
                    "l2": "inputs larger than L2 (site tensors and left operand exceed 129 MB per step)"},
         "roofline": roof, "gpu_launches": launches, "clocks": clk,
         "setup_s": {"generate": t_gen, "load": t_load},
@@ -513,8 +520,9 @@ def run_reference(args, rank, ws):
 
 
 def run_batching(args, rank, ws, local):
-    """Many independent MPS of uneven shape in one batched engine call (grouped tcgen05 launches
-    captured in a CUDA graph) against the same jobs sampled one after another."""
+    """Many independent MPS of uneven shape in one batched engine call (one persistent tcgen05 launch,
+    captured in a CUDA graph) against the same jobs sampled one after another, on the BF16 path and on
+    the FP32 plain path."""
     import torch
 
     import paper_2512_20064_gb300 as F
@@ -522,15 +530,21 @@ def run_batching(args, rank, ws, local):
     torch.cuda.set_device(local)
     precision = args.precision or "bf16x2"
     specs = gen.batch_jobs(args.jobs, rows_cap=args.rows_cap)
+    for sp in specs:
+        sp["N"] = max(1, int(round(sp["N"] * args.rows_scale)))
     t_gen = time.perf_counter()
-    chains = []
+    chains, chains32 = [], []
     for j, sp in enumerate(specs):
         b, ts, idx = gen.mps_tensors(sp["M"], sp["d"], sp["chi"], base_seed=sp["base_seed"], skew=1.5, pool=4,
                                      device=f"cuda:{local}")
         s = F.Sampler(device=local, precision=precision)
         s.load_chain(ts, site_index=idx)
-        del ts
         chains.append((s, b))
+        if not args.no_fp32_compare:
+            s32 = F.Sampler(device=local, precision="fp32")
+            s32.load_chain(ts, site_index=idx)
+            chains32.append(s32)
+        del ts
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
     units = sum(sp["N"] * sp["M"] for sp in specs)
@@ -546,42 +560,69 @@ def run_batching(args, rank, ws, local):
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    t0 = time.perf_counter()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
+    ms_graph = 0.0
+    t0 = time.perf_counter()
+    ev0.record(stream)
     for _ in range(args.steps):
         F.fastmps_sample_batch(runner.h, jobs)
         launches += runner.stats()["launches"]
+        ms_graph += runner.stats()["ms_contract"]
+    ev1.record(stream)
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     clk = clocks.stop()
     st = runner.stats()
     batched = units * args.steps / dt
-    # the same jobs one after another (one engine call per job)
+    # the same jobs one after another (one engine call per job), BF16 and FP32
     t0 = time.perf_counter()
     for j, (s, b) in zip(jobs, chains):
         s.sample(b, j["d"], j["N"], j["seed"], job=j["job"], out_samples=j["out_samples"],
                  out_logprob=j["out_logprob"])
     torch.cuda.synchronize()
     separate = units / (time.perf_counter() - t0)
+    fp32 = None
+    if chains32:
+        j0 = jobs[0]  # warm the FP32 path once
+        chains32[0].sample(chains[0][1], j0["d"], min(j0["N"], 256), j0["seed"], job=0, out_samples=j0["out_samples"],
+                           out_logprob=j0["out_logprob"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j, s32, (_, b) in zip(jobs, chains32, chains):
+            s32.sample(b, j["d"], j["N"], j["seed"], job=j["job"], out_samples=j["out_samples"],
+                       out_logprob=j["out_logprob"])
+        torch.cuda.synchronize()
+        fp32 = units / (time.perf_counter() - t0)
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    ach = st["flops_algorithmic"] / (st["ms_contract"] / 1e3) / 1e12
+    ach = st["flops_algorithmic"] / (ms_graph / args.steps / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": batched, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16", "data": "synthetic (seeded skewed Haar isometries, GBS-shaped)",
-        "config": {"workload": f"batching: {len(specs)} MPS, M~U[64,2048], d in {{2,3,4,6}}, chi log-U[32,2048], "
-                               f"N log-U[1e3,1e6] capped at {args.rows_cap} rows per job, pool of 4 interior "
-                               "isometries per job", "precision": precision, "rows": int(sum(sp['N'] for sp in specs)),
-                   "sample_sites": int(units), "l2": "inputs larger than L2"},
-        "separate_calls": {"value": separate, "unit": UNIT, "speedup_batched": batched / separate},
+        "config": {"workload": f"batching: {len(specs)} MPS, M~U[64,2048], d in {{2,3,4,6}}, chi log-U[32,2048] "
+                               f"(end bonds capped), N log-U[1e3,1e6] x {args.rows_scale:g}"
+                               + (f" capped at {args.rows_cap}" if args.rows_cap else "")
+                               + ", pool of 4 interior isometries per job; one persistent launch per call",
+                   "precision": precision, "rows": int(sum(sp['N'] for sp in specs)),
+                   "sample_sites": int(units), "flops_algorithmic": st["flops_algorithmic"],
+                   "l2": "inputs larger than L2"},
+        "separate_calls_bf16": {"value": separate, "unit": UNIT, "speedup_batched": batched / separate},
+        "separate_calls_fp32": None if fp32 is None else {"value": fp32, "unit": UNIT,
+                                                          "speedup_batched": batched / fp32},
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "peak_nominal": NOMINAL_TFLOPS["bf16"], "frac_nominal": ach / NOMINAL_TFLOPS["bf16"],
                      "traffic": None, "peak_source": f"{peak_src} bf16_tflops_sustained",
-                     "kernel": "whole batched graph (grouped contraction + measurement)"},
-        "gpu_launches": launches, "clocks": clk, "setup_s": {"generate_and_load": t_gen},
+                     "kernel": "tc_batch_persistent_kernel (whole graph: contraction + measurement)"},
+        "gpu_launches": launches, "contract_launches_per_call": st["contract_launches"], "clocks": clk,
+        "setup_s": {"generate_and_load": t_gen},
     }
     runner.close()
     for s, _ in chains:
+        s.close()
+    for s in chains32:
         s.close()
     return line
 

@@ -45,7 +45,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
         return _SO
     tmp = _SO + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"]
+    cmd = ["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _SO)
     return _SO
@@ -57,7 +57,7 @@ def build_variant(src_text: str, out_path: str) -> str:
     c = out_path[:-3] + ".c"
     with open(c, "w") as f:
         f.write(src_text)
-    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", out_path, c, "-lm"],
+    subprocess.run(["gcc", "-O3", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", out_path, c, "-lm"],
                    check=True)
     return out_path
 
@@ -77,7 +77,7 @@ def _bind(lib):
         ctypes.c_int, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_void_p), ctypes.c_int, ctypes.c_uint64,
         ctypes.c_uint32, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
     lib.orc_sample_segment.restype = ctypes.c_int
     lib.orc_displacement.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_void_p]
     lib.orc_displacement.restype = None
@@ -222,7 +222,7 @@ def sample(bonds, tensors, seed: int, N: int, n0: int = 0, job: int = 0, site_in
     lp = np.zeros(N, np.float64)
     pr = np.zeros((N, M, d), np.float64) if want_probs else None
     rc = lib.orc_sample_segment(M, d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, job, n0, N, 0, M, None, 0,
-                                _vp(smp), _vp(lp), _vp(pr), None, None, None, nthreads, ex.lam_ptrs, mp, ld)
+                                _vp(smp), _vp(lp), _vp(pr), None, None, None, nthreads, ex.lam_ptrs, mp, ld, None)
     if rc != 0:
         raise RuntimeError(f"orc_sample_segment failed ({rc})")
     return (smp, lp, pr) if want_probs else (smp, lp)
@@ -239,7 +239,7 @@ def sample_prefix(bonds, tensors, seed: int, N: int, K: int, n0: int = 0, nthrea
     smp = np.zeros((N, M), np.uint8)
     lp = np.zeros(N, np.float64)
     rc = lib.orc_sample_segment(M, ch.d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, 0, n0, N, 0, K, _vp(vstate),
-                                ldv, _vp(smp), _vp(lp), None, None, None, None, nthreads, None, None, 0)
+                                ldv, _vp(smp), _vp(lp), None, None, None, None, nthreads, None, None, 0, None)
     if rc != 0:
         raise RuntimeError(f"orc_sample_segment failed ({rc})")
     return smp[:, :K], lp
@@ -264,7 +264,7 @@ def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=Non
     lib = _load(lib)
     M = len(bonds) - 1
     ex = _Extras(M, bonds, lams, mu)
-    rows = np.asarray(rows, dtype=np.int64)
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
     forced = np.ascontiguousarray(np.asarray(forced, dtype=np.uint8))
     R = rows.shape[0]
     assert forced.shape == (R, M)
@@ -288,20 +288,14 @@ def replay(bonds, tensors, seed: int, rows, forced, job: int = 0, site_index=Non
             ch = _Chain(bonds, tensors, site_index, sites=range(k0, k1))
         if probs is None:
             probs = np.zeros((R, M, ch.d), np.float64)
-        # rows are arbitrary indices: run each contiguous run of indices as one call
-        i = 0
-        while i < R:
-            j = i + 1
-            while j < R and rows[j] == rows[j - 1] + 1:
-                j += 1
-            mp, ld = ex.mu_rows(i, j)
-            rc = lib.orc_sample_segment(M, ch.d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, job, int(rows[i]), j - i,
-                                        k0, k1, _vp(vstate[i:j]), ldv, None, _vp(lp[i:j]), _vp(probs[i:j]),
-                                        _vp(forced[i:j]), _vp(own[i:j]), _vp(margin[i:j]), nthreads, ex.lam_ptrs,
-                                        mp, ld)
-            if rc != 0:
-                raise RuntimeError(f"orc_sample_segment (replay) failed ({rc})")
-            i = j
+        # rows are arbitrary sample indices: one call over all of them, each row keyed by its own index
+        mp, ld = ex.mu_rows(0, R)
+        rc = lib.orc_sample_segment(M, ch.d, ch.bond_ptr(), ch.ptrs, int(ch.f32), seed, job, 0, R,
+                                    k0, k1, _vp(vstate), ldv, None, _vp(lp), _vp(probs),
+                                    _vp(forced), _vp(own), _vp(margin), nthreads, ex.lam_ptrs,
+                                    mp, ld, _vp(rows))
+        if rc != 0:
+            raise RuntimeError(f"orc_sample_segment (replay) failed ({rc})")
         del ch
     return {"probs": probs, "own": own, "margin": margin, "logprob": lp}
 

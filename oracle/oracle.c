@@ -95,31 +95,45 @@ double orc_uniform(uint64_t seed, uint64_t n, uint32_t k, uint32_t job)
 }
 
 /* ------------------------------------------------------------------------ */
-/* One site of one sample, complex double.                                   */
+/* One site of a batch of samples, complex double.                           */
 /* ------------------------------------------------------------------------ */
 
-/* y[s*chi_r + b] (interleaved re, im) = sum_a v[a] A[a, s, b].  Plain loops.
- * A holds interleaved complex doubles (a_is_f32 = 0) or floats (a_is_f32 = 1);
- * float entries are widened exactly to double. */
+/* For every sample r of a batch (Algorithm 2 contracts the left environments
+ * of a whole batch of samples with the site tensor at once):
+ * y_r[s*chi_r + b] (interleaved re, im) = sum_a v_r[a] A[a, s, b], the sum
+ * taken over a in increasing order.  Plain loops; the sample loop sits inside
+ * the loop over a only so that a row of A is read once per batch -- each
+ * sample's sums are the same operations in the same order as for a batch of
+ * one.  A holds interleaved complex doubles (a_is_f32 = 0) or floats
+ * (a_is_f32 = 1); float entries are widened exactly to double. */
+#define ORC_BATCH 8 /* samples contracted together per site (Algorithm 2's batch) */
+
 static inline double orc_elem(const void *A, int a_is_f32, size_t i)
 {
     return a_is_f32 ? (double)((const float *)A)[i] : ((const double *)A)[i];
 }
 
-static void orc_contract(const double *v, int chi_l, int d, int chi_r, const void *A, int a_is_f32, double *y)
+static void orc_contract(int nrows, double *const *vs, int chi_l, int d, int chi_r, const void *A, int a_is_f32,
+                         double *const *ys, double *arow)
 {
     const int cols = d * chi_r;
-    for (int c = 0; c < cols; ++c) {
-        y[2 * c] = 0.0;
-        y[2 * c + 1] = 0.0;
-    }
-    for (int a = 0; a < chi_l; ++a) {
-        const double vr = v[2 * a], vi = v[2 * a + 1];
-        const size_t row = (size_t)2 * a * cols;
+    for (int r = 0; r < nrows; ++r)
         for (int c = 0; c < cols; ++c) {
-            const double ar = orc_elem(A, a_is_f32, row + 2 * c), ai = orc_elem(A, a_is_f32, row + 2 * c + 1);
-            y[2 * c] += vr * ar - vi * ai;
-            y[2 * c + 1] += vr * ai + vi * ar;
+            ys[r][2 * c] = 0.0;
+            ys[r][2 * c + 1] = 0.0;
+        }
+    for (int a = 0; a < chi_l; ++a) {
+        const size_t row = (size_t)2 * a * cols;
+        /* row a of A as doubles (float entries widened exactly), read once for the batch */
+        for (int c = 0; c < 2 * cols; ++c) arow[c] = orc_elem(A, a_is_f32, row + c);
+        for (int r = 0; r < nrows; ++r) {
+            const double vr = vs[r][2 * a], vi = vs[r][2 * a + 1];
+            double *y = ys[r];
+            for (int c = 0; c < cols; ++c) {
+                const double ar = arow[2 * c], ai = arow[2 * c + 1];
+                y[2 * c] += vr * ar - vi * ai;
+                y[2 * c + 1] += vr * ai + vi * ar;
+            }
         }
     }
 }
@@ -291,14 +305,15 @@ static int max_bond(int M, const int *bond)
  * a_is_f32, complex floats.  lam (nullable): Vidal form, lam[k] = Lambda_k
  * (bond[k+1] doubles) and A[k] = Gamma_k.  mu (nullable): GBS displacement,
  * interleaved complex doubles, amplitude of row i at site k at
- * mu[2*(k*ldmu + i)] (re) and +1 (im).  Returns 0, -1 on bad arguments, -2
- * on allocation failure.
+ * mu[2*(k*ldmu + i)] (re) and +1 (im).  nlist (nullable): row i is sample
+ * nlist[i] (its uniform is keyed by that index) instead of n0+i.  Returns 0,
+ * -1 on bad arguments, -2 on allocation failure.
  */
 int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int a_is_f32, uint64_t seed,
                        uint32_t job, int64_t n0, int64_t N, int k0, int k1, double *vstate, int ldv,
                        uint8_t *samples, double *logprob, double *probs, const uint8_t *forced,
                        uint8_t *own_draw, double *margin, int nthreads, const double *const *lam,
-                       const double *mu, int64_t ldmu)
+                       const double *mu, int64_t ldmu, const int64_t *nlist)
 {
     if (M < 1 || d < 2 || d > 255 || N < 0 || !bond || !A) return -1;
     if (mu && ldmu < N) return -1;
@@ -308,84 +323,112 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
     const int chi = max_bond(M, bond);
     if (vstate && ldv < chi) return -1;
     int bad = 0;
+    enum { B = ORC_BATCH };
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel reduction(| : bad)
 #endif
     {
-        double *v = (double *)malloc(sizeof(double) * 2 * (size_t)chi);
-        double *y = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi);
+        double *vbuf = (double *)malloc(sizeof(double) * 2 * (size_t)chi * B);
+        double *ybuf = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi * B);
         double *w = (double *)malloc(sizeof(double) * (size_t)d);
         double *Dm = (double *)malloc(sizeof(double) * 2 * (size_t)d * d);
         double *ytmp = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi);
-        if (!v || !y || !w || !Dm || !ytmp) bad = 1;
+        double *arow = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi);
+        if (!vbuf || !ybuf || !w || !Dm || !ytmp || !arow) bad = 1;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
-        for (int64_t i = 0; i < N; ++i) {
+        for (int64_t i0 = 0; i0 < N; i0 += B) {
             if (bad) continue;
-            const uint64_t n = (uint64_t)(n0 + i);
-            if (vstate) {
-                for (int b = 0; b < 2 * bond[k0]; ++b) v[b] = vstate[(size_t)i * 2 * ldv + b];
-            } else {
-                v[0] = 1.0;
-                v[1] = 0.0;
+            const int nb = (int)(N - i0 < B ? N - i0 : B);
+            double lps[B];
+            int deads[B];
+            double *vr_[B], *yr_[B];
+            for (int j = 0; j < nb; ++j) {
+                const int64_t i = i0 + j;
+                double *v = vbuf + (size_t)j * 2 * chi;
+                if (vstate) {
+                    for (int b = 0; b < 2 * bond[k0]; ++b) v[b] = vstate[(size_t)i * 2 * ldv + b];
+                } else {
+                    v[0] = 1.0;
+                    v[1] = 0.0;
+                }
+                lps[j] = 0.0;
+                deads[j] = 0;
             }
-            double lp = 0.0;
-            int dead = 0;
             for (int k = k0; k < k1; ++k) {
                 const int cl = bond[k], cr = bond[k + 1];
-                if (dead) {
-                    if (samples) samples[i * M + k] = 0;
-                    if (own_draw) own_draw[i * M + k] = 0;
-                    if (margin) margin[i * M + k] = INFINITY;
-                    if (probs)
-                        for (int t = 0; t < d; ++t) probs[((size_t)i * M + k) * d + t] = NAN;
-                    continue;
-                }
-                orc_contract(v, cl, d, cr, A[k], a_is_f32, y);
-                if (mu) {
-                    const double *m = mu + 2 * ((size_t)k * ldmu + (size_t)i);
-                    orc_displacement(m[0], m[1], d, Dm);
-                    orc_displace(y, d, cr, Dm, ytmp);
-                }
-                if (lam)
-                    orc_block_norms_lambda(y, d, cr, lam[k], w);
-                else
-                    orc_block_norms(y, d, cr, w);
-                const double u = orc_uniform(seed, n, (uint32_t)k, job);
-                double Z, mg;
-                const int mine = orc_draw(w, d, u, &Z, &mg);
-                const int s = forced ? (int)forced[i * M + k] : mine;
-                if (own_draw) own_draw[i * M + k] = (uint8_t)mine;
-                if (margin) margin[i * M + k] = mg;
-                if (probs)
-                    for (int t = 0; t < d; ++t) probs[((size_t)i * M + k) * d + t] = w[t] / Z;
-                if (samples) samples[i * M + k] = (uint8_t)s;
-                if (s < 0 || s >= d || !(w[s] > 0.0)) {
-                    /* a forced outcome of zero probability: the replay of this row stops */
-                    lp = -INFINITY;
-                    dead = 1;
-                    continue;
-                }
-                lp += log(w[s]) - log(Z);
-                const double inv = 1.0 / sqrt(w[s]);
-                for (int b = 0; b < cr; ++b) {
-                    v[2 * b] = y[2 * (s * cr + b)] * inv;
-                    v[2 * b + 1] = y[2 * (s * cr + b) + 1] * inv;
-                }
-                if (lam)
-                    for (int b = 0; b < cr; ++b) {
-                        v[2 * b] *= lam[k][b];
-                        v[2 * b + 1] *= lam[k][b];
+                /* the contraction of every live sample of the batch at site k */
+                int nl = 0;
+                for (int j = 0; j < nb; ++j)
+                    if (!deads[j]) {
+                        vr_[nl] = vbuf + (size_t)j * 2 * chi;
+                        yr_[nl] = ybuf + (size_t)j * 2 * d * chi;
+                        ++nl;
                     }
+                orc_contract(nl, vr_, cl, d, cr, A[k], a_is_f32, yr_, arow);
+                for (int j = 0; j < nb; ++j) {
+                    const int64_t i = i0 + j;
+                    const uint64_t n = nlist ? (uint64_t)nlist[i] : (uint64_t)(n0 + i);
+                    double *v = vbuf + (size_t)j * 2 * chi;
+                    double *y = ybuf + (size_t)j * 2 * d * chi;
+                    if (deads[j]) {
+                        if (samples) samples[i * M + k] = 0;
+                        if (own_draw) own_draw[i * M + k] = 0;
+                        if (margin) margin[i * M + k] = INFINITY;
+                        if (probs)
+                            for (int t = 0; t < d; ++t) probs[((size_t)i * M + k) * d + t] = NAN;
+                        continue;
+                    }
+                    if (mu) {
+                        const double *m = mu + 2 * ((size_t)k * ldmu + (size_t)i);
+                        orc_displacement(m[0], m[1], d, Dm);
+                        orc_displace(y, d, cr, Dm, ytmp);
+                    }
+                    if (lam)
+                        orc_block_norms_lambda(y, d, cr, lam[k], w);
+                    else
+                        orc_block_norms(y, d, cr, w);
+                    const double u = orc_uniform(seed, n, (uint32_t)k, job);
+                    double Z, mg;
+                    const int mine = orc_draw(w, d, u, &Z, &mg);
+                    const int s = forced ? (int)forced[i * M + k] : mine;
+                    if (own_draw) own_draw[i * M + k] = (uint8_t)mine;
+                    if (margin) margin[i * M + k] = mg;
+                    if (probs)
+                        for (int t = 0; t < d; ++t) probs[((size_t)i * M + k) * d + t] = w[t] / Z;
+                    if (samples) samples[i * M + k] = (uint8_t)s;
+                    if (s < 0 || s >= d || !(w[s] > 0.0)) {
+                        /* a forced outcome of zero probability: the replay of this row stops */
+                        lps[j] = -INFINITY;
+                        deads[j] = 1;
+                        continue;
+                    }
+                    lps[j] += log(w[s]) - log(Z);
+                    const double inv = 1.0 / sqrt(w[s]);
+                    for (int b = 0; b < cr; ++b) {
+                        v[2 * b] = y[2 * (s * cr + b)] * inv;
+                        v[2 * b + 1] = y[2 * (s * cr + b) + 1] * inv;
+                    }
+                    if (lam)
+                        for (int b = 0; b < cr; ++b) {
+                            v[2 * b] *= lam[k][b];
+                            v[2 * b + 1] *= lam[k][b];
+                        }
+                }
             }
-            if (logprob) logprob[i] += lp;
-            if (vstate)
-                for (int b = 0; b < 2 * bond[k1]; ++b) vstate[(size_t)i * 2 * ldv + b] = dead ? NAN : v[b];
+            for (int j = 0; j < nb; ++j) {
+                const int64_t i = i0 + j;
+                const double *v = vbuf + (size_t)j * 2 * chi;
+                if (logprob) logprob[i] += lps[j];
+                if (vstate)
+                    for (int b = 0; b < 2 * bond[k1]; ++b) vstate[(size_t)i * 2 * ldv + b] = deads[j] ? NAN : v[b];
+            }
         }
-        free(v);
-        free(y);
+        free(vbuf);
+        free(ybuf);
+        free(arow);
         free(w);
         free(Dm);
         free(ytmp);
@@ -401,7 +444,7 @@ int orc_sample(int M, int d, const int *bond, const double *const *A, uint64_t s
     if (logprob)
         for (int64_t i = 0; i < N; ++i) logprob[i] = 0.0;
     return orc_sample_segment(M, d, bond, (const void *const *)A, 0, seed, job, n0, N, 0, M, NULL, 0, samples,
-                              logprob, probs, forced, own_draw, margin, nthreads, NULL, NULL, 0);
+                              logprob, probs, forced, own_draw, margin, nthreads, NULL, NULL, 0, NULL);
 }
 
 /* ------------------------------------------------------------------------ */

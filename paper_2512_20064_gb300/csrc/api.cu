@@ -1311,6 +1311,7 @@ int handle_view(fastmps_handle h, HandleView *out) {
     out->residency = h->opt.residency;
     out->stream = h->stream;
     out->num_sms = h->num_sms;
+    out->max_microbatch = h->opt.max_microbatch;
     return FASTMPS_OK;
 }
 

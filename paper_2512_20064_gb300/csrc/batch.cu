@@ -3,17 +3,21 @@
 // Schedule.  Job j has M_j sites and N_j rows, processed in C_j chunks of at
 // most N2_j rows (N2_j bounded by a shared FP32-scratch budget).  Round r
 // advances every job with r < C_j * M_j by one step: chunk c = r / M_j at
-// site k = r % M_j.  The steps of one round are independent (different
-// jobs), so one grouped contraction launch and one grouped measurement
-// launch serve the whole round; consecutive rounds of a job are ordered by
-// the stream.  Segment tables for every round are built on the host, copied
-// to device memory once, and the launch sequence of all rounds is captured
-// into a CUDA graph that later calls with the same job table replay.
+// site k = r % M_j.  One persistent kernel runs every round of every job:
+// its task list is the tiles of all segments (job, chunk, site) in round
+// order, taken from a device counter, and a task waits (bounded) only for the
+// measurement of its own job's rows at the previous step -- not for a whole
+// round -- so rounds of different jobs overlap freely.  The segment table is
+// built on the host and copied to device memory once; the call's launches
+// (counter resets, left-boundary initialisation, the persistent kernel, the
+// output transposes) are captured into a CUDA graph that later calls with the
+// same job table replay.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -69,8 +73,9 @@ struct JobBufs {
 
 struct BatchState {
     std::vector<std::unique_ptr<JobBufs>> jobs;
-    Buf segs_dev, meas_dev, segs_host, meas_host, err;
+    Buf segs_dev, meas_dev, segs_host, meas_host, err, counters;
     std::vector<uint64_t> signature;
+    int64_t launches = 0;  // kernels of one replay of the graph
     cudaGraphExec_t graph = nullptr;
     ~BatchState() {
         if (graph) cudaGraphExecDestroy(graph);
@@ -100,6 +105,13 @@ struct JobPlan {
     int M, d, ldV, ncols_max, ldP_max;
     int64_t N, N_pad, N2, chunks, rounds;
 };
+
+// Test hook: FASTMPS_TEST_STALL_DEPENDENCY=1 makes every task wait for one measurement more than ever
+// happens, with a 100 ms wait limit, so the persistent kernel's bounded waits run out.
+bool stall_test_requested() {
+    const char *v = getenv("FASTMPS_TEST_STALL_DEPENDENCY");
+    return v && v[0] == '1';
+}
 
 }  // namespace
 
@@ -175,6 +187,8 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
         const int64_t share = std::max<int64_t>((int64_t)256 << 20,
                                                 total_rows > 0 ? budget * std::max<int64_t>(J.N, 1) / total_rows : 0);
         P.N2 = std::min(P.N_pad, std::max<int64_t>(128, share / ((int64_t)P.ncols_max * 4) / 128 * 128));
+        if (rv.max_microbatch > 0)  // the runner's option caps the rows of a chunk
+            P.N2 = std::min(P.N2, std::max<int64_t>(128, rv.max_microbatch / 128 * 128));
         P.chunks = J.N > 0 ? (J.N + P.N2 - 1) / P.N2 : 0;
         P.rounds = P.chunks * J.M;
         R = std::max(R, P.rounds);
@@ -204,8 +218,10 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
     int *d_err = bs->err.as<int>();
 
     // ---- signature: reuse the captured graph when nothing changed -----------------
+    const bool stall = stall_test_requested();
     std::vector<uint64_t> sig;
     sig.push_back((uint64_t)count);
+    sig.push_back((uint64_t)stall);
     for (int j = 0; j < count; ++j) {
         const fastmps_job &J = jobs[j];
         const uint64_t f[] = {(uint64_t)(uintptr_t)J.chain, (uint64_t)J.M, (uint64_t)J.d, (uint64_t)J.n0,
@@ -227,27 +243,25 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
             cudaGraphExecDestroy(bs->graph);
             bs->graph = nullptr;
         }
-        // ---- segment tables of every round ---------------------------------------
-        std::vector<int> nseg(R), seg_off(R + 1, 0);
-        for (int64_t r = 0; r < R; ++r) {
-            int n = 0;
-            for (int j = 0; j < count; ++j) n += r < plan[j].rounds ? 1 : 0;
-            nseg[r] = n;
-            seg_off[r + 1] = seg_off[r] + n;
-        }
-        const size_t total_segs = (size_t)seg_off[R];
+        // ---- segment table of every round, in task order ----------------------------
+        size_t total_segs = 0;
+        for (int64_t r = 0; r < R; ++r)
+            for (int j = 0; j < count; ++j) total_segs += r < plan[j].rounds ? 1 : 0;
+        // m-tile slots of each job (counters of completed measurements)
+        std::vector<int64_t> slot_base(count + 1, 0);
+        for (int j = 0; j < count; ++j) slot_base[j + 1] = slot_base[j] + plan[j].N2 / 128;
         if (!bs->segs_host.host) bs->segs_host.host = true;
         if (!bs->meas_host.host) bs->meas_host.host = true;
-        if (!bs->segs_host.ensure(total_segs * sizeof(TcSegment)) ||
+        if (!bs->segs_host.ensure(total_segs * sizeof(PSegment)) ||
             !bs->meas_host.ensure(total_segs * sizeof(MeasureArgs)) ||
-            !bs->segs_dev.ensure(total_segs * sizeof(TcSegment)) ||
+            !bs->segs_dev.ensure(total_segs * sizeof(PSegment)) ||
             !bs->meas_dev.ensure(total_segs * sizeof(MeasureArgs)))
             return set_error(runner, FASTMPS_ERR_OOM, "segment-table allocation failed");
-        TcSegment *hs = bs->segs_host.as<TcSegment>();
+        PSegment *hs = bs->segs_host.as<PSegment>();
         MeasureArgs *hm = bs->meas_host.as<MeasureArgs>();
-        std::vector<int> tiles(R), row_blocks(R);
+        int64_t task = 0, done = 0;
+        size_t si = 0;
         for (int64_t r = 0; r < R; ++r) {
-            int si = seg_off[r], tile = 0, rb = 0;
             for (int j = 0; j < count; ++j) {
                 const JobPlan &P = plan[j];
                 if (r >= P.rounds) continue;
@@ -267,14 +281,14 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
                 }
                 const int64_t row0 = c * P.N2;
                 const int64_t rows = std::min<int64_t>(P.N2, P.N - row0);
-                TcSegment &S = hs[si];
+                PSegment &S = hs[si];
                 memset(&S, 0, sizeof S);
                 for (int p = 0; p < 3; ++p)
                     if (!encode_bf16_map(&S.tmA[p], B.V[cur][p < a_planes ? p : 0].p, L.K_pad, P.N_pad, P.ldV, 128))
                         return set_error(runner, FASTMPS_ERR_CUDA, "tensor map encoding failed");
                 S.tmB[0] = sv.tmB[0];
                 S.tmB[1] = sv.tmB[1];
-                S.tile_begin = tile;
+                S.task_begin = task;
                 S.num_m_tiles = (int)(roundup(rows, 128) / 128);
                 S.num_n_tiles = L.ncols / L.bn;
                 S.num_k_blocks = L.K_pad / 64;
@@ -282,12 +296,16 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
                 S.idesc = idesc_bf16_f32(128, L.bn);
                 S.tx_bytes = (uint32_t)a_planes * 16384u + (uint32_t)b_planes * (uint32_t)L.bn * 128u;
                 S.row0 = (int)row0;
+                S.step = (int)r;  // chunk c at site k is the job's step c * M + k = r
+                S.slot_base = slot_base[j];
+                S.done_base = done;
+                // fixed row strides (the job's widest site): m-tiles of consecutive steps run
+                // concurrently, so a row's scratch must not move when the site's width changes
                 S.Y = B.Y.as<float>();
-                S.ldY = L.ncols;
+                S.ldY = P.ncols_max;
                 S.P = B.P.as<float>();
-                S.ldP = L.ncols / L.bn;
+                S.ldP = P.ldP_max;
                 S.rows_valid = (int)rows;
-                S.row_block_begin = rb;
                 MeasureArgs &m = hm[si];
                 m = MeasureArgs{};
                 m.Y = S.Y;
@@ -314,26 +332,28 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
                 m.trace = nullptr;
                 m.trace_rows = 0;
                 m.err = d_err;
-                tile += S.num_m_tiles * S.num_n_tiles;
-                rb += (int)((rows + 31) / 32);
+                task += (int64_t)S.num_m_tiles * S.num_n_tiles;
+                done += S.num_m_tiles;
                 ++si;
             }
-            tiles[r] = tile;
-            row_blocks[r] = rb;
         }
-        e = cudaMemcpyAsync(bs->segs_dev.p, hs, total_segs * sizeof(TcSegment), cudaMemcpyHostToDevice, st);
+        // counters: [0, 2) task queue (64-bit), then measured[slot], then tiles_done[segment m-tile]
+        const size_t counter_ints = 4 + (size_t)slot_base[count] + (size_t)done;
+        if (!bs->counters.ensure(counter_ints * sizeof(int)))
+            return set_error(runner, FASTMPS_ERR_OOM, "counter allocation failed");
+        e = cudaMemcpyAsync(bs->segs_dev.p, hs, total_segs * sizeof(PSegment), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(bs->meas_dev.p, hm, total_segs * sizeof(MeasureArgs), cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return set_error(runner, FASTMPS_ERR_CUDA, "segment-table upload failed");
 
-        // ---- capture the launch sequence of all rounds ------------------------------
+        // ---- capture the call: resets, initialisation, one persistent launch, transposes ------
         std::vector<uint8_t *> out_dst(count, nullptr);
         for (int j = 0; j < count; ++j)
             if (jobs[j].out_samples)
                 out_dst[j] = device_pointer(jobs[j].out_samples) ? jobs[j].out_samples
                                                                  : bs->jobs[j]->stage_out.as<uint8_t>();
-        e = prepare_contract_grouped();
+        e = prepare_batch_persistent();
         if (e != cudaSuccess) return set_error(runner, FASTMPS_ERR_CUDA, "kernel attribute setup failed");
         cudaStream_t cap;
         if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess)
@@ -343,8 +363,9 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
             cudaStreamDestroy(cap);
             return set_error(runner, FASTMPS_ERR_CUDA, "stream capture failed to start");
         }
-        int64_t launches = 0, contract_launches = 0;
+        int64_t launches = 0;
         cudaMemsetAsync(d_err, 0, sizeof(int), cap);
+        cudaMemsetAsync(bs->counters.p, 0, counter_ints * sizeof(int), cap);
         for (int j = 0; j < count; ++j) {
             const JobPlan &P = plan[j];
             if (P.rounds == 0) continue;
@@ -355,26 +376,26 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
             launch_init_left_bf16(V0, a_planes, P.N_pad, P.ldV, cap);
             ++launches;
         }
-        cudaError_t le = cudaSuccess;
-        for (int64_t r = 0; r < R && le == cudaSuccess; ++r) {
-            GroupedArgs g;
-            g.segs = bs->segs_dev.as<TcSegment>() + seg_off[r];
-            g.meas = bs->meas_dev.as<MeasureArgs>() + seg_off[r];
-            g.nseg = nseg[r];
-            g.total_tiles = tiles[r];
-            g.total_row_blocks = row_blocks[r];
-            g.a_planes = a_planes;
-            g.b_planes = b_planes;
-            g.nprod = nprod;
-            for (int q = 0; q < kMaxProducts; ++q) {
-                g.prod_a[q] = pa[q];
-                g.prod_b[q] = pb[q];
-            }
-            le = launch_contract_grouped(g, rv.num_sms, d_err, cap);
-            launch_measure_grouped(g, cap);
-            launches += 2;
-            ++contract_launches;
+        PersistentArgs g;
+        g.segs = bs->segs_dev.as<PSegment>();
+        g.meas = bs->meas_dev.as<MeasureArgs>();
+        g.nseg = (int)total_segs;
+        g.total_tasks = task;
+        int *ctr = bs->counters.as<int>();
+        g.queue = ctr;
+        g.measured = ctr + 4;
+        g.tiles_done = ctr + 4 + slot_base[count];
+        g.a_planes = a_planes;
+        g.b_planes = b_planes;
+        g.nprod = nprod;
+        for (int q = 0; q < kMaxProducts; ++q) {
+            g.prod_a[q] = pa[q];
+            g.prod_b[q] = pb[q];
         }
+        g.wait_limit_ns = stall ? 100000000ull : kWaitLimitNs;
+        g.stall_test = stall ? 1 : 0;
+        const cudaError_t le = launch_batch_persistent(g, rv.num_sms, d_err, cap);
+        ++launches;
         for (int j = 0; j < count; ++j) {
             const JobPlan &P = plan[j];
             if (P.rounds == 0 || !jobs[j].out_samples) continue;
@@ -397,19 +418,10 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
             return set_error(runner, FASTMPS_ERR_CUDA, "graph instantiation failed");
         }
         bs->signature = sig;
-        stats->launches = launches;
-        stats->contract_launches = contract_launches;
-    } else {
-        stats->launches = 0;  // filled below from the cached plan
+        bs->launches = launches;
     }
-    // launches of a replay equal those of the capture
-    if (stats->launches == 0) {
-        int64_t l = 2 * R;
-        for (int j = 0; j < count; ++j)
-            if (plan[j].rounds) l += 1 + (jobs[j].out_samples ? 1 : 0);
-        stats->launches = l;
-        stats->contract_launches = R;
-    }
+    stats->launches = bs->launches;
+    stats->contract_launches = 1;  // one persistent launch runs every round of every job
 
     // ---- run ----------------------------------------------------------------------
     cudaEvent_t e0, e1;

@@ -18,6 +18,7 @@ enum DeviceError : int {
     kDevTimeoutMma = 2,
     kDevTimeoutEpilogue = 3,
     kDevTimeoutMeasure = 4,
+    kDevTimeoutDependency = 5,  // a task's left rows were not measured within the wait limit
     kDevNumeric = 16,
 };
 
@@ -213,6 +214,43 @@ __device__ __forceinline__ float ld_shared_cluster_f32(uint32_t cluster_addr) {
 // Full barrier over every thread of every CTA of the cluster (all threads of each warp take part).
 __device__ __forceinline__ void cluster_sync_all() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Named barriers among a subset of warps.  The non-.aligned forms are used
+// because lanes of one warp may reach them at different times.
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Named barrier that also ORs a predicate over the participating threads: a
+// group decides together whether to leave a loop, so no thread is left
+// waiting at a later barrier for a thread that already left.
+__device__ __forceinline__ bool named_bar_any(int id, int nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+// Acquire load / release add at GPU scope (progress counters shared by thread blocks).
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_gpu(int *p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Orders this thread's generic-proxy global accesses with its later (or others' earlier, through
+// synchronisation) async-proxy (TMA) accesses.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map) {

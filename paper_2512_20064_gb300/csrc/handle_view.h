@@ -16,6 +16,7 @@ struct HandleView {
     int residency;
     cudaStream_t stream;
     int num_sms;
+    int64_t max_microbatch;  // rows per contraction launch requested in the options (0: automatic)
 };
 
 struct SiteView {

@@ -150,38 +150,42 @@ void launch_transpose_outcomes(const uint8_t *O, int64_t ldO, int64_t N, int M, 
 
 namespace fastmps {
 
-// ---- grouped (batched) contraction + measurement ---------------------------
-// One segment = one job's chunk of rows at one site.  The grouped kernels run
-// the tiles (and rows) of all segments of a round in one launch; segment
-// tables live in device memory (64-byte aligned for the tensor maps).
-struct TcSegment {  // 64-byte aligned through its CUtensorMap members
+// ---- persistent batched kernel: every round of every job in one launch --------------------------
+// Tasks are the tiles of all segments of all rounds, in round order (segments of round r, each
+// m-tile-major); a segment's tasks occupy [task_begin, task_begin + num_m_tiles * num_n_tiles).
+struct PSegment {  // 64-byte aligned through its CUtensorMap members
     CUtensorMap tmA[3];
     CUtensorMap tmB[2];
-    int tile_begin;      // first global tile index of the segment
+    int64_t task_begin;
     int num_m_tiles, num_n_tiles, num_k_blocks, bn;
     uint32_t idesc, tx_bytes;
-    int row0;            // first row of the chunk in the job's left-operand buffers (TMA y coordinate)
+    int row0;            // TMA y coordinate of the chunk's first row in the job's left-operand buffers
+    int step;            // c * M + k: measurements every m-tile of this chunk has had before this segment
+    int64_t slot_base;   // measured[slot_base + mt]: measurements completed by m-tile slot mt of the job
+    int64_t done_base;   // tiles_done[done_base + mt]: finished tiles of m-tile mt of this segment
     float *Y;
     int64_t ldY;
     float *P;
     int ldP;
     int rows_valid;
-    int row_block_begin; // first global 32-row block of the segment (grouped measurement)
 };
 
-struct GroupedArgs {
-    const TcSegment *segs;     // device
+struct PersistentArgs {
+    const PSegment *segs;      // device
     const MeasureArgs *meas;   // device, one per segment
     int nseg;
-    int total_tiles;
-    int total_row_blocks;
+    int64_t total_tasks;
+    int *queue;                // device: next task (zero at launch)
+    int *measured;             // device: per job m-tile slot (zero at launch)
+    int *tiles_done;           // device: per segment m-tile (zero at launch)
     int a_planes, b_planes, nprod;
     int prod_a[kMaxProducts], prod_b[kMaxProducts];
+    uint64_t wait_limit_ns;    // bound of every wait (a dependency that never resolves ends the launch)
+    int stall_test;            // test hook: dependencies ask for one measurement more than ever happens
 };
 
 // Sets the kernel's shared-memory attribute (call once before launching, outside stream capture).
-cudaError_t prepare_contract_grouped();
-cudaError_t launch_contract_grouped(const GroupedArgs &g, int num_sms, int *d_err, cudaStream_t st);
-void launch_measure_grouped(const GroupedArgs &g, cudaStream_t st);
+cudaError_t prepare_batch_persistent();
+cudaError_t launch_batch_persistent(const PersistentArgs &g, int num_sms, int *d_err, cudaStream_t st);
 
 }  // namespace fastmps

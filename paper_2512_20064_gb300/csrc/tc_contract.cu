@@ -95,28 +95,6 @@ struct TcParams {
     MeasureArgs m;
 };
 
-// Named barriers among a subset of warps.  The non-.aligned forms are used
-// because lanes of one warp may reach them at different times.
-__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
-    asm volatile("barrier.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
-// Named barrier that also ORs a predicate over the participating threads: a
-// group decides together whether to leave a loop, so no thread is left
-// waiting at a later barrier for a thread that already left.
-__device__ __forceinline__ bool named_bar_any(int id, int nthreads, bool pred) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t"
-        "setp.ne.u32 p, %1, 0;\n\t"
-        "barrier.red.or.pred q, %2, %3, p;\n\t"
-        "selp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"((uint32_t)pred), "r"(id), "r"(nthreads)
-        : "memory");
-    return r != 0;
-}
-
 __device__ __forceinline__ void record_error(int *err, volatile int *abort_flag, int code) {
     *abort_flag = 1;
     atomicCAS(err, 0, code);

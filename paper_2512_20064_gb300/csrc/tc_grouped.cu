@@ -1,15 +1,14 @@
-// Grouped contraction and measurement: many independent chains in one launch.
+// Persistent batched contraction and measurement: many independent chains,
+// every site, in one launch.
 //
-// A "round" advances every active job (one MPS, one chunk of its rows) by one
-// site.  tc_contract_grouped_kernel is the persistent tcgen05 contraction of
-// tc_contract.cu (TMA producer warp, MMA warp, four epilogue warps, two TMEM
-// accumulators) run over the concatenated tile space of all segments of the
-// round: each tile looks up its segment (tensor maps in device memory,
-// n-tile width, K extent, scratch pointers), so jobs with different bond
-// dimensions, physical dimensions and row counts share the GPU in one launch.
-// measure_grouped_kernel then measures the rows of every segment
-// (Algorithm 2), one warp per 32 rows.  All rounds of a batch are captured
-// into one CUDA graph by the host engine.
+// The kernel is the tcgen05 contraction of tc_contract.cu (TMA producer warp,
+// MMA warp, four epilogue warps, two TMEM accumulators) with four measurement
+// warps, run over one task list: the tiles of every (job, chunk, site)
+// segment in round order.  Each task looks up its segment (tensor maps in
+// device memory, n-tile width, K extent, scratch pointers), so jobs with
+// different bond dimensions, physical dimensions and row counts share the GPU
+// in one launch; dependencies between consecutive sites of a job are kept per
+// 128-row m-tile with counters in global memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -24,21 +23,12 @@ namespace fastmps {
 namespace {
 
 constexpr int kBM = 128;
-constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;
 constexpr uint32_t kATileBytes = 16384;      // 128 rows x 128 bytes
 constexpr uint32_t kBPlaneBytesMax = 32768;  // 256 rows x 128 bytes
 constexpr int kMaxStages = 8;
 constexpr int kSmemLimit = 232448;
-constexpr int kBarrierBytes = 512;
-
-struct GParams {
-    const TcSegment *segs;
-    int nseg, total_tiles, stages, a_planes, b_planes, nprod;
-    uint32_t prod_code, stage_bytes;
-    int *err;
-};
 
 __device__ __forceinline__ void record_error(int *err, volatile int *abort_flag, int code) {
     *abort_flag = 1;
@@ -53,15 +43,74 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity) 
     return true;
 }
 
-// Segment of global tile t, searching forward from *cursor (tiles visited in increasing order).
-__device__ __forceinline__ const TcSegment *segment_of(const GParams &p, int t, int *cursor) {
-    int s = *cursor;
-    while (s + 1 < p.nseg && p.segs[s + 1].tile_begin <= t) ++s;
-    *cursor = s;
-    return &p.segs[s];
+// ===========================================================================
+// Persistent batched kernel: every round of every job in one launch.
+//
+// The tasks are the tiles of all segments of all rounds in round order.  The
+// producer thread of each thread block takes the next task from a global
+// counter (atomicAdd), so a block never waits on a task that no running block
+// has taken: a task's predecessors come earlier in the order and have been
+// taken already.  Before loading a task's left rows it waits -- bounded -- until
+// the job's m-tile slot has been measured `step` times (the rows of chunk c at
+// site k are written by the measurement of site k-1, and the chunk's scratch
+// rows are free once the previous step's measurement has read them).  The
+// epilogue stores the FP32 tile and its sums of squares and counts the finished
+// tiles of the m-tile; the block that finishes the last one hands the m-tile to
+// its four measurement warps, which draw, write the next left rows (Algorithm 2)
+// and release the slot's counter.  Warps: 0 TMA producer, 1 MMA issuer, 2-5
+// epilogue, 6-9 measurement (320 threads).
+// ===========================================================================
+constexpr int kPThreads = 320;
+constexpr int kTaskRing = 16;
+constexpr int kMRing = 4;
+constexpr int kPBarrierBytes = 3072;
+
+struct PParams {
+    const PSegment *segs;
+    const MeasureArgs *meas;
+    int nseg;
+    int64_t total_tasks;
+    unsigned long long *queue;
+    int *measured, *tiles_done;
+    int stages, a_planes, b_planes, nprod;
+    uint32_t prod_code, stage_bytes;
+    uint64_t limit_ns;
+    int stall;
+    int *err;
+};
+
+// Last segment whose first task is <= t (segments ordered by task_begin).
+__device__ __forceinline__ int psegment_of(const PParams &p, int64_t t) {
+    int lo = 0, hi = p.nseg - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.segs[mid].task_begin <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const GParams p) {
+// Bounded wait for *cnt >= target (GPU-scope acquire).  Gives up early when any block has recorded
+// an error; returns false then or when the limit runs out (*timed_out says which).
+__device__ __forceinline__ bool wait_counter(const int *cnt, int target, const PParams &p, bool *timed_out) {
+    *timed_out = false;
+    if (ld_acquire_gpu(cnt) >= target) return true;
+    const uint64_t t0 = global_ns();
+    uint32_t iter = 0;
+    while (ld_acquire_gpu(cnt) < target) {
+        __nanosleep(100);
+        if (((++iter) & 31u) == 0u) {
+            if (*reinterpret_cast<volatile int *>(p.err) != 0) return false;
+            if (global_ns() - t0 > p.limit_ns) {
+                *timed_out = true;
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kPThreads, 1) tc_batch_persistent_kernel(const PParams p) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -70,8 +119,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
     uint64_t *tfull = empty + p.stages;
     uint64_t *tempty = tfull + 2;
     uint64_t *drain = tempty + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    uint64_t *task_full = drain + 1;            // [kTaskRing] task published by the producer
+    uint64_t *task_empty = task_full + kTaskRing;  // [kTaskRing] read by the MMA thread and the epilogue
+    uint64_t *mfull = task_empty + kTaskRing;    // [kMRing] m-tile handed to the measurement warps
+    uint64_t *mempty = mfull + kMRing;
+    int64_t *task_id = reinterpret_cast<int64_t *>(mempty + kMRing);  // [kTaskRing]
+    int *task_seg = reinterpret_cast<int *>(task_id + kTaskRing);    // [kTaskRing]
+    int *m_seg = task_seg + kTaskRing;                               // [kMRing]
+    int *m_mt = m_seg + kMRing;                                      // [kMRing]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(m_mt + kMRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *m_sstar = reinterpret_cast<int *>(tmem_slot + 4);      // [128]
+    float *m_scale = reinterpret_cast<float *>(m_sstar + kBM);  // [128]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -84,6 +143,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
         mbar_init(&tempty[0], 128);
         mbar_init(&tempty[1], 128);
         mbar_init(drain, 1);
+        for (int r = 0; r < kTaskRing; ++r) {
+            mbar_init(&task_full[r], 1);
+            mbar_init(&task_empty[r], 2);
+        }
+        for (int r = 0; r < kMRing; ++r) {
+            mbar_init(&mfull[r], 1);
+            mbar_init(&mempty[r], kBM);
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -98,21 +165,49 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------- TMA producer ----------------
-            int stage = 0, cursor = 0;
+            // ---------------- TMA producer: takes tasks, waits for their left rows ----------------
+            int stage = 0;
             uint32_t phase = 0;
             int last_parity[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) last_parity[s] = -1;
             bool failed = false;
-            for (int t = blockIdx.x; t < p.total_tiles && !failed; t += gridDim.x) {
-                const TcSegment *sg = segment_of(p, t, &cursor);
-                const int lt = t - sg->tile_begin;
-                const int mt = lt / sg->num_n_tiles;
-                const int nt = lt - mt * sg->num_n_tiles;
+            for (int64_t seq = 0; !failed; ++seq) {
+                const int slot = (int)(seq % kTaskRing);
+                const uint32_t tpar = (uint32_t)((seq / kTaskRing) & 1);
+                if (!mbar_wait_bounded(&task_empty[slot], tpar ^ 1u, abort_flag, p.limit_ns)) {
+                    record_error(p.err, abort_flag, kDevTimeoutProducer);
+                    break;
+                }
+                const int64_t t = (int64_t)atomicAdd(p.queue, 1ull);
+                if (t >= p.total_tasks) {
+                    task_id[slot] = -1;
+                    mbar_arrive(&task_full[slot]);
+                    break;
+                }
+                const int si = psegment_of(p, t);
+                const PSegment *sg = &p.segs[si];
+                const int64_t lt = t - sg->task_begin;
+                const int mt = (int)(lt / sg->num_n_tiles);
+                const int nt = (int)(lt - (int64_t)mt * sg->num_n_tiles);
+                const int target = sg->step + p.stall;
+                if (target > 0) {
+                    bool timed_out;
+                    if (!wait_counter(p.measured + sg->slot_base + mt, target, p, &timed_out)) {
+                        if (timed_out) record_error(p.err, abort_flag, kDevTimeoutDependency);
+                        else *abort_flag = 1;
+                        break;
+                    }
+                    // the rows were written through the generic proxy by another block: order them
+                    // before this thread's tensor-memory-access (async proxy) loads
+                    fence_proxy_async_global();
+                }
+                task_id[slot] = t;
+                task_seg[slot] = si;
+                mbar_arrive(&task_full[slot]);
                 const int y_a = sg->row0 + mt * kBM;
                 const int y_b = nt * sg->bn;
                 for (int kb = 0; kb < sg->num_k_blocks; ++kb) {
-                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag)) {
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.limit_ns)) {
                         record_error(p.err, abort_flag, kDevTimeoutProducer);
                         failed = true;
                         break;
@@ -132,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
                     }
                 }
             }
-            if (failed)
+            if (*abort_flag)
                 for (int s = 0; s < p.stages; ++s)
                     if (last_parity[s] >= 0) mbar_wait_drain(&full[s], (uint32_t)last_parity[s]);
         }
@@ -140,22 +235,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            int stage = 0, lt = 0, cursor = 0;
+            int stage = 0;
             uint32_t phase = 0;
-            bool failed = false, issued = false;
-            for (int t = blockIdx.x; t < p.total_tiles && !failed; t += gridDim.x, ++lt) {
-                const TcSegment *sg = segment_of(p, t, &cursor);
-                const int buf = lt & 1;
-                const uint32_t use = (uint32_t)(lt >> 1);
-                if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag)) {
+            bool issued = false;
+            for (int64_t seq = 0;; ++seq) {
+                const int slot = (int)(seq % kTaskRing);
+                if (!mbar_wait_bounded(&task_full[slot], (uint32_t)((seq / kTaskRing) & 1), abort_flag,
+                                       p.limit_ns)) {
                     record_error(p.err, abort_flag, kDevTimeoutMma);
-                    failed = true;
+                    break;
+                }
+                const int64_t t = task_id[slot];
+                const int si = task_seg[slot];
+                mbar_arrive(&task_empty[slot]);
+                if (t < 0) break;
+                const PSegment *sg = &p.segs[si];
+                const int buf = (int)(seq & 1);
+                const uint32_t use = (uint32_t)(seq >> 1);
+                if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag, p.limit_ns)) {
+                    record_error(p.err, abort_flag, kDevTimeoutMma);
                     break;
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)buf * kAccStride;
+                const uint32_t idesc = sg->idesc;
+                bool failed = false;
                 for (int kb = 0; kb < sg->num_k_blocks; ++kb) {
-                    if (!mbar_wait_bounded(&full[stage], phase, abort_flag)) {
+                    if (!mbar_wait_bounded(&full[stage], phase, abort_flag, p.limit_ns)) {
                         record_error(p.err, abort_flag, kDevTimeoutMma);
                         failed = true;
                         break;
@@ -170,7 +276,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
                         const uint64_t bd = sw128_kmajor_desc(sb + pb * kBPlaneBytesMax);
 #pragma unroll
                         for (int k16 = 0; k16 < 4; ++k16)
-                            tc_mma_bf16(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), sg->idesc,
+                            tc_mma_bf16(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), idesc,
                                         (kb | q | k16) != 0 ? 1u : 0u);
                     }
                     issued = true;
@@ -183,24 +289,38 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
                 if (failed) break;
                 tc_commit(&tfull[buf]);
             }
-            if (failed && issued) {
+            if (*abort_flag && issued) {
                 tc_commit(drain);
                 mbar_wait_drain(drain, 0u);
             }
         }
         __syncwarp();
-    } else {
+    } else if (warp < 6) {
         // ---------------- epilogue: warps 2..5 ----------------
         const int quad = warp & 3;
-        int lt = 0, cursor = 0;
-        for (int t = blockIdx.x; t < p.total_tiles; t += gridDim.x, ++lt) {
-            const TcSegment *sg = segment_of(p, t, &cursor);
-            const int buf = lt & 1;
-            const uint32_t use = (uint32_t)(lt >> 1);
-            const int tl = t - sg->tile_begin;
-            const int mt = tl / sg->num_n_tiles;
-            const int nt = tl - mt * sg->num_n_tiles;
-            if (!mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag)) {
+        int ring = 0;
+        uint32_t ring_phase = 0;
+        for (int64_t seq = 0;; ++seq) {
+            const int slot = (int)(seq % kTaskRing);
+            const bool got = mbar_wait_bounded(&task_full[slot], (uint32_t)((seq / kTaskRing) & 1), abort_flag,
+                                               p.limit_ns);
+            if (named_bar_any(1, 128, !got)) {
+                record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                break;
+            }
+            const int64_t t = task_id[slot];
+            const int si = task_seg[slot];
+            named_bar_sync(1, 128);  // every thread has read the slot
+            if (threadIdx.x == 64) mbar_arrive(&task_empty[slot]);
+            if (t < 0) break;
+            const PSegment *sg = &p.segs[si];
+            const int64_t lt = t - sg->task_begin;
+            const int mt = (int)(lt / sg->num_n_tiles);
+            const int nt = (int)(lt - (int64_t)mt * sg->num_n_tiles);
+            const int buf = (int)(seq & 1);
+            const uint32_t use = (uint32_t)(seq >> 1);
+            const bool ready = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag, p.limit_ns);
+            if (named_bar_any(1, 128, !ready)) {
                 record_error(p.err, abort_flag, kDevTimeoutEpilogue);
                 break;
             }
@@ -230,8 +350,79 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
             tc_fence_before();
             mbar_arrive(&tempty[buf]);
             if (valid) sg->P[(int64_t)row * sg->ldP + nt] = ss;
+            // count the tile; the block that finishes the m-tile's last tile measures it
+            named_bar_sync(1, 128);
+            if (threadIdx.x == 64) {
+                __threadfence();  // the group's stores (ordered by the barrier) before the count
+                const int old = atomicAdd(p.tiles_done + sg->done_base + mt, 1);
+                if (old == sg->num_n_tiles - 1) {
+                    __threadfence();  // every block's tiles of this m-tile before the measurement reads them
+                    if (!mbar_wait_bounded(&mempty[ring], ring_phase ^ 1u, abort_flag, p.limit_ns)) {
+                        record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                    } else {
+                        m_seg[ring] = si;
+                        m_mt[ring] = mt;
+                        mbar_arrive(&mfull[ring]);
+                        if (++ring == kMRing) {
+                            ring = 0;
+                            ring_phase ^= 1u;
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (threadIdx.x == 64) {
+            // no more tiles from this block: stop the measurement warps
+            if (mbar_wait_bounded(&mempty[ring], ring_phase ^ 1u, abort_flag, p.limit_ns)) {
+                m_seg[ring] = -1;
+                mbar_arrive(&mfull[ring]);
+            }
+        }
+    } else {
+        // ---------------- measurement: warps 6..9 ----------------
+        const int m = threadIdx.x - 192;  // the row of the m-tile this thread draws
+        const int mw = m >> 5;
+        int ring = 0;
+        uint32_t ring_phase = 0;
+        while (true) {
+            const bool ready = mbar_wait_bounded(&mfull[ring], ring_phase, abort_flag, p.limit_ns);
+            if (named_bar_any(2, 128, !ready)) {
+                record_error(p.err, abort_flag, kDevTimeoutMeasure);
+                break;
+            }
+            const int si = m_seg[ring];
+            const int mt = m_mt[ring];
+            mbar_arrive(&mempty[ring]);
+            if (++ring == kMRing) {
+                ring = 0;
+                ring_phase ^= 1u;
+            }
+            if (si < 0) break;
+            const MeasureArgs &a = p.meas[si];
+            const int rows = p.segs[si].rows_valid;
+            const int row = mt * kBM + m;
+            int sstar = 0;
+            float scale = 0.f;
+            if (row < rows) sstar = measure_draw(a, row, &scale);
+            m_sstar[m] = sstar;
+            m_scale[m] = scale;
+            named_bar_sync(2, 128);
+            for (int j = 0; j < 32; ++j) {
+                const int r = mt * kBM + mw * 32 + j;
+                if (r >= rows) break;
+                const int sj = m_sstar[mw * 32 + j];
+                const float *ysrc = a.Y + (int64_t)r * a.ldY + (int64_t)sj * a.Cs;
+                measure_write_row(a, lane, ysrc, m_scale[mw * 32 + j], a.row0 + r);
+            }
+            named_bar_sync(2, 128);  // the m-tile's next left rows are written
+            if (threadIdx.x == 192) {
+                fence_proxy_async_global();
+                red_release_add_gpu(p.measured + p.segs[si].slot_base + mt, 1);
+            }
         }
     }
+
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -240,74 +431,43 @@ __global__ void __launch_bounds__(kThreads, 1) tc_contract_grouped_kernel(const 
     }
 }
 
-constexpr int kMeasureThreads = 128;
-constexpr int kMeasureWarps = kMeasureThreads / 32;
-
-// One warp per 32 rows of one segment; warp w of the grid covers global 32-row block w.
-__global__ void __launch_bounds__(kMeasureThreads)
-measure_grouped_kernel(const TcSegment *__restrict__ segs, const MeasureArgs *__restrict__ meas, int nseg,
-                       int total_blocks) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gb = blockIdx.x * kMeasureWarps + warp;
-    if (gb >= total_blocks) return;
-    int lo = 0, hi = nseg - 1;  // last segment with row_block_begin <= gb
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (segs[mid].row_block_begin <= gb) lo = mid;
-        else hi = mid - 1;
-    }
-    const MeasureArgs &a = meas[lo];
-    const int base = (gb - segs[lo].row_block_begin) * 32;
-    if (base >= a.rows) return;
-    const int row = base + lane;
-    int sstar = 0;
-    float scale = 0.f;
-    if (row < a.rows) sstar = measure_draw(a, row, &scale);
-    const int count = min(32, a.rows - base);
-    for (int j = 0; j < count; ++j) {
-        const int sj = __shfl_sync(0xffffffffu, sstar, j);
-        const float scj = __shfl_sync(0xffffffffu, scale, j);
-        const int r = base + j;
-        measure_write_row(a, lane, a.Y + (int64_t)r * a.ldY + (int64_t)sj * a.Cs, scj, a.row0 + r);
-    }
-}
-
 }  // namespace
 
-cudaError_t prepare_contract_grouped() {
-    return cudaFuncSetAttribute(tc_contract_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+cudaError_t prepare_batch_persistent() {
+    return cudaFuncSetAttribute(tc_batch_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
 }
 
-cudaError_t launch_contract_grouped(const GroupedArgs &g, int num_sms, int *d_err, cudaStream_t st) {
-    if (g.nseg <= 0 || g.total_tiles <= 0) return cudaSuccess;
-    GParams p;
-    p.segs = g.segs;
-    p.nseg = g.nseg;
-    p.total_tiles = g.total_tiles;
-    p.a_planes = g.a_planes;
-    p.b_planes = g.b_planes;
-    p.nprod = g.nprod;
+cudaError_t launch_batch_persistent(const PersistentArgs &g, int num_sms, int *d_err, cudaStream_t st) {
+    if (g.nseg <= 0 || g.total_tasks <= 0) return cudaSuccess;
     if (g.nprod < 1 || g.nprod > kMaxProducts || g.a_planes < 1 || g.a_planes > 3 || g.b_planes < 1 ||
         g.b_planes > 2)
         return cudaErrorInvalidValue;
+    PParams p;
+    p.segs = g.segs;
+    p.meas = g.meas;
+    p.nseg = g.nseg;
+    p.total_tasks = g.total_tasks;
+    p.queue = reinterpret_cast<unsigned long long *>(g.queue);
+    p.measured = g.measured;
+    p.tiles_done = g.tiles_done;
+    p.a_planes = g.a_planes;
+    p.b_planes = g.b_planes;
+    p.nprod = g.nprod;
     p.prod_code = 0;
     for (int q = 0; q < g.nprod; ++q)
         p.prod_code |= ((uint32_t)g.prod_a[q] | ((uint32_t)g.prod_b[q] << 2)) << (4 * q);
     p.stage_bytes = (uint32_t)g.a_planes * kATileBytes + (uint32_t)g.b_planes * kBPlaneBytesMax;
-    p.stages = (kSmemLimit - 1024 - kBarrierBytes) / (int)p.stage_bytes;
+    p.stages = (kSmemLimit - 1024 - kPBarrierBytes) / (int)p.stage_bytes;
     if (p.stages > kMaxStages) p.stages = kMaxStages;
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
+    p.limit_ns = g.wait_limit_ns;
+    p.stall = g.stall_test ? 1 : 0;
     p.err = d_err;
-    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kBarrierBytes;
-    const int grid = g.total_tiles < num_sms ? g.total_tiles : num_sms;
-    tc_contract_grouped_kernel<<<grid, kThreads, smem, st>>>(p);
+    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kPBarrierBytes;
+    const int grid = g.total_tasks < num_sms ? (int)g.total_tasks : num_sms;
+    tc_batch_persistent_kernel<<<grid, kPThreads, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-void launch_measure_grouped(const GroupedArgs &g, cudaStream_t st) {
-    if (g.nseg <= 0 || g.total_row_blocks <= 0) return;
-    const int grid = (g.total_row_blocks + kMeasureWarps - 1) / kMeasureWarps;
-    measure_grouped_kernel<<<grid, kMeasureThreads, 0, st>>>(g.segs, g.meas, g.nseg, g.total_row_blocks);
-}
 
 }  // namespace fastmps

@@ -20,7 +20,7 @@ MUTANTS = {
                               "const size_t row = (size_t)2 * a * (cols == chi_l ? cols : chi_r);"),
     "no_cumulative_sum": ("        acc += w[s];\n        C[s] = acc;", "        acc += w[s];\n        C[s] = w[s];"),
     "threshold_not_scaled_by_Z": ("const double t = u * Z;", "const double t = u;"),
-    "logprob_without_Z": ("lp += log(w[s]) - log(Z);", "lp += log(w[s]);"),
+    "logprob_without_Z": ("lps[j] += log(w[s]) - log(Z);", "lps[j] += log(w[s]);"),
     "no_renormalisation": ("const double inv = 1.0 / sqrt(w[s]);", "const double inv = 1.0;"),
     "uniform_wrong_site_key": ("orc_uniform(seed, n, (uint32_t)k, job)", "orc_uniform(seed, n, (uint32_t)(k + 1), job)"),
     "philox_wrong_multiplier": ("#define ORC_PHILOX_M1 0xCD9E8D57u", "#define ORC_PHILOX_M1 0xCD9E8D59u"),
@@ -29,8 +29,8 @@ MUTANTS = {
                               "v[2 * b] = y[2 * (((s + 1) % d) * cr + b)] * inv;"),
     "vidal_lambda_not_squared": ("acc += (re * re + im * im) * lam[b] * lam[b];",
                                  "acc += (re * re + im * im) * lam[b];"),
-    "vidal_carry_without_lambda": ("v[2 * b] *= lam[k][b];\n                        v[2 * b + 1] *= lam[k][b];",
-                                   "v[2 * b] *= 1.0;\n                        v[2 * b + 1] *= 1.0;"),
+    "vidal_carry_without_lambda": ("v[2 * b] *= lam[k][b];\n                            v[2 * b + 1] *= lam[k][b];",
+                                   "v[2 * b] *= 1.0;\n                            v[2 * b + 1] *= 1.0;"),
     "displacement_transposed": ("const double dr = D[2 * (s * d + t)], di = D[2 * (s * d + t) + 1];",
                                 "const double dr = D[2 * (t * d + s)], di = D[2 * (t * d + s) + 1];"),
     "zassenhaus_lowering_sign": ("Y[(j - 1) * n + j] = -conj(mu) * r;", "Y[(j - 1) * n + j] = conj(mu) * r;"),
