@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="precision",
                     choices=["precision", "plain", "tiny", "batching", "streaming", "displacement", "knee",
-                             "dynamic"])
+                             "dynamic", "splitk"])
     ap.add_argument("--rows-cap", type=int, default=None, help="batching: cap on the rows sampled per job")
     ap.add_argument("--rows-scale", type=float, default=1 / 16,
                     help="batching: each job's N (log-uniform in [1e3, 1e6]) is multiplied by this factor")
@@ -788,11 +788,54 @@ def run_knee(args, rank, ws, local):
             "peak": float(peaks.get("bf16_tflops_sustained", 1700.0)), "peak_source": src, "points": points}
 
 
+def run_splitk(args, rank, ws, local):
+    """On-chip split-K study (the paper's single- vs double-site split of Sec. 3.2, inside one GPU):
+    contraction throughput against the rows per contraction launch, with one thread block per output
+    tile and with a cluster of 2 or 4 blocks splitting the contraction index of each tile (partial
+    tiles added through distributed shared memory).  Shapes: chi = 10^4, d = 3 (the streaming
+    workload's bond dimension) and chi = 256, d = 4 (where few rows give fewer tiles than SMs)."""
+    import torch
+
+    import paper_2512_20064_gb300 as F
+
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    results = []
+    for (M, d, chi, N) in ((20, 3, 10_000, 4096), (16, 4, 256, 8192)):
+        b, ts, idx = gen.mps_tensors(M, d, chi, base_seed=6060, skew=1.5, pool=2, device=device)
+        out_s = torch.empty((N, M), dtype=torch.uint8, device=device)
+        out_l = torch.empty(N, dtype=torch.float64, device=device)
+        for n2 in (128, 256, 512, 1024, 2048, 4096, 8192):
+            if n2 > N:
+                continue
+            row = {"chi": chi, "d": d, "rows_per_launch": n2}
+            for ks in (0, 2, 4):
+                with F.Sampler(device=local, precision=args.precision or "bf16x2", max_microbatch=n2,
+                               k_split=ks) as s:
+                    s.load_chain(ts, site_index=idx)
+                    for _ in range(max(1, args.warmup)):
+                        s.sample(b, d, N, 1, out_samples=out_s, out_logprob=out_l)
+                    torch.cuda.synchronize()
+                    s.sample(b, d, N, 2, out_samples=out_s, out_logprob=out_l)
+                    st = s.stats()
+                row[f"tflops_issued_ksplit{max(ks, 1)}"] = st["flops_issued"] / (st["ms_contract"] / 1e3) / 1e12
+                row[f"ms_contract_ksplit{max(ks, 1)}"] = st["ms_contract"]
+            results.append(row)
+        del ts
+        torch.cuda.empty_cache()
+    peaks, src = measured_peaks()
+    return {"metric": "contraction TFLOP/s (issued) vs rows per launch, with and without on-chip split-K",
+            "unit": "TFLOP/s", "n_gpus": 1, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "M=20 d=3 chi=1e4 (N=4096) and M=16 d=4 chi=256 (N=8192), pool of 2 interior "
+                                   "isometries", "precision": args.precision or "bf16x2"},
+            "peak": float(peaks.get("bf16_tflops_sustained", 1700.0)), "peak_source": src, "points": results}
+
+
 def main():
     args = parse()
     rank, ws, local = dist_setup()
-    if args.workload in ("knee", "dynamic") and args.impl == "ours":
-        line = (run_knee if args.workload == "knee" else run_dynamic)(args, rank, ws, local)
+    if args.workload in ("knee", "dynamic", "splitk") and args.impl == "ours":
+        line = {"knee": run_knee, "dynamic": run_dynamic, "splitk": run_splitk}[args.workload](args, rank, ws, local)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

@@ -95,6 +95,11 @@ typedef struct fastmps_options {
                                renormalised block -- no FP32 scratch.  Sites whose row does not
                                fit one cluster (more than 32 column tiles, or column tiles not
                                a multiple of 64 wide) take mode 0. */
+    int k_split;            /* BF16 modes, separate measurement: 0 or 1 = one thread block per output
+                               tile; 2..8 = a thread-block cluster of that many blocks per tile, each
+                               summing its share of the contraction index, partial tiles added
+                               through distributed shared memory (the paper's single- vs
+                               double-site split of Sec. 3.2, inside one GPU; an experiment). */
 } fastmps_options;
 
 typedef struct fastmps_ctx *fastmps_handle;

@@ -40,7 +40,8 @@ C64, C128 = 0, 1
 
 class fastmps_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("residency", ctypes.c_int), ("max_microbatch", ctypes.c_int64),
-                ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p), ("fused_measure", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p), ("fused_measure", ctypes.c_int),
+                ("k_split", ctypes.c_int)]
 
 
 class fastmps_stats(ctypes.Structure):
@@ -405,13 +406,14 @@ class Sampler:
     """A handle of the library: load site tensors once, then sample many times."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", residency: str = "hbm", max_microbatch: int = 0,
-                 stream=None, fused_measure=False, autotune: bool = False):
+                 stream=None, fused_measure=False, autotune: bool = False, k_split: int = 0):
         """``fused_measure``: False / "separate" (measurement kernel after each contraction), True / "cta"
         (measurement warps inside the contraction kernel), "cluster" (single-pass cluster kernel, no
         scratch, where a site's row fits one cluster)."""
         o = fastmps_default_options()
         o.fused_measure = MEASUREMENTS[fused_measure] if isinstance(fused_measure, str) else int(bool(fused_measure))
         o.autotune = int(bool(autotune))
+        o.k_split = int(k_split)
         o.precision = PRECISIONS[precision]
         o.residency = RESIDENCIES[residency]
         o.max_microbatch = int(max_microbatch)

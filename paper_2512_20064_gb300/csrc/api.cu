@@ -114,6 +114,7 @@ struct DevBuf {
 
 struct Tensor {
     SiteLayout L;
+    int measure_mode = 0;  // autotuned: 2 = single-pass cluster kernel for this site, 0 = two-pass
     // resident operands (device)
     DevBuf B_hi, B_lo, Bt, B8;
     float fp8_scale = 1.f;  // FP8: stored value = e4m3(A * fp8_scale)
@@ -274,12 +275,16 @@ bool is_device_ptr(const void *p) {
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner: n-tile width of the tensor-core contraction per site shape.
-// Candidates are 256, 128 and 64 columns (those not wider than the padded
-// block 2 chi_r); each is timed on a probe contraction of 8192 rows of the
-// real operand layout, best of three.  Results are cached per process and,
-// when FASTMPS_TUNE_CACHE names a file, in that file as a flat JSON object
-// {"precision:chi_l:d:chi_r": bn, ...}.
+// Autotuner: n-tile width and measurement mode per site shape.
+// Candidates are the two-pass path (contraction + measurement kernel) with
+// 256, 128 and 64 columns per n-tile (those not wider than the padded block
+// 2 chi_r), and the single-pass cluster kernel where the site's row fits one
+// cluster; each is timed on a probe of 8192 rows (contraction and
+// measurement of one site), best of three.  The pipeline depth is not a
+// candidate: with one thread block per SM the deepest ring that fits shared
+// memory never loses.  Results are cached per process and, when
+// FASTMPS_TUNE_CACHE names a file, in that file as a flat JSON object
+// {"precision:chi_l:d:chi_r": bn + 10000 * mode, ...} (mode 2: cluster).
 // ---------------------------------------------------------------------------
 std::mutex g_tune_mutex;
 std::map<std::string, int> g_tuned;
@@ -328,26 +333,37 @@ void tune_cache_store() {
     fclose(f);
 }
 
-// Times one probe contraction per candidate width on the staged tensor; returns the fastest width.
+// Times the candidates on the staged tensor; returns bn + 10000 * mode of the fastest.
 int autotune_bn(fastmps_handle h, int chi_l, int d, int chi_r, int is_f64) {
     const PrecisionPlan plan = plan_of(h->opt.precision);
     const int widest = (int)std::min<int64_t>(256, roundup(2 * (int64_t)chi_r, 32));
     const int64_t rows = 8192;
     int best = widest;
     float best_ms = 1e30f;
-    for (int bn : {256, 128, 64}) {
+    const int K_next = (int)roundup(2 * (int64_t)chi_r, 64);
+    DevBuf Vn[3], O, logp, err;
+    bool ok = O.ensure((size_t)rows) && logp.ensure((size_t)rows * 8) && err.ensure(sizeof(int));
+    for (int p = 0; p < plan.a_planes; ++p) ok = ok && Vn[p].ensure((size_t)rows * K_next * 2);
+    if (!ok) return best;
+    for (int cand = 0; cand < 4; ++cand) {
+        const bool cluster = cand == 3;
+        const int bn = cluster ? widest : (cand == 0 ? 256 : cand == 1 ? 128 : 64);
         if (bn > widest) continue;
         SiteLayout L = make_layout(h->opt.precision, chi_l, d, chi_r, bn);
-        DevBuf B[2], V[3], Y, P, err;
-        bool ok = true;
+        int cC = 0, cT = 0;
+        if (cluster && !(cluster_plan(L, &cC, &cT) && cluster_capacity(plan.a_planes, plan.b_planes, L) > 0))
+            continue;
+        DevBuf B[2], V[3], Y, P;
         for (int p = 0; p < plan.b_planes; ++p) ok = ok && B[p].ensure((size_t)L.ncols * L.K_pad * 2);
         for (int p = 0; p < plan.a_planes; ++p) ok = ok && V[p].ensure((size_t)rows * L.K_pad * 2);
-        ok = ok && Y.ensure((size_t)rows * L.ncols * 4) && P.ensure((size_t)rows * (L.ncols / L.bn) * 4) &&
-             err.ensure(sizeof(int));
+        if (!cluster)
+            ok = ok && Y.ensure((size_t)rows * L.ncols * 4) && P.ensure((size_t)rows * (L.ncols / L.bn) * 4);
         if (!ok) break;
         launch_repack_bf16(h->staging.p, is_f64, L, B[0].as<__nv_bfloat16>(),
                            plan.b_planes > 1 ? B[1].as<__nv_bfloat16>() : nullptr, h->stream);
-        for (int p = 0; p < plan.a_planes; ++p) cudaMemsetAsync(V[p].p, 0, V[p].bytes, h->stream);
+        __nv_bfloat16 *Vp[3] = {nullptr, nullptr, nullptr};
+        for (int p = 0; p < plan.a_planes; ++p) Vp[p] = V[p].as<__nv_bfloat16>();
+        launch_init_left_bf16(Vp, plan.a_planes, rows, L.K_pad, h->stream);  // every row the vector [1, 0, ...]
         cudaMemsetAsync(err.p, 0, sizeof(int), h->stream);
         TcArgs ta;
         ta.a_planes = plan.a_planes;
@@ -365,14 +381,37 @@ int autotune_bn(fastmps_handle h, int chi_l, int d, int chi_r, int is_f64) {
         ta.row0 = 0;
         ta.rows_pad = (int)rows;
         ContractOut co{Y.as<float>(), L.ncols, P.as<float>(), L.ncols / L.bn, (int)rows};
-        ta.has_tmY = encode_2d_f32_scratch(&ta.tmY, Y.p, L.ncols, rows, L.ncols);
+        ta.has_tmY = !cluster && encode_2d_f32_scratch(&ta.tmY, Y.p, L.ncols, rows, L.ncols);
+        MeasureArgs ma{};
+        ma.Y = co.Y;
+        ma.ldY = co.ldY;
+        ma.P = co.P;
+        ma.ldP = co.ldP;
+        ma.d = d;
+        ma.chi_r = chi_r;
+        ma.Cs = L.Cs;
+        ma.tiles_per_s = L.tiles_per_s;
+        ma.rows = (int)rows;
+        ma.seed = 1;
+        ma.ld_next = K_next;
+        ma.K_next = K_next;
+        for (int p = 0; p < plan.a_planes; ++p) ma.Vp[p] = Vn[p].as<__nv_bfloat16>();
+        ma.nplanes = plan.a_planes;
+        ma.outcomes = O.as<uint8_t>();
+        ma.logp = logp.as<double>();
+        ma.err = err.as<int>();
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float ms_min = 1e30f;
         for (int rep = 0; rep < 3; ++rep) {
             cudaEventRecord(e0, h->stream);
-            launch_contract_tc(ta, L, co, h->num_sms, err.as<int>(), h->stream);
+            if (cluster) {
+                launch_contract_tc_cluster(ta, L, (int)rows, err.as<int>(), h->stream, ma);
+            } else {
+                launch_contract_tc(ta, L, co, h->num_sms, err.as<int>(), h->stream);
+                launch_measure(ma, h->stream);
+            }
             cudaEventRecord(e1, h->stream);
             cudaEventSynchronize(e1);
             float ms = 0;
@@ -387,7 +426,7 @@ int autotune_bn(fastmps_handle h, int chi_l, int d, int chi_r, int is_f64) {
         }
         if (ms_min < best_ms) {
             best_ms = ms_min;
-            best = bn;
+            best = bn + (cluster ? 20000 : 0);
         }
     }
     return best;
@@ -475,15 +514,16 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
             tune_cache_load();
             const std::string key = tune_key(h->opt.precision, chi_l, d, chi_r);
             auto it = g_tuned.find(key);
-            int bn;
+            int code;
             if (it != g_tuned.end()) {
-                bn = it->second;
+                code = it->second;
             } else {
-                bn = autotune_bn(h, chi_l, d, chi_r, dtype == FASTMPS_C128);
-                g_tuned[key] = bn;
+                code = autotune_bn(h, chi_l, d, chi_r, dtype == FASTMPS_C128);
+                g_tuned[key] = code;
                 tune_cache_store();
             }
-            t.L = make_layout(h->opt.precision, chi_l, d, chi_r, bn);
+            t.L = make_layout(h->opt.precision, chi_l, d, chi_r, code % 10000);
+            t.measure_mode = code / 10000;
         }
         const size_t op_elems = (size_t)t.L.ncols * t.L.K_pad;
         if (!t.B_hi.ensure(op_elems * 2)) return fail(h, FASTMPS_ERR_OOM, "site operand allocation failed");
@@ -587,7 +627,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         ts[k] = t;
         ldV = std::max(ldV, t->L.K_pad);
         int cC = 0, cT = 0;
-        on_cluster[k] = want_cluster && cluster_plan(t->L, &cC, &cT) &&
+        on_cluster[k] = (want_cluster || (t->measure_mode == 2 && h->opt.fused_measure == 0 && is_bf16(h) &&
+                                          !is_fp8(h) && !mu_dev)) &&
+                        cluster_plan(t->L, &cC, &cT) &&
                         cluster_capacity(plan_of(h->opt.precision).a_planes, plan_of(h->opt.precision).b_planes,
                                          t->L) > 0;
         if (!on_cluster[k]) {
@@ -881,7 +923,10 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 ta.row0 = r0;
                 ta.rows_pad = (int)rows_pad;
                 ta.has_tmY = !fused && encode_2d_f32_scratch(&ta.tmY, co.Y, L.ncols, rows, L.ncols);
-                e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st, fused ? &ma : nullptr);
+                if (h->opt.k_split >= 2 && ta.has_tmY && !fp8 && L.K_pad / L.bk >= h->opt.k_split)
+                    e = launch_contract_tc_splitk(ta, L, co, h->opt.k_split, d_err, st);
+                else
+                    e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st, fused ? &ma : nullptr);
                 if (e != cudaSuccess) return cuda_fail(h, e, "contraction launch");
             } else {
                 launch_contract_f32(h->V[cur][0].as<float>(), ldV, r0, rows_pad, t->Bt.as<float>(), L, co, st);
@@ -961,6 +1006,7 @@ void fastmps_default_options(fastmps_options *opt) {
     opt->autotune = 0;
     opt->stream = nullptr;
     opt->fused_measure = 0;
+    opt->k_split = 0;
 }
 
 int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) {
@@ -974,6 +1020,10 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
     if (opt) o = *opt;
     if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_FP8X2) {
         g_create_error = "unknown precision";
+        return FASTMPS_ERR_INVALID_ARG;
+    }
+    if (o.k_split < 0 || o.k_split > 8) {
+        g_create_error = "k_split must be 0..8";
         return FASTMPS_ERR_INVALID_ARG;
     }
     if (o.residency != FASTMPS_RESIDENT_HBM && o.residency != FASTMPS_HOST_STREAM) {

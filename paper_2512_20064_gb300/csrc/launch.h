@@ -84,6 +84,13 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
 // Single-pass cluster variant (no scratch): true if the site's row fits one cluster's tensor memory
 // (C CTAs of T n-tiles each, C <= 16, the n-tile width a multiple of 64).
 bool cluster_plan(const SiteLayout &L, int *C, int *T);
+// On-chip split-K (a study of the paper's single- vs double-site splitting inside one GPU): a cluster of
+// ksplit CTAs per output tile, each accumulating 1/ksplit of the k-blocks; partial tiles are added
+// through distributed shared memory into rank 0, which writes Y and P as launch_contract_tc does
+// (a.has_tmY required).  The sum is taken in rank order, so Y differs from the unsplit kernel by
+// rounding only.
+cudaError_t launch_contract_tc_splitk(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int ksplit,
+                                      int *d_err, cudaStream_t st, int *clusters_out = nullptr);
 // Clusters of the site's plan that can be resident at once on the current device (0: not runnable).
 int cluster_capacity(int a_planes, int b_planes, const SiteLayout &L);
 // Contraction + measurement of rows_valid rows in one launch; m describes the draw and the next left

@@ -74,7 +74,7 @@ constexpr int kMaxClusterTiles = 32;         // cluster variant: n-tiles per m-t
 constexpr int kMaxClusterCTAs = 16;          // largest (non-portable) cluster
 constexpr uint32_t kClusterBytes = 64 + 4 * 128 * 4 * 2;  // 4 mbarriers + partial sums [2][T <= 4][128]
 
-enum TcMode : int { kTwoPass = 0, kFusedCta = 1, kClusterFused = 2 };
+enum TcMode : int { kTwoPass = 0, kFusedCta = 1, kClusterFused = 2, kSplitK = 3 };
 
 struct TcParams {
     int num_m_tiles, num_n_tiles, num_k_blocks, bn;
@@ -91,6 +91,7 @@ struct TcParams {
     int rows_valid;
     int *err;
     int cl_T;  // cluster variant: n-tiles per CTA per m-tile (the cluster has num_n_tiles / cl_T CTAs)
+    int ksplit;  // split-K variant: CTAs per cluster, each accumulating 1/ksplit of the k-blocks
     // fused measurement
     MeasureArgs m;
 };
@@ -122,6 +123,12 @@ __device__ __forceinline__ bool tile_of(const TcParams &p, int i, int &mt, int &
         nt = (int)cluster_ctarank() * p.cl_T + (i - q * p.cl_T);
         mt = (int)cluster_id_x() + q * (int)cluster_count_x();
         return mt < p.num_m_tiles;
+    }
+    if (kMode == kSplitK) {
+        const int tile = (int)cluster_id_x() + i * (int)cluster_count_x();
+        mt = tile / p.num_n_tiles;
+        nt = tile - mt * p.num_n_tiles;
+        return tile < p.num_m_tiles * p.num_n_tiles;
     }
     if (kMode == kFusedCta) {
         const int q = i / p.num_n_tiles;
@@ -316,6 +323,122 @@ __device__ __forceinline__ void cluster_epilogue(const TcParams &p, uint32_t tme
     }
 }
 
+// ---------------------------------------------------------------------------
+// Split-K variant: a cluster of S CTAs computes one output tile, CTA rank j
+// accumulating k-blocks [j*nkb/S, (j+1)*nkb/S) in its own tensor memory.  Ranks
+// j >= 1 stage each 128 x 32 chunk of their partial tile in shared memory (the
+// swizzled layout of the scratch store) and signal rank 0 with a remote
+// mbarrier arrive; rank 0 adds the partial chunks to its own through
+// distributed shared memory (rank order), releases the staging buffer, and
+// stores the sum and the row's sum of squares like the two-pass epilogue.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 ld_shared_cluster_v4(uint32_t cluster_addr) {
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(cluster_addr)
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void splitk_epilogue(const TcParams &p, const CUtensorMap *tmY, uint32_t tmem_base,
+                                                uint64_t *tfull, uint64_t *tempty, uint64_t *chunk_ready,
+                                                uint64_t *chunk_free, uint8_t *ystage, volatile int *abort_flag,
+                                                int warp, int lane) {
+    const int quad = warp & 3;
+    const int rl = quad * 32 + lane;  // row of the tile (tensor-memory lane)
+    const uint32_t rank = cluster_ctarank();
+    const uint32_t S = (uint32_t)p.ksplit;
+    const uint32_t ystage_addr = smem_u32(ystage);
+    int lt = 0;
+    uint32_t q = 0;  // chunks handled so far (staging buffer q & 1)
+    int mt, nt;
+    for (int i = 0; tile_of<kSplitK>(p, i, mt, nt); ++i, ++lt) {
+        const int buf = lt & 1;
+        const uint32_t use = (uint32_t)(lt >> 1);
+        const bool ready = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag);
+        if (named_bar_any(1, 128, !ready)) {
+            record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+            return;
+        }
+        tc_fence_after();
+        const int row = mt * kBM + rl;
+        const bool valid = row < p.rows_valid;
+        const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)buf * kAccStride;
+        float ss = 0.f;
+        for (int ch = 0; ch < p.bn / 32; ++ch, ++q) {
+            const uint32_t sbuf = q & 1u, sphase = (q >> 1) & 1u;
+            uint8_t *sb = ystage + sbuf * kYStageBytes;
+            uint32_t r[32];
+            tmem_ld_32x32b_x32(taddr + (uint32_t)(ch * 32), r);
+            tc_wait_ld();
+            if (rank != 0) {
+                // stage this rank's partial chunk once rank 0 has consumed the buffer's previous chunk
+                if (q >= 2) {
+                    const bool fr = mbar_wait_cluster_bounded(&chunk_free[sbuf], sphase ^ 1u, abort_flag);
+                    if (named_bar_any(1, 128, !fr)) {
+                        record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                        return;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    *reinterpret_cast<float4 *>(sb + rl * 128 + ((j ^ (rl & 7)) * 16)) =
+                        make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                    __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                named_bar_sync(1, 128);
+                if (threadIdx.x == 64) mbar_arrive_cluster(mapa_shared(smem_u32(&chunk_ready[sbuf]), 0));
+                continue;
+            }
+            // rank 0: add the other ranks' partial chunks in rank order
+            if (S > 1) {
+                const bool rd = mbar_wait_cluster_bounded(&chunk_ready[sbuf], sphase, abort_flag);
+                if (named_bar_any(1, 128, !rd)) {
+                    record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                    return;
+                }
+                for (uint32_t j = 1; j < S; ++j) {
+                    const uint32_t base = mapa_shared(ystage_addr + sbuf * kYStageBytes, j);
+#pragma unroll
+                    for (int g = 0; g < 8; ++g) {
+                        const float4 v = ld_shared_cluster_v4(base + (uint32_t)(rl * 128 + ((g ^ (rl & 7)) * 16)));
+                        r[4 * g] = __float_as_uint(__uint_as_float(r[4 * g]) + v.x);
+                        r[4 * g + 1] = __float_as_uint(__uint_as_float(r[4 * g + 1]) + v.y);
+                        r[4 * g + 2] = __float_as_uint(__uint_as_float(r[4 * g + 2]) + v.z);
+                        r[4 * g + 3] = __float_as_uint(__uint_as_float(r[4 * g + 3]) + v.w);
+                    }
+                }
+                named_bar_sync(1, 128);  // every row's remote reads of this buffer are done
+                if (threadIdx.x == 64)
+                    for (uint32_t j = 1; j < S; ++j) mbar_arrive_cluster(mapa_shared(smem_u32(&chunk_free[sbuf]), j));
+            }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float v = __uint_as_float(r[j]);
+                ss = fmaf(v, v, ss);
+            }
+            // stage the summed chunk in this CTA's buffer and store it with TMA (as the two-pass epilogue)
+            if (threadIdx.x == 64) bulk_wait_read_1();
+            named_bar_sync(1, 128);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<float4 *>(sb + rl * 128 + ((j ^ (rl & 7)) * 16)) =
+                    make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+            fence_proxy_async_smem();
+            named_bar_sync(1, 128);
+            if (threadIdx.x == 64) {
+                tma_store_2d(tmY, sb, nt * p.bn + ch * 32, mt * kBM);
+                bulk_commit();
+            }
+        }
+        tc_fence_before();
+        mbar_arrive(&tempty[buf]);
+        if (rank == 0 && valid) p.P[(int64_t)row * p.ldP + nt] = ss;
+    }
+    if (rank == 0 && threadIdx.x == 64) bulk_wait_all();
+}
+
 template <int kMode, bool kFp8>
 __global__ void __launch_bounds__(kMode == kFusedCta ? kThreadsFused : kThreads, 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
@@ -324,6 +447,11 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                    const TcParams p) {
     constexpr bool kFused = kMode == kFusedCta;
     constexpr bool kCluster = kMode == kClusterFused;
+    constexpr bool kSplit = kMode == kSplitK;
+    // split-K: this CTA's share of the k-blocks
+    const int kb_lo = kSplit ? (int)(cluster_ctarank() * (uint32_t)p.num_k_blocks / (uint32_t)p.ksplit) : 0;
+    const int kb_hi = kSplit ? (int)((cluster_ctarank() + 1) * (uint32_t)p.num_k_blocks / (uint32_t)p.ksplit)
+                             : p.num_k_blocks;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
@@ -369,6 +497,12 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                 mbar_init(&pfree[b], csize);
             }
         }
+        if (kSplit) {  // pready: a chunk staged by every other rank (rank 0); pfree: buffer consumed (ranks > 0)
+            for (int b = 0; b < 2; ++b) {
+                mbar_init(&pready[b], p.ksplit > 1 ? (uint32_t)(p.ksplit - 1) : 1u);
+                mbar_init(&pfree[b], 1);
+            }
+        }
         *abort_flag = 0;
         fence_mbar_init();
     }
@@ -385,8 +519,8 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     }
     tc_fence_before();
     __syncthreads();
-    // cluster variant: every CTA's barriers are initialised before any remote arrive
-    if (kCluster) cluster_sync_all();
+    // cluster variants: every CTA's barriers are initialised before any remote arrive
+    if (kCluster || kSplit) cluster_sync_all();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
@@ -402,7 +536,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             for (int i = 0; !failed && tile_of<kMode>(p, i, mt, nt); ++i) {
                 const int y_a = p.row0 + mt * kBM;
                 const int y_b = nt * p.bn;
-                for (int kb = 0; kb < p.num_k_blocks; ++kb) {
+                for (int kb = kb_lo; kb < kb_hi; ++kb) {
                     if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag)) {
                         record_error(p.err, abort_flag, kDevTimeoutProducer);
                         failed = true;
@@ -450,7 +584,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)buf * kAccStride;
-                for (int kb = 0; kb < p.num_k_blocks; ++kb) {
+                for (int kb = kb_lo; kb < kb_hi; ++kb) {
                     if (!mbar_wait_bounded(&full[stage], phase, abort_flag)) {
                         record_error(p.err, abort_flag, kDevTimeoutMma);
                         failed = true;
@@ -470,12 +604,11 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                         for (int k16 = 0; k16 < kBK / 16; ++k16) {
                             // +32 bytes along K inside the swizzle row = +2 in the address field
                             // (16 BF16 or 32 FP8 elements per MMA)
+                            const uint32_t acc = ((kb - kb_lo) | q | k16) != 0 ? 1u : 0u;
                             if (kFp8)
-                                tc_mma_f8(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), p.idesc,
-                                          (kb | q | k16) != 0 ? 1u : 0u);
+                                tc_mma_f8(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), p.idesc, acc);
                             else
-                                tc_mma_bf16(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), p.idesc,
-                                            (kb | q | k16) != 0 ? 1u : 0u);
+                                tc_mma_bf16(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), p.idesc, acc);
                         }
                     }
                     issued = true;
@@ -498,6 +631,9 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     } else if (kCluster && warp < 6) {
         // ---------------- cluster epilogue: warps 2..5 ----------------
         cluster_epilogue(p, tmem_base, tfull, tempty, pready, pfree, part, abort_flag, warp, lane);
+    } else if (kSplit && warp < 6) {
+        // ---------------- split-K epilogue: warps 2..5 ----------------
+        splitk_epilogue(p, &tmY, tmem_base, tfull, tempty, pready, pfree, ystage, abort_flag, warp, lane);
     } else if (warp < 6) {
         // ---------------- epilogue: warps 2..5 ----------------
         const int quad = warp & 3;  // tensor-memory lane quarter this warp may access
@@ -626,8 +762,8 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
 
     tc_fence_before();
     __syncthreads();
-    // cluster variant: no CTA leaves while another may still read its partial sums or arrive on its barriers
-    if (kCluster) cluster_sync_all();
+    // cluster variants: no CTA leaves while another may still read its shared memory or arrive on its barriers
+    if (kCluster || kSplit) cluster_sync_all();
     if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kTmemCols);
@@ -690,6 +826,8 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     p.ldP = o.ldP;
     p.rows_valid = o.rows_valid;
     p.err = d_err;
+    p.cl_T = 1;
+    p.ksplit = 1;
     if (fused) {
         p.m = *fused;
     } else {
@@ -832,6 +970,7 @@ cudaError_t launch_contract_tc_cluster(const TcArgs &a, const SiteLayout &L, int
     p.rows_valid = rows_valid;
     p.err = d_err;
     p.cl_T = T;
+    p.ksplit = 1;
     p.m = m;
     if (p.num_m_tiles <= 0) return cudaSuccess;
     (void)smem;
@@ -845,6 +984,75 @@ cudaError_t launch_contract_tc_cluster(const TcArgs &a, const SiteLayout &L, int
     const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
     const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
     e = cudaLaunchKernelEx(&cfg, kern, a.tmA[0], a1, a2, a.tmB[0], b1, a.tmA[0], p);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_tc_splitk(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int ksplit,
+                                      int *d_err, cudaStream_t st, int *clusters_out) {
+    if (a.fp8 || !a.has_tmY || ksplit < 2 || ksplit > 8) return cudaErrorInvalidValue;
+    if (a.nprod < 1 || a.nprod > kMaxProducts || a.a_planes < 1 || a.a_planes > 3 || a.b_planes < 1 ||
+        a.b_planes > 2)
+        return cudaErrorInvalidValue;
+    TcParams p;
+    p.num_m_tiles = a.rows_pad / kBM;
+    p.num_n_tiles = L.ncols / L.bn;
+    p.num_k_blocks = L.K_pad / L.bk;
+    if (p.num_k_blocks < ksplit) return cudaErrorInvalidValue;
+    p.bn = L.bn;
+    p.a_planes = a.a_planes;
+    p.b_planes = a.b_planes;
+    p.nprod = a.nprod;
+    p.prod_code = 0;
+    for (int q = 0; q < a.nprod; ++q) {
+        if (a.prod_a[q] < 0 || a.prod_a[q] >= a.a_planes || a.prod_b[q] < 0 || a.prod_b[q] >= a.b_planes)
+            return cudaErrorInvalidValue;
+        p.prod_code |= ((uint32_t)a.prod_a[q] | ((uint32_t)a.prod_b[q] << 2)) << (4 * q);
+    }
+    p.b_plane_bytes = (uint32_t)L.bn * 128;
+    p.stage_bytes = (uint32_t)a.a_planes * kATileBytes + (uint32_t)a.b_planes * p.b_plane_bytes;
+    p.stages = stages_for(p.stage_bytes, 2 * kYStageBytes + kClusterBytes);
+    if (p.stages < 2) return cudaErrorInvalidConfiguration;
+    p.tma_store = 1;
+    p.row0 = (int)a.row0;
+    p.idesc = idesc_bf16_f32(kBM, L.bn);
+    p.Y = o.Y;
+    p.ldY = o.ldY;
+    p.P = o.P;
+    p.ldP = o.ldP;
+    p.rows_valid = o.rows_valid;
+    p.err = d_err;
+    p.cl_T = 1;
+    p.ksplit = ksplit;
+    p.m = MeasureArgs{};
+    const int tiles = p.num_m_tiles * p.num_n_tiles;
+    if (tiles <= 0) return cudaSuccess;
+    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kBarrierBytes + 2 * kYStageBytes + kClusterBytes;
+    auto kern = tc_contract_kernel<kSplitK, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ksplit;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)ksplit);
+    int ncl_max = 0;
+    e = cudaOccupancyMaxActiveClusters(&ncl_max, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (ncl_max <= 0) return cudaErrorInvalidConfiguration;
+    const int ncl = tiles < ncl_max ? tiles : ncl_max;
+    if (clusters_out) *clusters_out = ncl;
+    cfg.gridDim = dim3((unsigned)(ncl * ksplit));
+    cfg.stream = st;
+    const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
+    const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
+    e = cudaLaunchKernelEx(&cfg, kern, a.tmA[0], a1, a2, a.tmB[0], b1, a.tmY, p);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

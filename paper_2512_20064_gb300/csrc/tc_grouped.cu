@@ -79,9 +79,18 @@ struct PParams {
     int *err;
 };
 
-// Last segment whose first task is <= t (segments ordered by task_begin).
-__device__ __forceinline__ int psegment_of(const PParams &p, int64_t t) {
-    int lo = 0, hi = p.nseg - 1;
+// Last segment whose first task is <= t (segments ordered by task_begin).  A block takes tasks in
+// increasing order, so the search gallops forward from the block's previous segment `from`.
+__device__ __forceinline__ int psegment_of(const PParams &p, int64_t t, int from) {
+    int lo = from, hi = from, step = 1;
+    while (hi + 1 < p.nseg && p.segs[hi + 1].task_begin <= t) {
+        lo = hi + 1;
+        hi = hi + step < p.nseg - 1 ? hi + step : p.nseg - 1;
+        step <<= 1;
+        if (p.segs[hi].task_begin > t) break;
+        lo = hi;
+    }
+    if (p.segs[hi].task_begin <= t) return hi;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (p.segs[mid].task_begin <= t) lo = mid;
@@ -171,6 +180,7 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_batch_persistent_kernel(const
             int last_parity[kMaxStages];
             for (int s = 0; s < kMaxStages; ++s) last_parity[s] = -1;
             bool failed = false;
+            int seg_cursor = 0;
             for (int64_t seq = 0; !failed; ++seq) {
                 const int slot = (int)(seq % kTaskRing);
                 const uint32_t tpar = (uint32_t)((seq / kTaskRing) & 1);
@@ -184,7 +194,8 @@ __global__ void __launch_bounds__(kPThreads, 1) tc_batch_persistent_kernel(const
                     mbar_arrive(&task_full[slot]);
                     break;
                 }
-                const int si = psegment_of(p, t);
+                const int si = psegment_of(p, t, seg_cursor);
+                seg_cursor = si;
                 const PSegment *sg = &p.segs[si];
                 const int64_t lt = t - sg->task_begin;
                 const int mt = (int)(lt / sg->num_n_tiles);

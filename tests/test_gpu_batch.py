@@ -93,8 +93,9 @@ def test_batch_rejects_mismatched_precision():
 
 
 def test_autotuner_picks_a_width_caches_it_and_stays_correct(tmp_path, monkeypatch):
-    """autotune=1 times the candidate n-tile widths per site shape, records the choice in the JSON cache
-    file, and the sampler stays within tolerance of the oracle with the chosen layout."""
+    """autotune=1 times the candidate n-tile widths and measurement modes (two-pass, single-pass cluster)
+    per site shape, records the choice (bn + 10000 * mode) in the JSON cache file, and the sampler stays
+    within tolerance of the oracle with the chosen layout and mode."""
     import json
 
     import paper_2512_20064_gb300 as F
@@ -106,7 +107,8 @@ def test_autotuner_picks_a_width_caches_it_and_stays_correct(tmp_path, monkeypat
         s.load_chain(ts)
         smp, lp, tr = s.sample(b, 4, 4096, 5, trace_rows=64)
     table = json.loads(cache.read_text())
-    assert "1:256:4:256" in table and table["1:256:4:256"] in (64, 128, 256)
+    code = table["1:256:4:256"]
+    assert code % 10000 in (64, 128, 256) and code // 10000 in (0, 2)
     print("tuned widths", table)
     rep = parity.check(b, [quant.dequant_bf16(A, 1) for A in ts], 5, np.arange(64), smp[:64], lp[:64], 1e-4,
                        dev_trace=tr, trace_rows=64)

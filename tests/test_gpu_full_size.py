@@ -107,4 +107,4 @@ def test_precision_workload_1024_rows(precision_chain, precision):
         summary["storage_error_max"] = float(storage.max())
         summary["storage_error_last_64"] = float(storage[:, -64:].max())
         summary["device_vs_original_max"] = float(total.max())
-    print(f"\nPRECISION_PARITY {precision} N={N} rows={rows.size} {summary}")
+    print(f"\nPRECISION_PARITY {precision} N={N} rows={rows.size} {summary}", flush=True)
