@@ -96,3 +96,45 @@ def dequant_e4m3(A) -> np.ndarray:
     re = np.asarray(A.real, dtype=np.float32).astype(np.float64)
     im = np.asarray(A.imag, dtype=np.float32).astype(np.float64)
     return (e4m3_round(re * s) + 1j * e4m3_round(im * s)) / s
+
+
+# ---------------------------------------------------------------------------
+# FP16 (IEEE-754 binary16: 11 significant bits, 5 exponent bits with bias 15,
+# largest finite 65504, subnormals down to 2^-24), round to nearest, ties to
+# even; stored with a per-site power-of-two scale.
+# ---------------------------------------------------------------------------
+
+FP16_TOP = 32768.0
+
+
+def fp16_round(x) -> np.ndarray:
+    """Round float32 values to the nearest binary16 value (ties to even), returned as float64.
+
+    Restated from the format with integer arithmetic on the float32 bit patterns (finite inputs
+    whose magnitude stays below 65520, so that nothing rounds to infinity)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    a = np.abs(x).astype(np.float64)
+    _, ex = np.frexp(a)                      # a = m * 2^ex, m in [0.5, 1)
+    e = np.maximum(ex - 1, -14)              # exponent of the leading bit; -14 for subnormals
+    q = np.ldexp(1.0, (e - 10).astype(np.int64))  # spacing of representable values at that exponent
+    r = np.round(a / q) * q                  # a / q is exact in float64; numpy rounds halves to even
+    r[a == 0] = 0.0
+    return np.copysign(r, x.astype(np.float64))
+
+
+def fp16_site_scale(A) -> float:
+    """Power-of-two scale of an FP16 site store: the largest 2^j with max|Re, Im| * 2^j <= 32768."""
+    A = np.asarray(A)
+    m = float(max(np.abs(np.asarray(A.real, np.float32)).max(), np.abs(np.asarray(A.imag, np.float32)).max()))
+    if m == 0.0:
+        return 1.0
+    return float(2.0 ** np.floor(np.log2(FP16_TOP / m)))
+
+
+def dequant_fp16(A) -> np.ndarray:
+    """The complex128 tensor an FP16 store with a per-site power-of-two scale represents."""
+    s = fp16_site_scale(A)
+    re = np.asarray(A.real, dtype=np.float32) * np.float32(s)
+    im = np.asarray(A.imag, dtype=np.float32) * np.float32(s)
+    return (fp16_round(re) + 1j * fp16_round(im)) / s
+

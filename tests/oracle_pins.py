@@ -613,5 +613,65 @@ def pin_dequant_e4m3(Q, seed=6):
     return True, ""
 
 
+def pin_fp16_hand_cases(Q):
+    """binary16: spacing 2^-10 in [1, 2), ties to even of both parities, the subnormal grid 2^-24, the
+    2^-14 boundary, the largest finite value."""
+    cases = [
+        (1.0, 1.0), (1.0 + 2.0 ** -11, 1.0), (1.0 + 3 * 2.0 ** -11, 1.0 + 2.0 ** -9),
+        (1.0 + 2.0 ** -11 + 2.0 ** -20, 1.0 + 2.0 ** -10), (2.0 - 2.0 ** -11, 2.0),
+        (2.0 ** -25, 0.0), (3 * 2.0 ** -25, 2.0 ** -23), (5 * 2.0 ** -26, 2.0 ** -24),
+        (2.0 ** -14 + 2.0 ** -25, 2.0 ** -14), (2.0 ** -14 + 3 * 2.0 ** -25, 2.0 ** -14 + 2.0 ** -23),
+        (65504.0, 65504.0), (65504.0 + 15.0, 65504.0), (-(1.0 + 3 * 2.0 ** -11), -(1.0 + 2.0 ** -9)),
+        (32768.0 + 16.0, 32768.0), (32768.0 + 48.0, 32768.0 + 64.0),
+    ]
+    x = np.asarray([c[0] for c in cases], np.float32)
+    want = np.asarray([c[1] for c in cases], np.float64)
+    got = Q.fp16_round(x)
+    if not np.array_equal(got, want):
+        bad = [(float(a), g, w) for a, g, w in zip(x, got, want) if g != w]
+        return False, f"fp16_round hand cases differ: {bad[:4]}"
+    return True, ""
+
+
+def pin_fp16_vs_torch(Q, n=200000, seed=7):
+    """fp16_round equals torch's float32 -> float16 cast on random magnitudes over the whole finite range,
+    subnormals included, and on every half-spacing tie of a dense grid."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal(n) * 2.0 ** rng.integers(-30, 16, size=n)).astype(np.float32)
+    x = x[np.abs(x) < 65504.0]
+    grid = (np.arange(-40000, 40001) * 2.0 ** -14).astype(np.float32)
+    for arr in (x, grid):
+        want = torch.from_numpy(arr.copy()).to(torch.float16).double().numpy()
+        if not np.array_equal(Q.fp16_round(arr), want):
+            return False, "fp16_round differs from torch's float16 cast"
+    return True, ""
+
+
+def pin_fp16_site_scale_and_dequant(Q, seed=8):
+    """The FP16 site scale is the power of two putting max|Re, Im| in [16384, 32768]; dequant_fp16 is
+    fp16(x * scale) / scale per part and is idempotent."""
+    rng = np.random.default_rng(seed)
+    for m in (1.0, 0.7, 3e-3, 32768.0, 16384.0, 20000.0):
+        A = rng.standard_normal((4, 2, 4)) + 1j * rng.standard_normal((4, 2, 4))
+        A *= m / max(np.abs(A.real).max(), np.abs(A.imag).max())
+        sc = Q.fp16_site_scale(A)
+        mx = float(max(np.abs(A.real.astype(np.float32)).max(), np.abs(A.imag.astype(np.float32)).max()))
+        if math.log2(sc) != round(math.log2(sc)) or not 16384.0 <= mx * sc <= 32768.0:
+            return False, f"scale {sc} for max {mx}"
+        D = Q.dequant_fp16(A)
+        re = A.real.astype(np.float32).astype(np.float64)
+        if not np.array_equal(D.real, Q.fp16_round((re * sc).astype(np.float32)) / sc):
+            return False, "dequant_fp16 is not the scaled rounding"
+        if not np.array_equal(Q.dequant_fp16(D), D):
+            return False, "dequant_fp16 is not idempotent"
+        rel = np.abs(D.real - re) / np.abs(re)
+        if rel[np.abs(re) * sc >= 2.0 ** -14].max() > 2.0 ** -11 * (1 + 1e-12):
+            return False, "relative error above half an 11-bit ulp among normals"
+    return True, ""
+
+
 QUANT_PINS = [pin_bf16_hand_cases, pin_bf16_vs_torch, pin_bf16_split, pin_dequant_bf16, pin_e4m3_hand_cases,
-              pin_e4m3_vs_torch, pin_e4m3_site_scale, pin_dequant_e4m3]
+              pin_e4m3_vs_torch, pin_e4m3_site_scale, pin_dequant_e4m3, pin_fp16_hand_cases, pin_fp16_vs_torch,
+              pin_fp16_site_scale_and_dequant]

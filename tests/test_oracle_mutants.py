@@ -118,14 +118,24 @@ QUANT_MUTANTS = {
     "e4m3_no_saturation": ("    r = np.minimum(r, E4M3_MAX)", "    r = r"),
     "e4m3_subnormal_floor_off_by_one": ("    e = np.maximum(ex - 1, -6)", "    e = np.maximum(ex - 1, -7)"),
     "e4m3_four_mantissa_bits": ("    q = np.ldexp(1.0, (e - 3).astype(np.int64))", "    q = np.ldexp(1.0, (e - 4).astype(np.int64))"),
-    "e4m3_ties_away_from_zero": ("    r = np.round(a / q) * q", "    r = np.floor(a / q + 0.5) * q"),
-    "e4m3_truncates": ("    r = np.round(a / q) * q", "    r = np.floor(a / q) * q"),
+    "e4m3_ties_away_from_zero": ("    r = np.round(a / q) * q                  # numpy rounds halves to even",
+                                 "    r = np.floor(a / q + 0.5) * q"),
+    "e4m3_truncates": ("    r = np.round(a / q) * q                  # numpy rounds halves to even",
+                       "    r = np.floor(a / q) * q"),
     "e4m3_scale_ceil": ("    return float(2.0 ** np.floor(np.log2(E4M3_MAX / m)))",
                         "    return float(2.0 ** np.ceil(np.log2(E4M3_MAX / m)))"),
     "e4m3_scale_one_too_small": ("    return float(2.0 ** np.floor(np.log2(E4M3_MAX / m)))",
                                  "    return float(2.0 ** (np.floor(np.log2(E4M3_MAX / m)) - 1))"),
     "dequant_e4m3_not_unscaled": ("    return (e4m3_round(re * s) + 1j * e4m3_round(im * s)) / s",
                                   "    return (e4m3_round(re * s) + 1j * e4m3_round(im * s))"),
+    "fp16_ten_mantissa_bits": ("    q = np.ldexp(1.0, (e - 10).astype(np.int64))", "    q = np.ldexp(1.0, (e - 9).astype(np.int64))"),
+    "fp16_subnormal_floor": ("    e = np.maximum(ex - 1, -14)", "    e = np.maximum(ex - 1, -15)"),
+    "fp16_ties_away": ("    r = np.round(a / q) * q                  # a / q is exact",
+                       "    r = np.floor(a / q + 0.5) * q            # a / q is exact"),
+    "fp16_scale_too_large": ("    return float(2.0 ** np.floor(np.log2(FP16_TOP / m)))",
+                             "    return float(2.0 ** np.ceil(np.log2(FP16_TOP / m)))"),
+    "dequant_fp16_imag_unscaled": ("    im = np.asarray(A.imag, dtype=np.float32) * np.float32(s)",
+                                   "    im = np.asarray(A.imag, dtype=np.float32)"),
 }
 
 
