@@ -68,6 +68,14 @@ extern "C" {
 /* Experiment: as FP8X1, with the left row split into two E4M3 residual planes at the same per-row
  * scale (V = V0 + V1, V1 = e4m3(v 2^r - V0)); two kind::f8f6f4 products V0 B + V1 B. */
 #define FASTMPS_FP8X2 6
+/* V0 B0 + V1 B0 with FP16 (binary16) operands: B = fp16(A * 2^a) with a per-site power of two putting
+ * max |Re|,|Im| in [16384, 32768] (11 significant bits against BF16's 8; Sec. 3.3.2 keeps the tensors
+ * in a 16-bit format), each left row as two FP16 residual planes of v * 2^r with a per-row power of
+ * two putting its largest entry in [16384, 32768] (22 significant bits against BF16x2's 16).  Both
+ * scales cancel in w / Z.  Same tensor-core rate as BF16x2.  Resident or host-streamed tensors;
+ * fastmps_sample, fastmps_sample_ex and fastmps_sample_traced only (not batched, displaced or
+ * allocation-free sampling). */
+#define FASTMPS_FP16X2 7
 
 /* Where site tensors live between uses (Sec. 3.1: I/O overlapped by a double buffer). */
 #define FASTMPS_RESIDENT_HBM 0    /* repacked once at load time, kept in device memory */
@@ -100,6 +108,12 @@ typedef struct fastmps_options {
                                summing its share of the contraction index, partial tiles added
                                through distributed shared memory (the paper's single- vs
                                double-site split of Sec. 3.2, inside one GPU; an experiment). */
+    int accum_chunk;        /* tensor-core modes, separate measurement: 0 = each output accumulated
+                               over the whole contraction index in one tensor-memory accumulator;
+                               c > 0 = n-tiles of 128 columns whose index is accumulated c k-blocks
+                               (64 entries each) at a time into fresh accumulators, the chunk sums
+                               added in FP32 registers with round-to-nearest (the tensor cores'
+                               own accumulation then only spans short partial sums). */
 } fastmps_options;
 
 typedef struct fastmps_ctx *fastmps_handle;

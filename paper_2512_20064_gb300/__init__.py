@@ -32,7 +32,7 @@ __all__ = [
 OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "SHAPE", -3: "NOT_LOADED", -4: "OOM", -5: "CUDA", -6: "TIMEOUT",
              -7: "UNSUPPORTED", -8: "NUMERIC"}
-PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16x3": 2, "bf16x3l": 3, "bf16x4": 4, "fp8x1": 5, "fp8x2": 6}
+PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16x3": 2, "bf16x3l": 3, "bf16x4": 4, "fp8x1": 5, "fp8x2": 6, "fp16x2": 7}
 RESIDENCIES = {"hbm": 0, "host_stream": 1}
 MEASUREMENTS = {"separate": 0, "cta": 1, "cluster": 2}
 C64, C128 = 0, 1
@@ -41,7 +41,7 @@ C64, C128 = 0, 1
 class fastmps_options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("residency", ctypes.c_int), ("max_microbatch", ctypes.c_int64),
                 ("autotune", ctypes.c_int), ("stream", ctypes.c_void_p), ("fused_measure", ctypes.c_int),
-                ("k_split", ctypes.c_int)]
+                ("k_split", ctypes.c_int), ("accum_chunk", ctypes.c_int)]
 
 
 class fastmps_stats(ctypes.Structure):
@@ -406,7 +406,8 @@ class Sampler:
     """A handle of the library: load site tensors once, then sample many times."""
 
     def __init__(self, device: int = 0, precision: str = "fp32", residency: str = "hbm", max_microbatch: int = 0,
-                 stream=None, fused_measure=False, autotune: bool = False, k_split: int = 0):
+                 stream=None, fused_measure=False, autotune: bool = False, k_split: int = 0,
+                 accum_chunk: int = 0):
         """``fused_measure``: False / "separate" (measurement kernel after each contraction), True / "cta"
         (measurement warps inside the contraction kernel), "cluster" (single-pass cluster kernel, no
         scratch, where a site's row fits one cluster)."""
@@ -414,6 +415,7 @@ class Sampler:
         o.fused_measure = MEASUREMENTS[fused_measure] if isinstance(fused_measure, str) else int(bool(fused_measure))
         o.autotune = int(bool(autotune))
         o.k_split = int(k_split)
+        o.accum_chunk = int(accum_chunk)
         o.precision = PRECISIONS[precision]
         o.residency = RESIDENCIES[residency]
         o.max_microbatch = int(max_microbatch)

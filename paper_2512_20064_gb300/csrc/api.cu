@@ -117,7 +117,7 @@ struct Tensor {
     int measure_mode = 0;  // autotuned: 2 = single-pass cluster kernel for this site, 0 = two-pass
     // resident operands (device)
     DevBuf B_hi, B_lo, Bt, B8;
-    float fp8_scale = 1.f;  // FP8: stored value = e4m3(A * fp8_scale)
+    float fp8_scale = 1.f;  // FP8: stored value = e4m3(A * fp8_scale); FP16: fp16(A * fp8_scale)
     CUtensorMap tmB[2];
     // streamed operand (pinned host, compact BF16 [chi_l][d][chi_r] (re, im), hi block then lo block)
     DevBuf host_compact;
@@ -170,6 +170,7 @@ int cuda_fail(fastmps_handle h, cudaError_t e, const char *what) {
 // Tensor-core precision modes (BF16 split planes or FP8); FP32 is the SIMT path.
 bool is_bf16(const fastmps_handle h) { return h->opt.precision != FASTMPS_FP32; }
 bool is_fp8(const fastmps_handle h) { return h->opt.precision == FASTMPS_FP8X1 || h->opt.precision == FASTMPS_FP8X2; }
+bool is_f16(const fastmps_handle h) { return h->opt.precision == FASTMPS_FP16X2; }
 
 // Planes of the split-precision operands and the products accumulated per precision mode.
 struct PrecisionPlan {
@@ -185,6 +186,7 @@ PrecisionPlan plan_of(int precision) {
         case FASTMPS_BF16X4: return {3, 2, 4, {0, 1, 2, 0}, {0, 0, 0, 1}};
         case FASTMPS_FP8X1: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
         case FASTMPS_FP8X2: return {2, 1, 2, {0, 1, 0, 0}, {0, 0, 0, 0}};
+        case FASTMPS_FP16X2: return {2, 1, 2, {0, 1, 0, 0}, {0, 0, 0, 0}};
         default: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
     }
 }
@@ -232,6 +234,11 @@ bool encode_2d_f32_scratch(CUtensorMap *map, const void *base, uint64_t cols, ui
     return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, cols, rows, ld_elems, 32, 128);
 }
 
+bool encode_2d_f16(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
+                   uint32_t box_inner, uint32_t box_outer) {
+    return encode_2d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, inner, outer, ld_elems, box_inner, box_outer);
+}
+
 // FP8 operands: rows of ld_elems bytes, 128-byte (128-element) boxes along K
 bool encode_2d_u8(CUtensorMap *map, const void *base, uint64_t inner, uint64_t outer, uint64_t ld_elems,
                   uint32_t box_outer) {
@@ -246,6 +253,31 @@ inline uint16_t host_bf16_bits(float x) {
     u += 0x7FFFu + lsb;
     return (uint16_t)(u >> 16);
 }
+// Host float -> binary16 bits, round to nearest, ties to even (finite inputs below 65520 in
+// magnitude): 11 significant bits for normals (exponent >= -14), multiples of 2^-24 below.
+inline uint16_t host_f16_bits(float x) {
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    const uint32_t sign = (u >> 16) & 0x8000u;
+    const uint32_t a = u & 0x7FFFFFFFu;
+    if (a >= 0x477FF000u) return (uint16_t)(sign | 0x7C00u);  // 65520 and above round past 65504
+    if (a <= 0x33000000u) return (uint16_t)sign;              // at most 2^-25: zero (a tie goes to even 0)
+    const int e = (int)(a >> 23) - 127;
+    const uint32_t mant = (a & 0x7FFFFFu) | 0x800000u;        // 24 significant bits
+    const uint32_t shift = e >= -14 ? 13u : (uint32_t)(13 + (-14 - e));
+    if (shift > 24) return (uint16_t)sign;
+    const uint32_t rem = mant & ((1u << shift) - 1u), half = 1u << (shift - 1u);
+    uint32_t m = mant >> shift;
+    if (rem > half || (rem == half && (m & 1u))) m += 1u;
+    if (e < -14) return (uint16_t)(sign | m);                  // subnormal (m = 0x400 is the least normal)
+    uint32_t he = (uint32_t)(e + 15);
+    if (m == 0x800u) {                                         // carry into the exponent
+        m = 0x400u;
+        he += 1u;
+    }
+    return (uint16_t)(sign | (he << 10) | (m & 0x3FFu));
+}
+
 inline float host_bf16_float(uint16_t b) {
     uint32_t u = (uint32_t)b << 16;
     float f;
@@ -441,7 +473,8 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
     const size_t lam_bytes = (size_t)chi_r * (dtype == FASTMPS_C128 ? 8 : 4);
     t.L = make_layout(h->opt.precision, chi_l, d, chi_r);
     const int64_t nelem = (int64_t)chi_l * d * chi_r;
-    const bool tune = h->opt.autotune && is_bf16(h) && !is_fp8(h) && h->opt.residency == FASTMPS_RESIDENT_HBM;
+    const bool tune = h->opt.autotune && is_bf16(h) && !is_fp8(h) && !is_f16(h) && h->opt.accum_chunk == 0 &&
+                      h->opt.residency == FASTMPS_RESIDENT_HBM;
     const size_t src_bytes = (size_t)nelem * (dtype == FASTMPS_C128 ? 16 : 8);
     cudaError_t e;
     const bool a_on_device = is_device_ptr(A);
@@ -467,16 +500,26 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
             return fail(h, FASTMPS_ERR_OOM, "pinned host allocation for a streamed tensor failed");
         uint16_t *dst = t.host_compact.as<uint16_t>();
         const int64_t n2 = nelem * 2;
-        for (int64_t i = 0; i < n2; ++i) {
-            float x;
+        auto value = [&](int64_t i) -> float {
             if (dtype == FASTMPS_C128) {
                 double v = static_cast<const double *>(A)[i];
                 if (lam) v *= reinterpret_cast<const double *>(lam_host.data())[(i >> 1) % chi_r];
-                x = (float)v;
-            } else {
-                x = static_cast<const float *>(A)[i];
-                if (lam) x *= reinterpret_cast<const float *>(lam_host.data())[(i >> 1) % chi_r];
+                return (float)v;
             }
+            float x = static_cast<const float *>(A)[i];
+            if (lam) x *= reinterpret_cast<const float *>(lam_host.data())[(i >> 1) % chi_r];
+            return x;
+        };
+        if (is_f16(h)) {
+            // binary16 at the per-site power-of-two scale that puts the largest |Re|, |Im| in [16384, 32768]
+            float amax = 0.f;
+            for (int64_t i = 0; i < n2; ++i) amax = std::max(amax, std::fabs(value(i)));
+            t.fp8_scale = amax > 0.f ? (float)std::exp2(std::floor(std::log2(32768.0 / (double)amax))) : 1.f;
+            for (int64_t i = 0; i < n2; ++i) dst[i] = host_f16_bits(value(i) * t.fp8_scale);
+            return FASTMPS_OK;
+        }
+        for (int64_t i = 0; i < n2; ++i) {
+            const float x = value(i);
             uint16_t hb = host_bf16_bits(x);
             dst[i] = hb;
             if (t.planes > 1) dst[n2 + i] = host_bf16_bits(x - host_bf16_float(hb));
@@ -506,6 +549,19 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
         t.fp8_scale = amax > 0.f ? (float)std::exp2(std::floor(std::log2(448.0 / (double)amax))) : 1.f;
         launch_repack_e4m3(h->staging.p, dtype == FASTMPS_C128, t.L, t.fp8_scale, t.B8.as<uint8_t>(), h->stream);
         if (!encode_2d_u8(&t.tmB[0], t.B8.p, t.L.K_pad, t.L.ncols, t.L.K_pad, t.L.bn))
+            return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
+        t.tmB[1] = t.tmB[0];
+    } else if (is_f16(h)) {
+        // per-site power-of-two scale that puts the largest |Re|, |Im| in [16384, 32768]
+        if (!t.B_hi.ensure(op_elems * 2) || !h->err.ensure(256)) return fail(h, FASTMPS_ERR_OOM, "allocation failed");
+        float amax = 0.f;
+        launch_absmax(h->staging.p, dtype == FASTMPS_C128, nelem, h->err.as<float>(), h->stream);
+        e = cudaMemcpyAsync(&amax, h->err.p, sizeof(float), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "site tensor maximum");
+        t.fp8_scale = amax > 0.f ? (float)std::exp2(std::floor(std::log2(32768.0 / (double)amax))) : 1.f;
+        launch_repack_f16(h->staging.p, dtype == FASTMPS_C128, t.L, t.fp8_scale, t.B_hi.as<uint16_t>(), h->stream);
+        if (!encode_2d_f16(&t.tmB[0], t.B_hi.p, t.L.K_pad, t.L.ncols, t.L.K_pad, 64, t.L.bn))
             return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
         t.tmB[1] = t.tmB[0];
     } else if (is_bf16(h)) {
@@ -611,7 +667,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
         return fail(h, FASTMPS_ERR_INVALID_ARG, "trace_rows > 0 needs trace_probs");
     std::vector<Tensor *> ts(M);
     std::vector<char> on_cluster(M, 0);  // single-pass cluster contraction + measurement at site k
-    const bool want_cluster = h->opt.fused_measure == 2 && is_bf16(h) && !is_fp8(h) && !mu_dev;
+    const bool want_cluster = h->opt.fused_measure == 2 && is_bf16(h) && !is_fp8(h) && !is_f16(h) && !mu_dev;
     int ldV = 64;
     int ncols_max = 0, ldP_max = 0;
     double flops = 0;
@@ -746,7 +802,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
     if (fp8) {
         launch_init_left_e4m3(h->V[0][0].as<uint8_t>(), N_pad, ldV, st);
         if (planes > 1) cudaMemsetAsync(h->V[0][1].p, 0, (size_t)N_pad * ldV, st);  // residual plane of [1]
-    } else if (bf16)
+    } else if (is_f16(h))
+        launch_init_left_f16(h->V[0][0].as<uint16_t>(), h->V[0][1].as<uint16_t>(), N_pad, ldV, st);
+    else if (bf16)
         launch_init_left_bf16(Vp[0], planes, N_pad, ldV, st);
     else
         launch_init_left_f32(h->V[0][0].as<float>(), N_pad, ldV, st);
@@ -809,8 +867,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 cudaEventRecord(h->slot_free[cur], st);
                 Bh = h->slot_hi.as<__nv_bfloat16>();
                 Bl = lo;
-                if (!encode_2d_bf16(&ta.tmB[0], Bh, L.K_pad, L.ncols, L.K_pad, 64, L.bn) ||
-                    (Bl && !encode_2d_bf16(&ta.tmB[1], Bl, L.K_pad, L.ncols, L.K_pad, 64, L.bn)))
+                const bool mapped = is_f16(h) ? encode_2d_f16(&ta.tmB[0], Bh, L.K_pad, L.ncols, L.K_pad, 64, L.bn)
+                                              : encode_2d_bf16(&ta.tmB[0], Bh, L.K_pad, L.ncols, L.K_pad, 64, L.bn);
+                if (!mapped || (Bl && !encode_2d_bf16(&ta.tmB[1], Bl, L.K_pad, L.ncols, L.K_pad, 64, L.bn)))
                     return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
                 if (!Bl) ta.tmB[1] = ta.tmB[0];
             } else {
@@ -825,10 +884,12 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 ta.prod_b[q] = plan.pb[q];
             }
             ta.fp8 = fp8;
+            ta.f16 = is_f16(h);
             for (int p = 0; p < 3; ++p) {
                 const int src = p < plan.a_planes ? p : 0;
                 const bool ok = fp8 ? encode_2d_u8(&ta.tmA[p], h->V[cur][src].p, L.K_pad, N_pad, ldV, 128)
-                                    : encode_2d_bf16(&ta.tmA[p], h->V[cur][src].p, L.K_pad, N_pad, ldV, 64, 128);
+                                : ta.f16 ? encode_2d_f16(&ta.tmA[p], h->V[cur][src].p, L.K_pad, N_pad, ldV, 64, 128)
+                                         : encode_2d_bf16(&ta.tmA[p], h->V[cur][src].p, L.K_pad, N_pad, ldV, 64, 128);
                 if (!ok) return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
             }
         }
@@ -905,6 +966,7 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
             ma.V32 = bf16 ? nullptr : h->V[nxt][0].as<float>();
             for (int p = 0; p < 3; ++p) ma.Vp[p] = fp8 ? nullptr : Vp[nxt][p];
             ma.nplanes = planes;
+            ma.f16 = is_f16(h) ? 1 : 0;
             ma.V8 = fp8 ? h->V[nxt][0].as<uint8_t>() : nullptr;
             ma.V8lo = (fp8 && planes > 1) ? h->V[nxt][1].as<uint8_t>() : nullptr;
             ma.outcomes = h->O.as<uint8_t>() + (int64_t)k * N_pad + r0;
@@ -923,7 +985,9 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 ta.row0 = r0;
                 ta.rows_pad = (int)rows_pad;
                 ta.has_tmY = !fused && encode_2d_f32_scratch(&ta.tmY, co.Y, L.ncols, rows, L.ncols);
-                if (h->opt.k_split >= 2 && ta.has_tmY && !fp8 && L.K_pad / L.bk >= h->opt.k_split)
+                if (h->opt.accum_chunk > 0 && ta.has_tmY && !fp8 && L.bn == 256)
+                    e = launch_contract_tc_promoted(ta, L, co, h->opt.accum_chunk, h->num_sms, d_err, st);
+                else if (h->opt.k_split >= 2 && ta.has_tmY && !fp8 && L.K_pad / L.bk >= h->opt.k_split)
                     e = launch_contract_tc_splitk(ta, L, co, h->opt.k_split, d_err, st);
                 else
                     e = launch_contract_tc(ta, L, co, h->num_sms, d_err, st, fused ? &ma : nullptr);
@@ -1007,6 +1071,7 @@ void fastmps_default_options(fastmps_options *opt) {
     opt->stream = nullptr;
     opt->fused_measure = 0;
     opt->k_split = 0;
+    opt->accum_chunk = 0;
 }
 
 int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) {
@@ -1018,8 +1083,12 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
     fastmps_options o;
     fastmps_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_FP8X2) {
+    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_FP16X2) {
         g_create_error = "unknown precision";
+        return FASTMPS_ERR_INVALID_ARG;
+    }
+    if (o.accum_chunk < 0 || o.accum_chunk > 4096) {
+        g_create_error = "accum_chunk must be 0..4096";
         return FASTMPS_ERR_INVALID_ARG;
     }
     if (o.k_split < 0 || o.k_split > 8) {
@@ -1032,7 +1101,7 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
     }
     if (o.residency == FASTMPS_HOST_STREAM &&
         (o.precision == FASTMPS_FP32 || o.precision == FASTMPS_FP8X1 || o.precision == FASTMPS_FP8X2)) {
-        g_create_error = "host streaming keeps BF16 tensors: use a BF16 precision";
+        g_create_error = "host streaming keeps 16-bit tensors: use a BF16 or the FP16 precision";
         return FASTMPS_ERR_UNSUPPORTED;
     }
     int ndev = 0;
@@ -1246,7 +1315,8 @@ int fastmps_sample_displaced(fastmps_handle h, int M, int d, const int *bond_dim
         if (d < 2 || d > kMaxDisplacedD)
             return fail(h, FASTMPS_ERR_SHAPE, "displaced sampling supports 2 <= d <= " +
                                                   std::to_string(kMaxDisplacedD));
-        if (is_fp8(h)) return fail(h, FASTMPS_ERR_UNSUPPORTED, "displaced sampling needs FP32 or a BF16 precision");
+        if (is_fp8(h) || is_f16(h))
+            return fail(h, FASTMPS_ERR_UNSUPPORTED, "displaced sampling needs FP32 or a BF16 precision");
         if (N == 0) return run_sample(h, M, d, bond_dims, n0, N, seed, job, out_samples, out_logprob, trace_rows,
                                       trace_probs);
         const float2 *mu_dev;

@@ -1,6 +1,7 @@
 // Site-tensor repacking, FP32 SIMT contraction, measurement (Algorithm 2) and
 // output transposition kernels.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -91,11 +92,12 @@ __global__ void expand_bf16_kernel(const __nv_bfloat16 *__restrict__ compact, in
         __nv_bfloat16 hi = __float2bfloat16_rn(0.f), lo = hi;
         if (!q.zero) {
             const int64_t e = 2 * q.cidx + (q.re_part ? 0 : 1);
+            // 16-bit values moved as bits (BF16 or FP16 planes); negation flips the sign bit of either format
             hi = compact[e];
-            if (q.sign < 0.f) hi = __hneg(hi);
+            if (q.sign < 0.f) hi = __ushort_as_bfloat16((unsigned short)(__bfloat16_as_ushort(hi) ^ 0x8000u));
             if (planes > 1) {
                 lo = compact[plane + e];
-                if (q.sign < 0.f) lo = __hneg(lo);
+                if (q.sign < 0.f) lo = __ushort_as_bfloat16((unsigned short)(__bfloat16_as_ushort(lo) ^ 0x8000u));
             }
         }
         B_hi[i] = hi;
@@ -126,6 +128,19 @@ __global__ void repack_e4m3_kernel(const void *__restrict__ src, int is_f64, int
         float x = 0.f;
         if (!q.zero) x = q.sign * load_part(src, is_f64, q.cidx, q.re_part ? 0 : 1);
         B8[i] = (uint8_t)__nv_cvt_float_to_fp8(x * scale, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+__global__ void repack_f16_kernel(const void *__restrict__ src, int is_f64, int chi_l, int d, int chi_r, int Cs,
+                                  int ncols, int K_pad, float scale, uint16_t *__restrict__ B16) {
+    const int64_t total = (int64_t)ncols * K_pad;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(i / K_pad);
+        const int kappa = (int)(i - (int64_t)c * K_pad);
+        const StackedPos q = stacked_pos(c, kappa, chi_l, d, chi_r, Cs);
+        float x = 0.f;
+        if (!q.zero) x = q.sign * load_part(src, is_f64, q.cidx, q.re_part ? 0 : 1);
+        B16[i] = __half_as_ushort(__float2half_rn(x * scale));
     }
 }
 
@@ -169,6 +184,13 @@ void launch_repack_e4m3(const void *src, int is_f64, const SiteLayout &L, float 
                                                               L.K_pad, scale, B8);
 }
 
+void launch_repack_f16(const void *src, int is_f64, const SiteLayout &L, float scale, uint16_t *B16,
+                       cudaStream_t st) {
+    const int64_t total = (int64_t)L.ncols * L.K_pad;
+    repack_f16_kernel<<<grid_for(total, 256), 256, 0, st>>>(src, is_f64, L.chi_l, L.d, L.chi_r, L.Cs, L.ncols,
+                                                             L.K_pad, scale, B16);
+}
+
 void launch_absmax(const void *src, int is_f64, int64_t n_complex, float *out_dev, cudaStream_t st) {
     cudaMemsetAsync(out_dev, 0, sizeof(float), st);
     absmax_kernel<<<grid_for(2 * n_complex, 256), 256, 0, st>>>(src, is_f64, 2 * n_complex, out_dev);
@@ -204,6 +226,19 @@ __global__ void init_left_e4m3_kernel(uint8_t *V8, int64_t rows, int ld) {
     const int64_t total = rows * ld;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
         V8[i] = (uint8_t)__nv_cvt_float_to_fp8((i % ld) == 0 ? 1.f : 0.f, __NV_SATFINITE, __NV_E4M3);
+}
+
+__global__ void init_left_f16_kernel(uint16_t *V0, uint16_t *V1, int64_t rows, int ld) {
+    const int64_t total = rows * ld;
+    const uint16_t one = __half_as_ushort(__float2half_rn(1.f)), zero = __half_as_ushort(__float2half_rn(0.f));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        V0[i] = (i % ld) == 0 ? one : zero;
+        V1[i] = zero;
+    }
+}
+
+void launch_init_left_f16(uint16_t *V0, uint16_t *V1, int64_t rows, int ld, cudaStream_t st) {
+    init_left_f16_kernel<<<grid_for(rows * ld, 256), 256, 0, st>>>(V0, V1, rows, ld);
 }
 
 void launch_init_left_e4m3(uint8_t *V8, int64_t rows, int ld, cudaStream_t st) {

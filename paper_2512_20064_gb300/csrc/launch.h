@@ -37,6 +37,9 @@ void launch_repack_e4m3(const void *src, int is_f64, const SiteLayout &L, float 
                         cudaStream_t st);
 // Largest |Re| or |Im| of an interleaved complex tensor (as float), into *out_dev (zeroed first).
 void launch_absmax(const void *src, int is_f64, int64_t n_complex, float *out_dev, cudaStream_t st);
+// FP16 operand B[c][kappa] (K-major, ld = K_pad) of value * scale (scale a power of two), binary16 bits.
+void launch_repack_f16(const void *src, int is_f64, const SiteLayout &L, float scale, uint16_t *B16,
+                       cudaStream_t st);
 // FP32 SIMT operand: Bt[kappa][c] (N-major, ld = ncols), float.
 void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *Bt, cudaStream_t st);
 
@@ -45,6 +48,8 @@ void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *
 void launch_init_left_bf16(__nv_bfloat16 *const *Vp, int nplanes, int64_t rows, int ld, cudaStream_t st);
 void launch_init_left_f32(float *V, int64_t rows, int ld, cudaStream_t st);
 void launch_init_left_e4m3(uint8_t *V8, int64_t rows, int ld, cudaStream_t st);
+// FP16 planes of v_0 = [1]: plane 0 holds 1.0 in column 0, plane 1 zeros.
+void launch_init_left_f16(uint16_t *V0, uint16_t *V1, int64_t rows, int ld, cudaStream_t st);
 
 // ---- contraction kernels ---------------------------------------------------
 struct ContractOut {
@@ -65,6 +70,7 @@ void launch_contract_f32(const float *V, int64_t ldV, int64_t row0, int64_t rows
 constexpr int kMaxProducts = 4;
 struct TcArgs {
     bool fp8 = false;  // E4M3 operands (one plane each), kind::f8f6f4
+    bool f16 = false;  // FP16 (binary16) operands instead of BF16, kind::f16
     bool has_tmY = false;  // tmY maps the FP32 scratch (ncols x rows, 32 x 128 boxes): TMA-store epilogue
     CUtensorMap tmY;
     CUtensorMap tmA[3];
@@ -91,6 +97,11 @@ bool cluster_plan(const SiteLayout &L, int *C, int *T);
 // rounding only.
 cudaError_t launch_contract_tc_splitk(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int ksplit,
                                       int *d_err, cudaStream_t st, int *clusters_out = nullptr);
+// Promoted accumulation: as launch_contract_tc (two-pass outputs Y and P, a.has_tmY required) with
+// n-tiles of 256 columns (L.bn == 256) whose contraction index is accumulated by the tensor cores
+// kchunk k-blocks at a time into fresh accumulators, the chunk sums being added in FP32 registers.
+cudaError_t launch_contract_tc_promoted(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int kchunk,
+                                        int num_sms, int *d_err, cudaStream_t st);
 // Clusters of the site's plan that can be resident at once on the current device (0: not runnable).
 int cluster_capacity(int a_planes, int b_planes, const SiteLayout &L);
 // Contraction + measurement of rows_valid rows in one launch; m describes the draw and the next left
@@ -114,8 +125,9 @@ struct MeasureArgs {
     int ld_next;              // ld of the next V buffer (elements)
     int K_next;               // entries of the next row that must be written (2 chi_r .. K_next-1 zeroed)
     float *V32;               // FP32 path (or nullptr)
-    __nv_bfloat16 *Vp[3];     // BF16 paths: planes of successive residuals
+    __nv_bfloat16 *Vp[3];     // BF16 paths: planes of successive residuals (FP16 path: binary16 bits)
     int nplanes;              // 2 or 3
+    int f16 = 0;              // FP16 path: two binary16 planes of each row scaled by a per-row power of two
     uint8_t *V8 = nullptr;    // FP8 path: E4M3 row scaled by a per-row power of two
     uint8_t *V8lo = nullptr;  // FP8X2: E4M3 residual plane at the same per-row scale (or nullptr)
     const float2 *mu = nullptr;  // displaced measurement: amplitude of each row of this micro-batch

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <stdint.h>
 
@@ -64,6 +65,25 @@ __device__ __forceinline__ void measure_write_row(const MeasureArgs &a, int lane
             }
         } else {
             for (int i = lane; i < a.K_next; i += 32) dst[i] = i < nreal ? ysrc[i] * scale : 0.f;
+        }
+        return;
+    }
+    if (a.f16) {
+        // FP16 row: scale the unit-norm row by the power of two that puts its largest entry in
+        // [16384, 32768] (the scale cancels in w/Z at the next site; small entries stay normal), then
+        // two binary16 planes of successive residuals, each rounded to nearest even
+        float m = 0.f;
+        for (int i = lane; i < nreal; i += 32) m = fmaxf(m, fabsf(__ldcg(ysrc + i) * scale));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const float s16 = m > 0.f ? exp2f(floorf(log2f(32768.f / m))) : 1.f;
+        uint16_t *d0 = reinterpret_cast<uint16_t *>(a.Vp[0]) + grow * a.ld_next;
+        uint16_t *d1 = reinterpret_cast<uint16_t *>(a.Vp[1]) + grow * a.ld_next;
+        for (int i = lane; i < a.K_next; i += 32) {
+            const float x = i < nreal ? (__ldcg(ysrc + i) * scale) * s16 : 0.f;
+            const __half h = __float2half_rn(x);
+            d0[i] = __half_as_ushort(h);
+            d1[i] = __half_as_ushort(__float2half_rn(x - __half2float(h)));
         }
         return;
     }

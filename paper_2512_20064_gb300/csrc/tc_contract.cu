@@ -74,7 +74,8 @@ constexpr int kMaxClusterTiles = 32;         // cluster variant: n-tiles per m-t
 constexpr int kMaxClusterCTAs = 16;          // largest (non-portable) cluster
 constexpr uint32_t kClusterBytes = 64 + 4 * 128 * 4 * 2;  // 4 mbarriers + partial sums [2][T <= 4][128]
 
-enum TcMode : int { kTwoPass = 0, kFusedCta = 1, kClusterFused = 2, kSplitK = 3 };
+enum TcMode : int { kTwoPass = 0, kFusedCta = 1, kClusterFused = 2, kSplitK = 3, kPromoted = 4 };
+constexpr int kThreadsPromoted = 320;        // TMA + MMA + 8 epilogue warps (two per lane quarter)
 
 struct TcParams {
     int num_m_tiles, num_n_tiles, num_k_blocks, bn;
@@ -92,6 +93,7 @@ struct TcParams {
     int *err;
     int cl_T;  // cluster variant: n-tiles per CTA per m-tile (the cluster has num_n_tiles / cl_T CTAs)
     int ksplit;  // split-K variant: CTAs per cluster, each accumulating 1/ksplit of the k-blocks
+    int kchunk;  // promoted accumulation: k-blocks per tensor-memory accumulator (n-tile of 128 columns)
     // fused measurement
     MeasureArgs m;
 };
@@ -439,8 +441,89 @@ __device__ __forceinline__ void splitk_epilogue(const TcParams &p, const CUtenso
     if (rank == 0 && threadIdx.x == 64) bulk_wait_all();
 }
 
+// ---------------------------------------------------------------------------
+// Promoted accumulation: the MMA issuer accumulates every p.kchunk k-blocks of
+// the contraction index into a fresh accumulator (two of 256 columns in
+// rotation), and eight epilogue warps add the chunk sums in FP32 registers,
+// rounding to nearest: warps w and w+4 share tensor-memory lane quarter w % 4
+// (the tile's rows) and take the low and high 128 columns of the tile.  The
+// tensor cores' accumulation then spans a few k-blocks only, where its partial
+// sums are small, and the long sum over the whole index is taken with correctly
+// rounded FP32 additions.  The tile is stored like the two-pass epilogue (TMA
+// stores of 128 x 32 chunks, each half through its own staging buffer) and
+// the row's sum of squares is the sum of the two halves' sums.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void promoted_epilogue(const TcParams &p, const CUtensorMap *tmY, uint32_t tmem_base,
+                                                  uint64_t *tfull, uint64_t *tempty, uint8_t *ystage, float *ss_hi,
+                                                  volatile int *abort_flag, int warp, int lane) {
+    const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;        // 0: columns 0..127 of the tile, 1: columns 128..255
+    const int rl = quad * 32 + lane;
+    const int elected = half == 0 ? 64 : 192;  // first thread of each half
+    const int nch = (p.num_k_blocks + p.kchunk - 1) / p.kchunk;
+    uint8_t *sb = ystage + (uint32_t)half * kYStageBytes;  // this half's staging buffer
+    uint32_t cq = 0;  // chunks consumed (buffer cq % 2)
+    int mt, nt;
+    for (int i = 0; tile_of<kPromoted>(p, i, mt, nt); ++i) {
+        float acc[128];
+        for (int c = 0; c < nch; ++c, ++cq) {
+            const int buf = (int)(cq & 1u);
+            const uint32_t use = cq >> 1;
+            const bool ready = mbar_wait_bounded(&tfull[buf], use & 1u, abort_flag);
+            if (named_bar_any(1, 256, !ready)) {
+                record_error(p.err, abort_flag, kDevTimeoutEpilogue);
+                return;
+            }
+            tc_fence_after();
+            const uint32_t taddr =
+                tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)buf * kAccStride + (uint32_t)(half * 128);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                uint32_t r[16];
+                tmem_ld_32x32b_x16(taddr + (uint32_t)(g * 16), r);
+                tc_wait_ld();
+                if (c == 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[g * 16 + j] = __uint_as_float(r[j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) acc[g * 16 + j] += __uint_as_float(r[j]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&tempty[buf]);
+        }
+        const int row = mt * kBM + rl;
+        float ss = 0.f;
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) ss = fmaf(acc[g * 32 + j], acc[g * 32 + j], ss);
+            if (threadIdx.x == elected) bulk_wait_read_0();  // this half's previous store has read sb
+            named_bar_sync(2 + half, 128);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                *reinterpret_cast<float4 *>(sb + rl * 128 + ((j ^ (rl & 7)) * 16)) =
+                    make_float4(acc[g * 32 + 4 * j], acc[g * 32 + 4 * j + 1], acc[g * 32 + 4 * j + 2],
+                                acc[g * 32 + 4 * j + 3]);
+            fence_proxy_async_smem();
+            named_bar_sync(2 + half, 128);
+            if (threadIdx.x == elected) {
+                tma_store_2d(tmY, sb, nt * p.bn + half * 128 + g * 32, mt * kBM);
+                bulk_commit();
+            }
+        }
+        // the row's sum of squares: low half + high half
+        if (half == 1) ss_hi[rl] = ss;
+        named_bar_sync(1, 256);
+        if (half == 0 && row < p.rows_valid) p.P[(int64_t)row * p.ldP + nt] = ss + ss_hi[rl];
+        named_bar_sync(1, 256);  // ss_hi is free for the next tile
+    }
+    if (threadIdx.x == elected) bulk_wait_all();
+}
+
 template <int kMode, bool kFp8>
-__global__ void __launch_bounds__(kMode == kFusedCta ? kThreadsFused : kThreads, 1)
+__global__ void __launch_bounds__(kMode == kFusedCta ? kThreadsFused : (kMode == kPromoted ? kThreadsPromoted : kThreads), 1)
 tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
                    const __grid_constant__ CUtensorMap tmA2, const __grid_constant__ CUtensorMap tmB0,
                    const __grid_constant__ CUtensorMap tmB1, const __grid_constant__ CUtensorMap tmY,
@@ -448,6 +531,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     constexpr bool kFused = kMode == kFusedCta;
     constexpr bool kCluster = kMode == kClusterFused;
     constexpr bool kSplit = kMode == kSplitK;
+    constexpr bool kPromo = kMode == kPromoted;
     // split-K: this CTA's share of the k-blocks
     const int kb_lo = kSplit ? (int)(cluster_ctarank() * (uint32_t)p.num_k_blocks / (uint32_t)p.ksplit) : 0;
     const int kb_hi = kSplit ? (int)((cluster_ctarank() + 1) * (uint32_t)p.num_k_blocks / (uint32_t)p.ksplit)
@@ -459,9 +543,9 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     uint8_t *ystage = smem + (size_t)p.stages * p.stage_bytes;  // 2 x 16 KB when p.tma_store
     uint64_t *full = reinterpret_cast<uint64_t *>(ystage + (p.tma_store ? 2 * kYStageBytes : 0u));
     uint64_t *empty = full + p.stages;
-    uint64_t *tfull = empty + p.stages;
-    uint64_t *tempty = tfull + 2;
-    uint64_t *drain = tempty + 2;
+    uint64_t *tfull = empty + p.stages;  // [4]: accumulator buffers (two 256-column, or four 128-column)
+    uint64_t *tempty = tfull + 4;
+    uint64_t *drain = tempty + 4;
     uint64_t *mfull = drain + 1;     // [kRing] m-tile handed to the measurement warps
     uint64_t *mempty = mfull + kRing;
     int *mt_slot = reinterpret_cast<int *>(mempty + kRing);
@@ -481,10 +565,10 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(&tfull[0], 1);
-        mbar_init(&tfull[1], 1);
-        mbar_init(&tempty[0], 128);
-        mbar_init(&tempty[1], 128);
+        for (int b = 0; b < 4; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kPromo ? 256 : 128);
+        }
         mbar_init(drain, 1);
         for (int r = 0; r < kRing; ++r) {
             mbar_init(&mfull[r], 1);
@@ -574,17 +658,34 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             bool failed = false;
             bool issued = false;
             int mt, nt;
+            uint32_t cq = 0;  // promoted accumulation: chunks issued so far (buffer cq % 2)
             for (int i = 0; !failed && tile_of<kMode>(p, i, mt, nt); ++i, ++lt) {
-                const int buf = lt & 1;
-                const uint32_t use = (uint32_t)(lt >> 1);
-                if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag)) {
-                    record_error(p.err, abort_flag, kDevTimeoutMma);
-                    failed = true;
-                    break;
+                int buf = lt & 1;
+                uint32_t d_tmem = 0;
+                if (!kPromo) {
+                    const uint32_t use = (uint32_t)(lt >> 1);
+                    if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag)) {
+                        record_error(p.err, abort_flag, kDevTimeoutMma);
+                        failed = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    d_tmem = tmem_base + (uint32_t)buf * kAccStride;
                 }
-                tc_fence_after();
-                const uint32_t d_tmem = tmem_base + (uint32_t)buf * kAccStride;
                 for (int kb = kb_lo; kb < kb_hi; ++kb) {
+                    const int kin = kPromo ? (kb - kb_lo) % p.kchunk : kb - kb_lo;  // k-block within the accumulator
+                    if (kPromo && kin == 0) {
+                        // a fresh 128-column accumulator for the next chunk of the contraction index
+                        buf = (int)(cq & 1u);
+                        const uint32_t use = cq >> 1;
+                        if (!mbar_wait_bounded(&tempty[buf], (use & 1u) ^ 1u, abort_flag)) {
+                            record_error(p.err, abort_flag, kDevTimeoutMma);
+                            failed = true;
+                            break;
+                        }
+                        tc_fence_after();
+                        d_tmem = tmem_base + (uint32_t)buf * kAccStride;
+                    }
                     if (!mbar_wait_bounded(&full[stage], phase, abort_flag)) {
                         record_error(p.err, abort_flag, kDevTimeoutMma);
                         failed = true;
@@ -604,7 +705,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                         for (int k16 = 0; k16 < kBK / 16; ++k16) {
                             // +32 bytes along K inside the swizzle row = +2 in the address field
                             // (16 BF16 or 32 FP8 elements per MMA)
-                            const uint32_t acc = ((kb - kb_lo) | q | k16) != 0 ? 1u : 0u;
+                            const uint32_t acc = (kin | q | k16) != 0 ? 1u : 0u;
                             if (kFp8)
                                 tc_mma_f8(d_tmem, ad + (uint64_t)(2 * k16), bd + (uint64_t)(2 * k16), p.idesc, acc);
                             else
@@ -617,9 +718,13 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
                         stage = 0;
                         phase ^= 1u;
                     }
+                    if (kPromo && (kin == p.kchunk - 1 || kb == kb_hi - 1)) {
+                        tc_commit(&tfull[buf]);
+                        ++cq;
+                    }
                 }
                 if (failed) break;
-                tc_commit(&tfull[buf]);
+                if (!kPromo) tc_commit(&tfull[buf]);
             }
             if (failed && issued) {
                 // wait for this thread's outstanding MMAs before tensor memory is freed
@@ -631,6 +736,9 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     } else if (kCluster && warp < 6) {
         // ---------------- cluster epilogue: warps 2..5 ----------------
         cluster_epilogue(p, tmem_base, tfull, tempty, pready, pfree, part, abort_flag, warp, lane);
+    } else if (kPromo) {
+        // ---------------- promoted-accumulation epilogue: warps 2..9 ----------------
+        promoted_epilogue(p, &tmY, tmem_base, tfull, tempty, ystage, m_scale, abort_flag, warp, lane);
     } else if (kSplit && warp < 6) {
         // ---------------- split-K epilogue: warps 2..5 ----------------
         splitk_epilogue(p, &tmY, tmem_base, tfull, tempty, pready, pfree, ystage, abort_flag, warp, lane);
@@ -818,7 +926,7 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
         }
     }
     p.row0 = (int)a.row0;
-    p.idesc = a.fp8 ? idesc_e4m3_f32(kBM, L.bn) : idesc_bf16_f32(kBM, L.bn);
+    p.idesc = a.fp8 ? idesc_e4m3_f32(kBM, L.bn) : (a.f16 ? idesc_f16_f32(kBM, L.bn) : idesc_bf16_f32(kBM, L.bn));
     if (a.fp8 && (fused || a.a_planes > 2 || a.b_planes != 1)) return cudaErrorInvalidValue;
     p.Y = o.Y;
     p.ldY = o.ldY;
@@ -828,6 +936,7 @@ cudaError_t launch_contract_tc(const TcArgs &a, const SiteLayout &L, const Contr
     p.err = d_err;
     p.cl_T = 1;
     p.ksplit = 1;
+    p.kchunk = 0;
     if (fused) {
         p.m = *fused;
     } else {
@@ -935,7 +1044,8 @@ int cluster_capacity(int a_planes, int b_planes, const SiteLayout &L) {
 cudaError_t launch_contract_tc_cluster(const TcArgs &a, const SiteLayout &L, int rows_valid, int *d_err,
                                        cudaStream_t st, const MeasureArgs &m, int *clusters_out) {
     int C = 0, T = 0;
-    if (a.fp8 || !cluster_plan(L, &C, &T)) return cudaErrorInvalidConfiguration;
+    // FP16 rows are scaled by their largest entry, which no single CTA of the cluster sees
+    if (a.fp8 || a.f16 || !cluster_plan(L, &C, &T)) return cudaErrorInvalidConfiguration;
     if (a.nprod < 1 || a.nprod > kMaxProducts || a.a_planes < 1 || a.a_planes > 3 || a.b_planes < 1 ||
         a.b_planes > 2 || m.nplanes != a.a_planes)
         return cudaErrorInvalidValue;
@@ -962,7 +1072,7 @@ cudaError_t launch_contract_tc_cluster(const TcArgs &a, const SiteLayout &L, int
     if (max_clusters <= 0) return cudaErrorInvalidConfiguration;
     p.tma_store = 0;
     p.row0 = (int)a.row0;
-    p.idesc = idesc_bf16_f32(kBM, L.bn);
+    p.idesc = a.f16 ? idesc_f16_f32(kBM, L.bn) : idesc_bf16_f32(kBM, L.bn);
     p.Y = nullptr;
     p.ldY = 0;
     p.P = nullptr;
@@ -971,6 +1081,7 @@ cudaError_t launch_contract_tc_cluster(const TcArgs &a, const SiteLayout &L, int
     p.err = d_err;
     p.cl_T = T;
     p.ksplit = 1;
+    p.kchunk = 0;
     p.m = m;
     if (p.num_m_tiles <= 0) return cudaSuccess;
     (void)smem;
@@ -1015,7 +1126,7 @@ cudaError_t launch_contract_tc_splitk(const TcArgs &a, const SiteLayout &L, cons
     if (p.stages < 2) return cudaErrorInvalidConfiguration;
     p.tma_store = 1;
     p.row0 = (int)a.row0;
-    p.idesc = idesc_bf16_f32(kBM, L.bn);
+    p.idesc = a.f16 ? idesc_f16_f32(kBM, L.bn) : idesc_bf16_f32(kBM, L.bn);
     p.Y = o.Y;
     p.ldY = o.ldY;
     p.P = o.P;
@@ -1024,6 +1135,7 @@ cudaError_t launch_contract_tc_splitk(const TcArgs &a, const SiteLayout &L, cons
     p.err = d_err;
     p.cl_T = 1;
     p.ksplit = ksplit;
+    p.kchunk = 0;
     p.m = MeasureArgs{};
     const int tiles = p.num_m_tiles * p.num_n_tiles;
     if (tiles <= 0) return cudaSuccess;
@@ -1054,6 +1166,56 @@ cudaError_t launch_contract_tc_splitk(const TcArgs &a, const SiteLayout &L, cons
     const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
     e = cudaLaunchKernelEx(&cfg, kern, a.tmA[0], a1, a2, a.tmB[0], b1, a.tmY, p);
     if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract_tc_promoted(const TcArgs &a, const SiteLayout &L, const ContractOut &o, int kchunk,
+                                        int num_sms, int *d_err, cudaStream_t st) {
+    if (a.fp8 || !a.has_tmY || L.bn != 256 || kchunk < 1) return cudaErrorInvalidValue;
+    if (a.nprod < 1 || a.nprod > kMaxProducts || a.a_planes < 1 || a.a_planes > 3 || a.b_planes < 1 ||
+        a.b_planes > 2)
+        return cudaErrorInvalidValue;
+    TcParams p;
+    p.num_m_tiles = a.rows_pad / kBM;
+    p.num_n_tiles = L.ncols / L.bn;
+    p.num_k_blocks = L.K_pad / L.bk;
+    p.bn = L.bn;
+    p.a_planes = a.a_planes;
+    p.b_planes = a.b_planes;
+    p.nprod = a.nprod;
+    p.prod_code = 0;
+    for (int q = 0; q < a.nprod; ++q) {
+        if (a.prod_a[q] < 0 || a.prod_a[q] >= a.a_planes || a.prod_b[q] < 0 || a.prod_b[q] >= a.b_planes)
+            return cudaErrorInvalidValue;
+        p.prod_code |= ((uint32_t)a.prod_a[q] | ((uint32_t)a.prod_b[q] << 2)) << (4 * q);
+    }
+    p.b_plane_bytes = (uint32_t)L.bn * 128;
+    p.stage_bytes = (uint32_t)a.a_planes * kATileBytes + (uint32_t)a.b_planes * p.b_plane_bytes;
+    p.stages = stages_for(p.stage_bytes, 2 * kYStageBytes);
+    if (p.stages < 2) return cudaErrorInvalidConfiguration;
+    p.tma_store = 1;
+    p.row0 = (int)a.row0;
+    p.idesc = a.f16 ? idesc_f16_f32(kBM, L.bn) : idesc_bf16_f32(kBM, L.bn);
+    p.Y = o.Y;
+    p.ldY = o.ldY;
+    p.P = o.P;
+    p.ldP = o.ldP;
+    p.rows_valid = o.rows_valid;
+    p.err = d_err;
+    p.cl_T = 1;
+    p.ksplit = 1;
+    p.kchunk = kchunk < p.num_k_blocks ? kchunk : p.num_k_blocks;
+    p.m = MeasureArgs{};
+    const int tiles = p.num_m_tiles * p.num_n_tiles;
+    if (tiles <= 0) return cudaSuccess;
+    const size_t smem = (size_t)p.stages * p.stage_bytes + 1024 + kBarrierBytes + 2 * kYStageBytes;
+    auto kern = tc_contract_kernel<kPromoted, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e != cudaSuccess) return e;
+    const int grid = tiles < num_sms ? tiles : num_sms;
+    const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
+    const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
+    kern<<<grid, kThreadsPromoted, smem, st>>>(a.tmA[0], a1, a2, a.tmB[0], b1, a.tmY, p);
     return cudaGetLastError();
 }
 
