@@ -217,7 +217,7 @@ def cpu_oracle_rate(w, b, tensors_host_fn, cpu_seconds: float, rows_max: int = 5
     probe = max(1e-3, time.perf_counter() - t0)
     flop_rate = cores * sum(site_flops[:Kp]) / probe
     budget = flop_rate * cpu_seconds                       # flops the timed sample may take
-    R = cores * 4
+    R = cores * 8                                          # the oracle works in batches of 8 rows per core
     K, acc = 0, 0.0
     while K < w.M and acc + R * site_flops[K] <= budget:
         acc += R * site_flops[K]
@@ -546,7 +546,7 @@ def run_batching(args, rank, ws, local):
     chains, chains32 = [], []
     for j, sp in enumerate(specs):
         b, ts, idx = gen.mps_tensors(sp["M"], sp["d"], sp["chi"], base_seed=sp["base_seed"], skew=1.5, pool=4,
-                                     device=f"cuda:{local}")
+                                     device=f"cuda:{local}" if args.gen_device == "cuda" else None)
         s = F.Sampler(device=local, precision=precision)
         s.load_chain(ts, site_index=idx)
         chains.append((s, b))

@@ -2,10 +2,11 @@
 configuration: site tensors generated on the device, one call of 2^18 rows (tensor-core modes: four
 micro-batches of 65536 rows) or 2^17 rows (FP32: two micro-batches).
 
-Modes: FP16x2 operands with promoted accumulation (the benchmark's low-precision mode; gated at 1e-4),
-the FP32 SIMT path (gated at 1e-5), and BF16x2 without promotion, whose error at this chain length is
-measured and reported but not gated: its 16-bit left rows and its tensor-core accumulation over the
-whole 2048-long index each drift by about 1e-4 by the last sites.
+Modes: FP16x2 operands with promoted accumulation (the benchmark's low-precision mode; gated at 1e-4)
+and the FP32 SIMT path (gated at 1e-5).  (BF16x2 without promotion misses 1e-4 at this chain length --
+3.2e-4 on the same 1024 rows -- and is not run by default.)  Further modes can be replayed and reported,
+ungated, by naming them in FASTMPS_PARITY_MODES, e.g. "bf16x2:0,bf16x3l:4,fp16x2:8"
+(precision:accum_chunk).
 
 1024 rows per mode are replayed by the oracle along the device's outcomes, the same number in every
 micro-batch (256 of each of four, or 512 of each of two): spread over the micro-batch, including its
@@ -16,6 +17,8 @@ error profile; for the 16-bit modes the oracle also replays 128 of the rows on t
 which gives the storage error (16-bit store vs original, oracle vs oracle) and the device's total
 error against the original tensors (reported, not gated).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -28,8 +31,10 @@ pytestmark = pytest.mark.gpu
 
 MICRO = 1 << 16
 # mode: (precision, accum_chunk, rows per call, tolerance gated or None)
-MODES = {"fp16x2-promoted": ("fp16x2", 4, 1 << 18, 1e-4), "fp32": ("fp32", 0, 1 << 17, 1e-5),
-         "bf16x2": ("bf16x2", 0, 1 << 18, None)}
+MODES = {"fp16x2-promoted": ("fp16x2", 4, 1 << 18, 1e-4), "fp32": ("fp32", 0, 1 << 17, 1e-5)}
+for _spec in filter(None, os.environ.get("FASTMPS_PARITY_MODES", "").split(",")):
+    _prec, _chunk = _spec.split(":")
+    MODES[_spec] = (_prec, int(_chunk), 1 << 18, None)
 STORAGE_ROWS = 128
 
 
@@ -91,8 +96,9 @@ def test_precision_workload_1024_rows(precision_chain, mode):
             return quant.dequant_fp16(ts[k].cpu().numpy())
     else:
         def tensor(k):
-            # what the BF16 store holds, exactly representable as complex64
-            return quant.dequant_bf16(ts[k].cpu().numpy(), 1).astype(np.complex64)
+            # what the BF16 store holds (hi + lo of a float32 fits a float32 again: complex64 is exact)
+            planes = 2 if precision in ("bf16x3", "bf16x4") else 1
+            return quant.dequant_bf16(ts[k].cpu().numpy(), planes).astype(np.complex64)
 
     rep = parity.check(b, tensor, w.sampler_seed, rows, smp, lp, tol if tol else 1.0, dev_trace=tr,
                        dev_trace_list=rows, site_chunk=32)
