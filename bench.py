@@ -175,8 +175,9 @@ class ClockSampler:
 # DRAM bytes (read + write) of one contraction launch at an interior site, from the committed ncu
 # captures (scaled by rows to the bench's launch size); None where no capture of the current kernel exists.
 CONTRACT_TRAFFIC = {
-    ("precision", "bf16x2", "separate"): (2.89e9, "profiles/tc_contract_precision_bf16x2.md"),
-    ("plain", "bf16x2", "separate"): (1.287e9, "profiles/tc_contract_plain_bf16x2.md"),
+    ("precision", "bf16x2", "separate", 0): (2.89e9, "profiles/tc_contract_precision_bf16x2.md"),
+    ("plain", "bf16x2", "separate", 0): (1.287e9, "profiles/tc_contract_plain_bf16x2.md"),
+    ("precision", "fp16x2", "separate", 4): (2.99e9, "profiles/tc_contract_precision_fp16x2_promoted.md"),
 }
 
 
@@ -213,9 +214,9 @@ def cpu_oracle_rate(w, b, tensors_host_fn, cpu_seconds: float, rows_max: int = 5
     Kp = min(w.M, max(8, (b.index(w.chi) + 2) if w.chi in b else 8))
     tsp = tensors_host_fn(Kp)
     t0 = time.perf_counter()
-    oracle.sample_prefix(b, tsp, w.sampler_seed, cores, Kp, nthreads=cores)
+    oracle.sample_prefix(b, tsp, w.sampler_seed, cores * 8, Kp, nthreads=cores)
     probe = max(1e-3, time.perf_counter() - t0)
-    flop_rate = cores * sum(site_flops[:Kp]) / probe
+    flop_rate = cores * 8 * sum(site_flops[:Kp]) / probe
     budget = flop_rate * cpu_seconds                       # flops the timed sample may take
     R = cores * 8                                          # the oracle works in batches of 8 rows per core
     K, acc = 0, 0.0
@@ -359,7 +360,7 @@ def run_ours(args, rank, ws, local):
             peak_note += " x 2 (nominal FP8/BF16 ratio)"
         achieved = flops_alg / (contract_ms / 1e3) / 1e12
         achieved_issued = flops_iss / (contract_ms / 1e3) / 1e12
-        tr = CONTRACT_TRAFFIC.get((args.workload, precision, measurement)) if not args.sites else None
+        tr = CONTRACT_TRAFFIC.get((args.workload, precision, measurement, args.accum_chunk_eff)) if not args.sites else None
         nominal = NOMINAL_TFLOPS["fp8" if precision in ("fp8x1", "fp8x2") else "bf16"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": tr[0] if tr else None, "traffic_source": tr[1] if tr else None,

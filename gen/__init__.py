@@ -231,7 +231,7 @@ WORKLOADS = {
     "plain": Workload("plain", M=256, d=4, chi=256, N=1 << 17, skew=1.5,
                       note="M=256 d=4 chi=256 skew exp(-s/1.5), N=2^17, complex64 resident"),
     "precision": Workload("precision", M=1024, d=4, chi=1024, N=1 << 20, skew=1.5,
-                          note="M=1024 d=4 chi=1024 skew exp(-s/1.5), N=2^20, BF16 split"),
+                          note="M=1024 d=4 chi=1024 skew exp(-s/1.5), N=2^20, 16-bit split operands"),
     "streaming": Workload("streaming", M=2048, d=3, chi=10_000, N=1 << 16, skew=1.5, pool=16,
                           note="M=2048 d=3 chi=1e4, pool of 16 interior isometries, host-streamed BF16, N=2^16"),
 }
