@@ -9,7 +9,8 @@ even) with integer operations on the float32 bit patterns; it shares nothing
 with the CUDA path.
 
 Pinned in ``tests/oracle_pins.py`` (``QUANT_PINS``): hand-derived rounding cases of
-both formats and an independent cross-check against torch's casts; planted
+every format, the hi/lo splits of both 16-bit formats, and an independent cross-check against
+torch's casts; planted
 mistakes (truncation, ties away from zero, no saturation, a wrong subnormal
 floor, a ceiling scale, ...) are each caught (``tests/test_oracle_mutants.py``).
 """
@@ -131,10 +132,26 @@ def fp16_site_scale(A) -> float:
     return float(2.0 ** np.floor(np.log2(FP16_TOP / m)))
 
 
-def dequant_fp16(A) -> np.ndarray:
-    """The complex128 tensor an FP16 store with a per-site power-of-two scale represents."""
+def fp16_split(x):
+    """``hi = fp16(x)``, ``lo = fp16(x - hi)``: two binary16 planes of float32 values (the difference is
+    exact in float32), returned as float64."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float32))
+    hi = fp16_round(x)
+    lo = fp16_round((x.astype(np.float64) - hi).astype(np.float32))
+    return hi, lo
+
+
+def dequant_fp16(A, planes: int = 1) -> np.ndarray:
+    """The complex128 tensor an FP16 store with a per-site power-of-two scale represents.
+
+    ``planes=1``: each scaled part rounded to binary16.  ``planes=2``: each scaled part held as a
+    ``hi + lo`` binary16 pair at the same scale (Sec. 3.3.2's 16-bit format, two planes)."""
     s = fp16_site_scale(A)
     re = np.asarray(A.real, dtype=np.float32) * np.float32(s)
     im = np.asarray(A.imag, dtype=np.float32) * np.float32(s)
-    return (fp16_round(re) + 1j * fp16_round(im)) / s
+    if planes == 1:
+        return (fp16_round(re) + 1j * fp16_round(im)) / s
+    rh, rl = fp16_split(re)
+    ih, il = fp16_split(im)
+    return ((rh + rl) + 1j * (ih + il)) / s
 

@@ -41,8 +41,8 @@ What pins what
   (ties to even of both parities, carries into the exponent, subnormal grids, the E4M3
   2^-6 boundary and saturation at 448, signed zero), cross-checked against torch's
   bfloat16 / float8_e4m3fn casts called as a library; the hi/lo split holds 16
-  significant bits; the FP8 site scale is the power of two that puts max|Re, Im| in
-  [224, 448].
+  significant bits (binary16: 22); the FP8 site scale is the power of two that puts
+  max|Re, Im| in [224, 448].
 """
 from __future__ import annotations
 
@@ -672,6 +672,61 @@ def pin_fp16_site_scale_and_dequant(Q, seed=8):
     return True, ""
 
 
+def pin_fp16_split(Q, n=100000, seed=9):
+    """hi = fp16(x), lo = fp16(x - hi): checked against torch's casts; two 11-bit planes hold 22
+    significant bits, |x - hi - lo| <= 2^-22 |x| wherever |x| >= 2^-3 (below, lo is subnormal and the
+    error is at most 2^-25); values with 22 significant bits are held exactly."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal(n) * 2.0 ** rng.integers(-20, 15, size=n)).astype(np.float32)
+    x = x[np.abs(x) <= 32768.0]
+    hi, lo = Q.fp16_split(x)
+    th = torch.from_numpy(x.copy()).to(torch.float16)
+    tl = (torch.from_numpy(x.copy()) - th.float()).to(torch.float16)
+    if not (np.array_equal(hi, th.double().numpy()) and np.array_equal(lo, tl.double().numpy())):
+        return False, "fp16_split planes differ from torch's casts"
+    a = np.abs(x.astype(np.float64))
+    err = np.abs(x.astype(np.float64) - hi - lo)
+    if not (err <= np.maximum(2.0 ** -22 * a, 2.0 ** -25)).all():
+        return False, f"hi + lo misses x by {float(err.max()):.3e}"
+    if not (err[a >= 0.125] <= 2.0 ** -22 * a[a >= 0.125]).all():
+        return False, "relative error above 2^-22 among |x| >= 2^-3"
+    y = _f32([1000.0 + 2.0 ** -12, -(3.0 + 2.0 ** -18), 1.0 + 2.0 ** -21, 20000.0 + 2.0 ** -6])
+    h, l = Q.fp16_split(y)
+    if not np.array_equal(h + l, y.astype(np.float64)):
+        return False, "a 22-bit value is not held exactly by hi + lo"
+    if not np.array_equal(h, _f32([1000.0, -3.0, 1.0, 20000.0]).astype(np.float64)):
+        return False, "hi is not the nearest binary16 value"
+    return True, ""
+
+
+def pin_dequant_fp16_two_planes(Q, seed=10):
+    """dequant_fp16(A, 2) is (hi + lo) / scale of each scaled part at the one-plane scale, within
+    2^-22 relative of the float32 parts (entries not tiny against the scale), and is idempotent."""
+    rng = np.random.default_rng(seed)
+    for m in (1.0, 0.37, 5e-4):
+        A = rng.standard_normal((6, 3, 5)) + 1j * rng.standard_normal((6, 3, 5))
+        A *= m / max(np.abs(A.real).max(), np.abs(A.imag).max())
+        sc = Q.fp16_site_scale(A)
+        D = Q.dequant_fp16(A, 2)
+        for part, dpart in ((A.real, D.real), (A.imag, D.imag)):
+            xs = (part.astype(np.float32) * np.float32(sc)).astype(np.float32)
+            hi = Q.fp16_round(xs)
+            lo = Q.fp16_round((xs.astype(np.float64) - hi).astype(np.float32))
+            if not np.array_equal(dpart, (hi + lo) / sc):
+                return False, "dequant_fp16(A, 2) is not the two-plane value"
+            ref = part.astype(np.float32).astype(np.float64)
+            big = np.abs(ref) * sc >= 0.125
+            if (np.abs(dpart - ref)[big] > 2.0 ** -22 * np.abs(ref)[big]).any():
+                return False, "two planes do not hold 22 bits"
+        if not np.array_equal(Q.dequant_fp16(D, 2), D):
+            return False, "dequant_fp16(., 2) is not idempotent"
+        if np.array_equal(Q.dequant_fp16(A, 1), D):
+            return False, "the second plane adds nothing"
+    return True, ""
+
+
 QUANT_PINS = [pin_bf16_hand_cases, pin_bf16_vs_torch, pin_bf16_split, pin_dequant_bf16, pin_e4m3_hand_cases,
               pin_e4m3_vs_torch, pin_e4m3_site_scale, pin_dequant_e4m3, pin_fp16_hand_cases, pin_fp16_vs_torch,
-              pin_fp16_site_scale_and_dequant]
+              pin_fp16_site_scale_and_dequant, pin_fp16_split, pin_dequant_fp16_two_planes]

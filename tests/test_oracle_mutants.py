@@ -136,6 +136,14 @@ QUANT_MUTANTS = {
                              "    return float(2.0 ** np.ceil(np.log2(FP16_TOP / m)))"),
     "dequant_fp16_imag_unscaled": ("    im = np.asarray(A.imag, dtype=np.float32) * np.float32(s)",
                                    "    im = np.asarray(A.imag, dtype=np.float32)"),
+    "fp16_lo_plane_unrounded": ("    lo = fp16_round((x.astype(np.float64) - hi).astype(np.float32))",
+                                "    lo = (x.astype(np.float64) - hi).astype(np.float32).astype(np.float64)"),
+    "fp16_lo_plane_dropped": ("    lo = fp16_round((x.astype(np.float64) - hi).astype(np.float32))",
+                              "    lo = hi * 0"),
+    "fp16_lo_as_bf16": ("    lo = fp16_round((x.astype(np.float64) - hi).astype(np.float32))",
+                        "    lo = bf16_round((x.astype(np.float64) - hi).astype(np.float32)).astype(np.float64)"),
+    "dequant_fp16_two_planes_lo_sign": ("    return ((rh + rl) + 1j * (ih + il)) / s",
+                                        "    return ((rh + rl) + 1j * (ih - il)) / s"),
 }
 
 
