@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="precision",
-                    choices=["precision", "plain", "tiny", "batching", "streaming", "displacement", "knee",
+                    choices=["precision", "plain", "tiny", "batching", "streaming", "displacement", "knee", "h2d",
                              "dynamic", "splitk"])
     ap.add_argument("--rows-cap", type=int, default=None, help="batching: cap on the rows sampled per job")
     ap.add_argument("--rows-scale", type=float, default=1 / 16,
@@ -57,7 +57,7 @@ def parse():
                     help="batching: skip running every job separately on the FP32 path")
     ap.add_argument("--jobs", type=int, default=64, help="batching: number of MPS")
     ap.add_argument("--precision", default=None,
-                    choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4", "fp8x1", "fp8x2"])
+                    choices=["fp32", "bf16x2", "bf16x3", "bf16x3l", "bf16x4", "fp8x1", "fp8x2", "fp16x2", "fp16x3"])
     ap.add_argument("--macro", type=int, default=None, help="rows per step (macro-batch)")
     ap.add_argument("--sites", type=int, default=None,
                     help="shorter chain of the same shape (for profiling captures; not a benchmark config)")
@@ -177,7 +177,19 @@ class ClockSampler:
 CONTRACT_TRAFFIC = {
     ("precision", "bf16x2", "separate", 0): (2.89e9, "profiles/tc_contract_precision_bf16x2.md"),
     ("plain", "bf16x2", "separate", 0): (1.287e9, "profiles/tc_contract_plain_bf16x2.md"),
-    ("precision", "fp16x2", "separate", 4): (2.99e9, "profiles/tc_contract_precision_fp16x2_promoted.md"),
+    ("precision", "fp16x2", "separate", 4): (2.85e9, "profiles/tc_contract_precision_fp16x2_promoted.md"),
+}
+
+
+# Conditional-probability error of the path on the precision workload (1024 replayed rows, every site),
+# from the committed parity runs: against the FP64 oracle on the tensors the store represents (the
+# gate), the storage error of the store itself, and the device against the oracle on the original
+# complex64 tensors.  Keyed by (workload, precision, accumulation chunk).
+ACCURACY = {
+    ("precision", "fp16x2", 4): {"max_err_vs_store": 3.85e-5, "storage_error": 6.35e-3, "max_err_vs_original": 6.36e-3},
+    ("precision", "fp16x3", 4): {"max_err_vs_store": 4.52e-5, "storage_error": 1.83e-6, "max_err_vs_original": 1.72e-5},
+    ("precision", "fp32", 0): {"max_err_vs_store": 9.55e-6, "storage_error": 0.0, "max_err_vs_original": 9.55e-6},
+    ("precision", "bf16x2", 0): {"max_err_vs_store": 3.18e-4, "storage_error": 7.21e-2, "max_err_vs_original": 7.21e-2},
 }
 
 
@@ -393,6 +405,10 @@ def run_ours(args, rank, ws, local):
         "roofline": roof, "gpu_launches": launches, "clocks": clk,
         "setup_s": {"generate": t_gen, "load": t_load},
     }
+    acc = ACCURACY.get((args.workload, precision, accum)) if not args.sites else None
+    if acc:
+        line["accuracy"] = dict(acc, rows=1024, tolerance=1e-5 if precision == "fp32" else 1e-4,
+                                source="profiles/precision_parity.md")
 
     if mu is not None:
         # displaced measurement: reads the whole FP32 row (d blocks of 2 chi_r), the amplitude, writes the
@@ -842,11 +858,72 @@ def run_splitk(args, rank, ws, local):
             "peak": float(peaks.get("bf16_tflops_sustained", 1700.0)), "peak_source": src, "points": results}
 
 
+def run_h2d(args, rank, ws, local):
+    """Link evidence for the streaming engine (Sec. 3.1 I/O overlap): the pinned-host to device copy rate
+    of one 1.2 GB site tensor (the BF16 size of a chi = 1e4, d = 3 site) alone, in 64 MB pieces, for a
+    pool of 16 distinct pinned buffers, from pageable memory, and while a saturating tensor-core GEMM runs
+    on another stream.  Plain copies and a library GEMM only: it measures the link, not the library."""
+    import torch
+
+    torch.cuda.set_device(local)
+    nbytes = 1_200_000_000
+    host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    host.fill_(1)
+    dev = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{local}")
+    cs = torch.cuda.Stream(device=local)
+
+    def timed(src, piece=None):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(cs):
+            e0.record(cs)
+            if piece is None:
+                dev.copy_(src, non_blocking=True)
+            else:
+                for o in range(0, nbytes, piece):
+                    dev[o:o + piece].copy_(src[o:o + piece], non_blocking=True)
+            e1.record(cs)
+        e1.synchronize()
+        return nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    for _ in range(max(1, args.warmup)):
+        timed(host)
+    out = {"alone_GBps": max(timed(host) for _ in range(3)),
+           "alone_64MB_pieces_GBps": max(timed(host, 64 << 20) for _ in range(3))}
+    a = torch.randn(8192, 8192, dtype=torch.bfloat16, device=f"cuda:{local}")
+    b = torch.randn(8192, 8192, dtype=torch.bfloat16, device=f"cuda:{local}")
+    for _ in range(3):
+        a @ b
+    torch.cuda.synchronize()
+    under = []
+    for _ in range(3):
+        for _ in range(60):
+            a @ b  # queued on the current stream, ~0.5 ms each
+        under.append(timed(host))
+        torch.cuda.synchronize()
+    out["under_gemm_load_GBps"] = under
+    pageable = torch.empty(nbytes // 4, dtype=torch.uint8)
+    t0 = time.perf_counter()
+    dev[: nbytes // 4].copy_(pageable)
+    torch.cuda.synchronize()
+    out["pageable_300MB_GBps"] = (nbytes // 4) / (time.perf_counter() - t0) / 1e9
+    del host
+    pool = [torch.empty(nbytes, dtype=torch.uint8, pin_memory=True) for _ in range(16)]
+    for x in pool:
+        x.fill_(2)
+    rates = [timed(x) for _ in range(2) for x in pool]
+    out["pool16_GBps_min"] = min(rates)
+    out["pool16_GBps_mean"] = sum(rates) / len(rates)
+    return {"metric": "pinned host -> device copy rate", "unit": "GB/s", "n_gpus": 1, "higher_is_better": True,
+            "value": out["alone_GBps"], "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "1.2 GB copies (one chi = 1e4, d = 3 site tensor in BF16)"}, "h2d": out}
+
+
 def main():
     args = parse()
     rank, ws, local = dist_setup()
-    if args.workload in ("knee", "dynamic", "splitk") and args.impl == "ours":
-        line = {"knee": run_knee, "dynamic": run_dynamic, "splitk": run_splitk}[args.workload](args, rank, ws, local)
+    if args.workload in ("knee", "dynamic", "splitk", "h2d") and args.impl == "ours":
+        line = {"knee": run_knee, "dynamic": run_dynamic, "splitk": run_splitk,
+                "h2d": run_h2d}[args.workload](args, rank, ws, local)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

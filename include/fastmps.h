@@ -76,6 +76,12 @@ extern "C" {
  * fastmps_sample, fastmps_sample_ex and fastmps_sample_traced only (not batched, displaced or
  * allocation-free sampling). */
 #define FASTMPS_FP16X2 7
+/* V0 B0 + V1 B0 + V0 B1 with FP16 operands: as FP16X2, with the site tensor kept as two binary16
+ * planes at the same per-site scale (B0 = fp16(A 2^a), B1 = fp16(A 2^a - B0), ~22 significant bits),
+ * so that the 16-bit store no longer moves the conditionals of long chains (the storage error of one
+ * binary16 plane reaches several 1e-3 at the end of a 1024-site chain); 3 products.  Same entry points
+ * as FP16X2. */
+#define FASTMPS_FP16X3 8
 
 /* Where site tensors live between uses (Sec. 3.1: I/O overlapped by a double buffer). */
 #define FASTMPS_RESIDENT_HBM 0    /* repacked once at load time, kept in device memory */
@@ -88,8 +94,9 @@ extern "C" {
 #define FASTMPS_C128 1  /* interleaved complex double (re, im) */
 
 typedef struct fastmps_options {
-    int precision;          /* FASTMPS_FP32 | FASTMPS_BF16X2 | _BF16X3 | _BF16X3L | _BF16X4 | _FP8X1 | _FP8X2 */
-    int residency;          /* FASTMPS_RESIDENT_HBM | FASTMPS_HOST_STREAM (BF16 modes only) */
+    int precision;          /* FASTMPS_FP32 | _BF16X2 | _BF16X3 | _BF16X3L | _BF16X4 | _FP8X1 | _FP8X2 | _FP16X2 |
+                               _FP16X3 */
+    int residency;          /* FASTMPS_RESIDENT_HBM | FASTMPS_HOST_STREAM (BF16 and FP16 modes only) */
     int64_t max_microbatch; /* rows per contraction launch; 0 = chosen from free memory */
     int autotune;           /* 1: time the candidate tile shapes once per new shape */
     void *stream;           /* cudaStream_t to run on; NULL = a stream owned by the handle */

@@ -32,7 +32,8 @@ __all__ = [
 OK = 0
 ERR_NAMES = {-1: "INVALID_ARG", -2: "SHAPE", -3: "NOT_LOADED", -4: "OOM", -5: "CUDA", -6: "TIMEOUT",
              -7: "UNSUPPORTED", -8: "NUMERIC"}
-PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16x3": 2, "bf16x3l": 3, "bf16x4": 4, "fp8x1": 5, "fp8x2": 6, "fp16x2": 7}
+PRECISIONS = {"fp32": 0, "bf16x2": 1, "bf16x3": 2, "bf16x3l": 3, "bf16x4": 4, "fp8x1": 5, "fp8x2": 6, "fp16x2": 7,
+              "fp16x3": 8}
 RESIDENCIES = {"hbm": 0, "host_stream": 1}
 MEASUREMENTS = {"separate": 0, "cta": 1, "cluster": 2}
 C64, C128 = 0, 1

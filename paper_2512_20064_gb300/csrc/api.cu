@@ -170,7 +170,9 @@ int cuda_fail(fastmps_handle h, cudaError_t e, const char *what) {
 // Tensor-core precision modes (BF16 split planes or FP8); FP32 is the SIMT path.
 bool is_bf16(const fastmps_handle h) { return h->opt.precision != FASTMPS_FP32; }
 bool is_fp8(const fastmps_handle h) { return h->opt.precision == FASTMPS_FP8X1 || h->opt.precision == FASTMPS_FP8X2; }
-bool is_f16(const fastmps_handle h) { return h->opt.precision == FASTMPS_FP16X2; }
+bool is_f16(const fastmps_handle h) {
+    return h->opt.precision == FASTMPS_FP16X2 || h->opt.precision == FASTMPS_FP16X3;
+}
 
 // Planes of the split-precision operands and the products accumulated per precision mode.
 struct PrecisionPlan {
@@ -187,6 +189,7 @@ PrecisionPlan plan_of(int precision) {
         case FASTMPS_FP8X1: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
         case FASTMPS_FP8X2: return {2, 1, 2, {0, 1, 0, 0}, {0, 0, 0, 0}};
         case FASTMPS_FP16X2: return {2, 1, 2, {0, 1, 0, 0}, {0, 0, 0, 0}};
+        case FASTMPS_FP16X3: return {2, 2, 3, {0, 1, 0, 0}, {0, 0, 1, 0}};
         default: return {1, 1, 1, {0, 0, 0, 0}, {0, 0, 0, 0}};
     }
 }
@@ -276,6 +279,14 @@ inline uint16_t host_f16_bits(float x) {
         he += 1u;
     }
     return (uint16_t)(sign | (he << 10) | (m & 0x3FFu));
+}
+
+// binary16 bits -> float (exact; finite inputs)
+inline float host_f16_float(uint16_t b) {
+    const int e = (b >> 10) & 0x1F;
+    const float m = (float)(b & 0x3FF);
+    const float v = e == 0 ? std::ldexp(m, -24) : std::ldexp(1024.f + m, e - 25);
+    return (b & 0x8000u) ? -v : v;
 }
 
 inline float host_bf16_float(uint16_t b) {
@@ -515,7 +526,12 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
             float amax = 0.f;
             for (int64_t i = 0; i < n2; ++i) amax = std::max(amax, std::fabs(value(i)));
             t.fp8_scale = amax > 0.f ? (float)std::exp2(std::floor(std::log2(32768.0 / (double)amax))) : 1.f;
-            for (int64_t i = 0; i < n2; ++i) dst[i] = host_f16_bits(value(i) * t.fp8_scale);
+            for (int64_t i = 0; i < n2; ++i) {
+                const float x = value(i) * t.fp8_scale;  // exact: a power-of-two scale
+                const uint16_t hb = host_f16_bits(x);
+                dst[i] = hb;
+                if (t.planes > 1) dst[n2 + i] = host_f16_bits(x - host_f16_float(hb));
+            }
             return FASTMPS_OK;
         }
         for (int64_t i = 0; i < n2; ++i) {
@@ -553,17 +569,21 @@ int load_tensor(fastmps_handle h, Tensor &t, int chi_l, int d, int chi_r, const 
         t.tmB[1] = t.tmB[0];
     } else if (is_f16(h)) {
         // per-site power-of-two scale that puts the largest |Re|, |Im| in [16384, 32768]
-        if (!t.B_hi.ensure(op_elems * 2) || !h->err.ensure(256)) return fail(h, FASTMPS_ERR_OOM, "allocation failed");
+        const bool two = plan_of(h->opt.precision).b_planes > 1;
+        if (!t.B_hi.ensure(op_elems * 2) || (two && !t.B_lo.ensure(op_elems * 2)) || !h->err.ensure(256))
+            return fail(h, FASTMPS_ERR_OOM, "allocation failed");
         float amax = 0.f;
         launch_absmax(h->staging.p, dtype == FASTMPS_C128, nelem, h->err.as<float>(), h->stream);
         e = cudaMemcpyAsync(&amax, h->err.p, sizeof(float), cudaMemcpyDeviceToHost, h->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "site tensor maximum");
         t.fp8_scale = amax > 0.f ? (float)std::exp2(std::floor(std::log2(32768.0 / (double)amax))) : 1.f;
-        launch_repack_f16(h->staging.p, dtype == FASTMPS_C128, t.L, t.fp8_scale, t.B_hi.as<uint16_t>(), h->stream);
-        if (!encode_2d_f16(&t.tmB[0], t.B_hi.p, t.L.K_pad, t.L.ncols, t.L.K_pad, 64, t.L.bn))
+        launch_repack_f16(h->staging.p, dtype == FASTMPS_C128, t.L, t.fp8_scale, t.B_hi.as<uint16_t>(),
+                          two ? t.B_lo.as<uint16_t>() : nullptr, h->stream);
+        if (!encode_2d_f16(&t.tmB[0], t.B_hi.p, t.L.K_pad, t.L.ncols, t.L.K_pad, 64, t.L.bn) ||
+            (two && !encode_2d_f16(&t.tmB[1], t.B_lo.p, t.L.K_pad, t.L.ncols, t.L.K_pad, 64, t.L.bn)))
             return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
-        t.tmB[1] = t.tmB[0];
+        if (!two) t.tmB[1] = t.tmB[0];
     } else if (is_bf16(h)) {
         if (tune) {
             std::lock_guard<std::mutex> lock(g_tune_mutex);
@@ -867,9 +887,11 @@ int run_sample(fastmps_handle h, int M, int d, const int *bonds, int64_t n0, int
                 cudaEventRecord(h->slot_free[cur], st);
                 Bh = h->slot_hi.as<__nv_bfloat16>();
                 Bl = lo;
-                const bool mapped = is_f16(h) ? encode_2d_f16(&ta.tmB[0], Bh, L.K_pad, L.ncols, L.K_pad, 64, L.bn)
-                                              : encode_2d_bf16(&ta.tmB[0], Bh, L.K_pad, L.ncols, L.K_pad, 64, L.bn);
-                if (!mapped || (Bl && !encode_2d_bf16(&ta.tmB[1], Bl, L.K_pad, L.ncols, L.K_pad, 64, L.bn)))
+                auto map16 = [&](CUtensorMap *m, const void *base) {
+                    return is_f16(h) ? encode_2d_f16(m, base, L.K_pad, L.ncols, L.K_pad, 64, L.bn)
+                                     : encode_2d_bf16(m, base, L.K_pad, L.ncols, L.K_pad, 64, L.bn);
+                };
+                if (!map16(&ta.tmB[0], Bh) || (Bl && !map16(&ta.tmB[1], Bl)))
                     return fail(h, FASTMPS_ERR_CUDA, "tensor map encoding failed");
                 if (!Bl) ta.tmB[1] = ta.tmB[0];
             } else {
@@ -1083,7 +1105,7 @@ int fastmps_create(fastmps_handle *out, int device, const fastmps_options *opt) 
     fastmps_options o;
     fastmps_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_FP16X2) {
+    if (o.precision < FASTMPS_FP32 || o.precision > FASTMPS_FP16X3) {
         g_create_error = "unknown precision";
         return FASTMPS_ERR_INVALID_ARG;
     }

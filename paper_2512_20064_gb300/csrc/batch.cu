@@ -134,7 +134,7 @@ extern "C" int fastmps_sample_batch(fastmps_handle runner, int count, const fast
     *stats = fastmps_stats{};
     if (count < 0 || (count > 0 && !jobs)) return set_error(runner, FASTMPS_ERR_INVALID_ARG, "bad job table");
     if (rv.precision == FASTMPS_FP32 || rv.precision == FASTMPS_FP8X1 || rv.precision == FASTMPS_FP8X2 ||
-        rv.precision == FASTMPS_FP16X2)
+        rv.precision == FASTMPS_FP16X2 || rv.precision == FASTMPS_FP16X3)
         return set_error(runner, FASTMPS_ERR_UNSUPPORTED, "batched sampling runs the BF16 tensor-core modes");
     char msg[256];
     int a_planes, b_planes, nprod, pa[kMaxProducts], pb[kMaxProducts];

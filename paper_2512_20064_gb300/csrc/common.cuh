@@ -309,6 +309,18 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
                  : "memory");
 }
 
+// Per-warpgroup register budget (every warp of the warpgroup executes the same instruction).  An
+// increase waits until the block's pool -- threads x registers per thread at launch -- holds enough
+// registers released by decreases, so the shares must sum to at most the launch total.
+template <uint32_t kRegs>
+__device__ __forceinline__ void setmaxnreg_dec() {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegs));
+}
+template <uint32_t kRegs>
+__device__ __forceinline__ void setmaxnreg_inc() {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegs));
+}
+
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // 32 lanes x 32 columns of 32-bit words: thread i of the warp gets lane (base + i), 32 consecutive columns.

@@ -132,7 +132,8 @@ __global__ void repack_e4m3_kernel(const void *__restrict__ src, int is_f64, int
 }
 
 __global__ void repack_f16_kernel(const void *__restrict__ src, int is_f64, int chi_l, int d, int chi_r, int Cs,
-                                  int ncols, int K_pad, float scale, uint16_t *__restrict__ B16) {
+                                  int ncols, int K_pad, float scale, uint16_t *__restrict__ B16,
+                                  uint16_t *__restrict__ B16_lo) {
     const int64_t total = (int64_t)ncols * K_pad;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(i / K_pad);
@@ -140,7 +141,10 @@ __global__ void repack_f16_kernel(const void *__restrict__ src, int is_f64, int 
         const StackedPos q = stacked_pos(c, kappa, chi_l, d, chi_r, Cs);
         float x = 0.f;
         if (!q.zero) x = q.sign * load_part(src, is_f64, q.cidx, q.re_part ? 0 : 1);
-        B16[i] = __half_as_ushort(__float2half_rn(x * scale));
+        const float xs = x * scale;  // exact: a power-of-two scale
+        const __half hi = __float2half_rn(xs);
+        B16[i] = __half_as_ushort(hi);
+        if (B16_lo) B16_lo[i] = __half_as_ushort(__float2half_rn(xs - __half2float(hi)));  // the residual is exact
     }
 }
 
@@ -185,10 +189,10 @@ void launch_repack_e4m3(const void *src, int is_f64, const SiteLayout &L, float 
 }
 
 void launch_repack_f16(const void *src, int is_f64, const SiteLayout &L, float scale, uint16_t *B16,
-                       cudaStream_t st) {
+                       uint16_t *B16_lo, cudaStream_t st) {
     const int64_t total = (int64_t)L.ncols * L.K_pad;
     repack_f16_kernel<<<grid_for(total, 256), 256, 0, st>>>(src, is_f64, L.chi_l, L.d, L.chi_r, L.Cs, L.ncols,
-                                                             L.K_pad, scale, B16);
+                                                             L.K_pad, scale, B16, B16_lo);
 }
 
 void launch_absmax(const void *src, int is_f64, int64_t n_complex, float *out_dev, cudaStream_t st) {

@@ -37,9 +37,10 @@ void launch_repack_e4m3(const void *src, int is_f64, const SiteLayout &L, float 
                         cudaStream_t st);
 // Largest |Re| or |Im| of an interleaved complex tensor (as float), into *out_dev (zeroed first).
 void launch_absmax(const void *src, int is_f64, int64_t n_complex, float *out_dev, cudaStream_t st);
-// FP16 operand B[c][kappa] (K-major, ld = K_pad) of value * scale (scale a power of two), binary16 bits.
+// FP16 operand B[c][kappa] (K-major, ld = K_pad) of value * scale (scale a power of two), binary16 bits;
+// B16_lo (optional) receives the rounding residual fp16(value * scale - B16).
 void launch_repack_f16(const void *src, int is_f64, const SiteLayout &L, float scale, uint16_t *B16,
-                       cudaStream_t st);
+                       uint16_t *B16_lo, cudaStream_t st);
 // FP32 SIMT operand: Bt[kappa][c] (N-major, ld = ncols), float.
 void launch_repack_f32(const void *src, int is_f64, const SiteLayout &L, float *Bt, cudaStream_t st);
 

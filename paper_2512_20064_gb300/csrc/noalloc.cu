@@ -100,7 +100,8 @@ extern "C" int fastmps_sample_noalloc(fastmps_handle h, int M, int d, const int 
         return set_error(h, FASTMPS_ERR_SHAPE, "bond_dims[0] and bond_dims[M] must be 1");
     if (hv.residency != FASTMPS_RESIDENT_HBM)
         return set_error(h, FASTMPS_ERR_UNSUPPORTED, "fastmps_sample_noalloc needs resident site tensors");
-    if (hv.precision == FASTMPS_FP8X1 || hv.precision == FASTMPS_FP8X2 || hv.precision == FASTMPS_FP16X2)
+    if (hv.precision == FASTMPS_FP8X1 || hv.precision == FASTMPS_FP8X2 || hv.precision == FASTMPS_FP16X2 ||
+        hv.precision == FASTMPS_FP16X3)
         return set_error(h, FASTMPS_ERR_UNSUPPORTED, "fastmps_sample_noalloc runs FP32 and the BF16 modes");
     if (N > 0 && ((out_samples && !device_pointer(out_samples)) || (out_logprob && !device_pointer(out_logprob))))
         return set_error(h, FASTMPS_ERR_INVALID_ARG, "fastmps_sample_noalloc writes device memory only");

@@ -75,7 +75,17 @@ constexpr int kMaxClusterCTAs = 16;          // largest (non-portable) cluster
 constexpr uint32_t kClusterBytes = 64 + 4 * 128 * 4 * 2;  // 4 mbarriers + partial sums [2][T <= 4][128]
 
 enum TcMode : int { kTwoPass = 0, kFusedCta = 1, kClusterFused = 2, kSplitK = 3, kPromoted = 4 };
-constexpr int kThreadsPromoted = 320;        // TMA + MMA + 8 epilogue warps (two per lane quarter)
+// Promoted accumulation: warpgroup 0 = TMA, MMA and two idle warps; warpgroups 1 and 2 = 8 epilogue
+// warps (two per tensor-memory lane quarter), each thread keeping a 128-column FP32 running sum.  Three
+// warps per SM sub-partition cap the launch at 168 registers per thread; warpgroup 0 returns registers
+// so that the epilogue warps can hold their sums without spilling.
+constexpr int kThreadsPromoted = 384;
+constexpr int kPromoRegsLaunch = 168;        // 65536 / (3 warps x 32 threads x 4 sub-partitions), rounded to 8
+constexpr int kPromoRegsCtl = 72;            // warpgroup 0 after setmaxnreg.dec
+constexpr int kPromoRegsEpi = 216;           // warpgroups 1 and 2 after setmaxnreg.inc
+static_assert(kPromoRegsCtl * 128 + kPromoRegsEpi * 256 <= kPromoRegsLaunch * kThreadsPromoted,
+              "register shares exceed the launch total");
+static_assert((kPromoRegsCtl + 2 * kPromoRegsEpi) * 32 <= 16384, "one sub-partition's register file");
 
 struct TcParams {
     int num_m_tiles, num_n_tiles, num_k_blocks, bn;
@@ -457,9 +467,9 @@ __device__ __forceinline__ void promoted_epilogue(const TcParams &p, const CUten
                                                   uint64_t *tfull, uint64_t *tempty, uint8_t *ystage, float *ss_hi,
                                                   volatile int *abort_flag, int warp, int lane) {
     const int quad = warp & 3;
-    const int half = (warp - 2) >> 2;        // 0: columns 0..127 of the tile, 1: columns 128..255
+    const int half = (warp - 4) >> 2;        // 0: columns 0..127 of the tile, 1: columns 128..255
     const int rl = quad * 32 + lane;
-    const int elected = half == 0 ? 64 : 192;  // first thread of each half
+    const int elected = half == 0 ? 128 : 256;  // first thread of each half
     const int nch = (p.num_k_blocks + p.kchunk - 1) / p.kchunk;
     uint8_t *sb = ystage + (uint32_t)half * kYStageBytes;  // this half's staging buffer
     uint32_t cq = 0;  // chunks consumed (buffer cq % 2)
@@ -478,20 +488,30 @@ __device__ __forceinline__ void promoted_epilogue(const TcParams &p, const CUten
             const uint32_t taddr =
                 tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)buf * kAccStride + (uint32_t)(half * 128);
 #pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                uint32_t r[16];
-                tmem_ld_32x32b_x16(taddr + (uint32_t)(g * 16), r);
+            for (int g = 0; g < 4; g += 2) {
+                // two 32-column loads in flight per wait
+                uint32_t r0[32], r1[32];
+                tmem_ld_32x32b_x32(taddr + (uint32_t)(g * 32), r0);
+                tmem_ld_32x32b_x32(taddr + (uint32_t)(g * 32 + 32), r1);
                 tc_wait_ld();
                 if (c == 0) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[g * 16 + j] = __uint_as_float(r[j]);
+                    for (int j = 0; j < 32; ++j) {
+                        acc[g * 32 + j] = __uint_as_float(r0[j]);
+                        acc[g * 32 + 32 + j] = __uint_as_float(r1[j]);
+                    }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) acc[g * 16 + j] += __uint_as_float(r[j]);
+                    for (int j = 0; j < 32; ++j) {
+                        acc[g * 32 + j] += __uint_as_float(r0[j]);
+                        acc[g * 32 + 32 + j] += __uint_as_float(r1[j]);
+                    }
                 }
             }
+            // the warp's tensor-memory reads are complete: one arrive per warp frees the buffer
             tc_fence_before();
-            mbar_arrive(&tempty[buf]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
         }
         const int row = mt * kBM + rl;
         float ss = 0.f;
@@ -567,7 +587,7 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
         }
         for (int b = 0; b < 4; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kPromo ? 256 : 128);
+            mbar_init(&tempty[b], kPromo ? 8 : 128);  // promoted: one arrive per epilogue warp
         }
         mbar_init(drain, 1);
         for (int r = 0; r < kRing; ++r) {
@@ -607,10 +627,9 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
     if (kCluster || kSplit) cluster_sync_all();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-
-    if (warp == 0) {
+    // ---------------- TMA producer (warp 0) ----------------
+    auto run_producer = [&]() {
         if (lane == 0) {
-            // ---------------- TMA producer ----------------
             int stage = 0;
             uint32_t phase = 0;
             int last_parity[kMaxStages];
@@ -649,9 +668,10 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             }
         }
         __syncwarp();
-    } else if (warp == 1) {
+    };
+    // ---------------- MMA issuer (warp 1) ----------------
+    auto run_mma = [&]() {
         if (lane == 0) {
-            // ---------------- MMA issuer ----------------
             int stage = 0;
             uint32_t phase = 0;
             int lt = 0;
@@ -733,12 +753,28 @@ tc_contract_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_consta
             }
         }
         __syncwarp();
+    };
+
+    if (kPromo) {
+        // each warpgroup sets its register budget before its warps take their roles
+        if (warp < 4) {
+            setmaxnreg_dec<kPromoRegsCtl>();
+            if (warp == 0)
+                run_producer();
+            else if (warp == 1)
+                run_mma();
+        } else {
+            setmaxnreg_inc<kPromoRegsEpi>();
+            // ---------------- promoted-accumulation epilogue: warps 4..11 ----------------
+            promoted_epilogue(p, &tmY, tmem_base, tfull, tempty, ystage, m_scale, abort_flag, warp, lane);
+        }
+    } else if (warp == 0) {
+        run_producer();
+    } else if (warp == 1) {
+        run_mma();
     } else if (kCluster && warp < 6) {
         // ---------------- cluster epilogue: warps 2..5 ----------------
         cluster_epilogue(p, tmem_base, tfull, tempty, pready, pfree, part, abort_flag, warp, lane);
-    } else if (kPromo) {
-        // ---------------- promoted-accumulation epilogue: warps 2..9 ----------------
-        promoted_epilogue(p, &tmY, tmem_base, tfull, tempty, ystage, m_scale, abort_flag, warp, lane);
     } else if (kSplit && warp < 6) {
         // ---------------- split-K epilogue: warps 2..5 ----------------
         splitk_epilogue(p, &tmY, tmem_base, tfull, tempty, pready, pfree, ystage, abort_flag, warp, lane);
@@ -1212,6 +1248,16 @@ cudaError_t launch_contract_tc_promoted(const TcArgs &a, const SiteLayout &L, co
     auto kern = tc_contract_kernel<kPromoted, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e != cudaSuccess) return e;
+    // the epilogue warpgroups' register increase is served from the launch's own registers: refuse a
+    // build whose launch count would leave the increase waiting
+    static int regs = -1;
+    if (regs < 0) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, kern);
+        if (e != cudaSuccess) return e;
+        regs = fa.numRegs;
+    }
+    if (regs * kThreadsPromoted < kPromoRegsCtl * 128 + kPromoRegsEpi * 256) return cudaErrorInvalidConfiguration;
     const int grid = tiles < num_sms ? tiles : num_sms;
     const CUtensorMap &a1 = a.tmA[a.a_planes > 1 ? 1 : 0], &a2 = a.tmA[a.a_planes > 2 ? 2 : 0];
     const CUtensorMap &b1 = a.tmB[a.b_planes > 1 ? 1 : 0];
