@@ -268,12 +268,16 @@ int fastmps_sample_noalloc(fastmps_handle h, int M, int d, const int *bond_dims,
  * Each job names a handle `chain` whose sites hold that MPS (loaded with
  * fastmps_load_site / fastmps_load_pool); every chain must live on the
  * runner's device and use the runner's precision (a BF16 mode) with resident
- * tensors.  The runner executes all jobs together: at every "round" each
- * active job advances one site for one chunk of its rows, and one grouped
- * tcgen05 contraction launch plus one grouped measurement launch serve all
- * jobs of the round.  The whole sequence of rounds is captured into a CUDA
- * graph on the first call with a given job table and replayed by later calls
- * with the same table (same chains, shapes, rows, seeds and output pointers).
+ * tensors.  Each job's rows are taken in chunks and every chunk through all
+ * of the job's sites; one persistent tcgen05 kernel runs every (job, chunk,
+ * site) step of the call, handing out 128-row tiles from a device work queue
+ * and ordering the steps of each 128-row block of a job with bounded waits on
+ * per-block step counters, so that different jobs (and different row blocks
+ * of one job) advance independently.  The call's launches are captured into a
+ * CUDA graph on the first call with a given job table and replayed by later
+ * calls with the same table (same chains, shapes, rows, seeds and output
+ * pointers).  A dependency wait that runs out gives FASTMPS_ERR_TIMEOUT and
+ * leaves the runner usable.
  * Per job: rows n0 .. n0+N-1, Philox counter word `job`; outputs as in
  * fastmps_sample_ex (host or device, or NULL).  Statistics of the call are
  * available from the runner with fastmps_get_stats.

@@ -1,4 +1,4 @@
-// Read-only views of a handle's state for entry points implemented outside api.cu (internal).
+// Read-only views of a handle's state for entry points compiled outside the handle's own units (internal).
 #pragma once
 
 #include <cuda.h>

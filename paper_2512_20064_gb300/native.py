@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfastmps.so")
-SOURCES = ["api.cu", "kernels.cu", "tc_contract.cu", "noalloc.cu", "tc_grouped.cu", "batch.cu", "gbs.cu", "bond_filter.cu"]
-HEADERS = ["common.cuh", "launch.h", "handle_view.h", "measure.cuh"]
+SOURCES = ["api.cu", "runtime.cu", "loader.cu", "engine.cu", "kernels.cu", "tc_contract.cu", "noalloc.cu", "tc_grouped.cu", "batch.cu", "gbs.cu", "bond_filter.cu"]
+HEADERS = ["common.cuh", "launch.h", "handle_view.h", "measure.cuh", "context.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I" + os.path.join(ROOT, "include")]
