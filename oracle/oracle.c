@@ -324,8 +324,16 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
     if (vstate && ldv < chi) return -1;
     int bad = 0;
     enum { B = ORC_BATCH };
+    /* rows per batch: ORC_BATCH, or fewer when the rows would not keep every thread busy (a batch's
+     * sums are those of its samples taken one by one, so the batch size changes no result) */
+    int64_t bsz = B;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
+    {
+        const int64_t nth = (int64_t)omp_get_max_threads();
+        const int64_t per = nth > 0 ? (N + nth - 1) / nth : (int64_t)B;
+        if (per < bsz) bsz = per < 1 ? 1 : per;
+    }
 #pragma omp parallel reduction(| : bad)
 #endif
     {
@@ -339,9 +347,9 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
-        for (int64_t i0 = 0; i0 < N; i0 += B) {
+        for (int64_t i0 = 0; i0 < N; i0 += bsz) {
             if (bad) continue;
-            const int nb = (int)(N - i0 < B ? N - i0 : B);
+            const int nb = (int)(N - i0 < bsz ? N - i0 : bsz);
             double lps[B];
             int deads[B];
             double *vr_[B], *yr_[B];

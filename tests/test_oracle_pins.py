@@ -127,6 +127,21 @@ def test_thread_count_independent():
     assert np.array_equal(s1, s2) and np.array_equal(l1, l2)
 
 
+def test_row_batching_changes_no_result():
+    """Rows are contracted in batches of up to 8 per thread, fewer when the rows would not keep every
+    thread busy; a row's sums do not depend on its batch, so 24 rows with 1, 6 and 24 threads (batches of
+    8, 4 and 1 rows) give bitwise the same outcomes, log-probabilities, conditionals and replays."""
+    b, ts = P._tiny()
+    runs = [oracle.sample(b, ts, 42, 24, want_probs=True, nthreads=t) for t in (1, 6, 24)]
+    for smp, lp, pr in runs[1:]:
+        assert np.array_equal(smp, runs[0][0]) and np.array_equal(lp, runs[0][1]) and np.array_equal(pr, runs[0][2])
+    rows = np.arange(3, 24, 2)
+    reps = [oracle.replay(b, ts, 42, rows, runs[0][0][rows], nthreads=t) for t in (1, 5, 16)]
+    for r in reps[1:]:
+        for key in ("probs", "own", "margin", "logprob"):
+            assert np.array_equal(r[key], reps[0][key]), key
+
+
 def test_pool_site_index():
     b, ts, idx = gen.mps_tensors(40, 3, 9, base_seed=4, pool=4)
     assert len(ts) < 40
