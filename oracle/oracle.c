@@ -101,12 +101,19 @@ double orc_uniform(uint64_t seed, uint64_t n, uint32_t k, uint32_t job)
 /* For every sample r of a batch (Algorithm 2 contracts the left environments
  * of a whole batch of samples with the site tensor at once):
  * y_r[s*chi_r + b] (interleaved re, im) = sum_a v_r[a] A[a, s, b], the sum
- * taken over a in increasing order.  Plain loops; the sample loop sits inside
- * the loop over a only so that a row of A is read once per batch -- each
- * sample's sums are the same operations in the same order as for a batch of
- * one.  A holds interleaved complex doubles (a_is_f32 = 0) or floats
+ * taken over a in increasing order.  Plain loops; the output columns are
+ * taken ORC_CBLOCK at a time, the real and imaginary parts of a block are
+ * accumulated in separate arrays, and within a block the sample loop sits
+ * inside the loop over a -- only so that a block's partial sums of the whole
+ * batch stay in the L1 cache, each entry of A is read once per batch and the
+ * compiler can use plain vector arithmetic.  Every output entry receives the
+ * same operations in the same order as in a row-at-a-time, column-at-a-time
+ * loop: starting from 0, y += (v_r * a_r - v_i * a_i) for the real part and
+ * y += (v_r * a_i + v_i * a_r) for the imaginary part, for a = 0, 1, ...
+ * A holds interleaved complex doubles (a_is_f32 = 0) or floats
  * (a_is_f32 = 1); float entries are widened exactly to double. */
 #define ORC_BATCH 8 /* samples contracted together per site (Algorithm 2's batch) */
+#define ORC_CBLOCK 128 /* output columns per block */
 
 static inline double orc_elem(const void *A, int a_is_f32, size_t i)
 {
@@ -114,27 +121,39 @@ static inline double orc_elem(const void *A, int a_is_f32, size_t i)
 }
 
 static void orc_contract(int nrows, double *const *vs, int chi_l, int d, int chi_r, const void *A, int a_is_f32,
-                         double *const *ys, double *arow)
+                         double *const *ys)
 {
     const int cols = d * chi_r;
-    for (int r = 0; r < nrows; ++r)
-        for (int c = 0; c < cols; ++c) {
-            ys[r][2 * c] = 0.0;
-            ys[r][2 * c + 1] = 0.0;
-        }
-    for (int a = 0; a < chi_l; ++a) {
-        const size_t row = (size_t)2 * a * cols;
-        /* row a of A as doubles (float entries widened exactly), read once for the batch */
-        for (int c = 0; c < 2 * cols; ++c) arow[c] = orc_elem(A, a_is_f32, row + c);
-        for (int r = 0; r < nrows; ++r) {
-            const double vr = vs[r][2 * a], vi = vs[r][2 * a + 1];
-            double *y = ys[r];
-            for (int c = 0; c < cols; ++c) {
-                const double ar = arow[2 * c], ai = arow[2 * c + 1];
-                y[2 * c] += vr * ar - vi * ai;
-                y[2 * c + 1] += vr * ai + vi * ar;
+    double ar[ORC_CBLOCK], ai[ORC_CBLOCK];
+    double yre[ORC_BATCH][ORC_CBLOCK], yim[ORC_BATCH][ORC_CBLOCK];
+    for (int c0 = 0; c0 < cols; c0 += ORC_CBLOCK) {
+        const int nc = cols - c0 < ORC_CBLOCK ? cols - c0 : ORC_CBLOCK;
+        for (int r = 0; r < nrows; ++r)
+            for (int c = 0; c < nc; ++c) {
+                yre[r][c] = 0.0;
+                yim[r][c] = 0.0;
+            }
+        for (int a = 0; a < chi_l; ++a) {
+            /* entries c0 .. c0+nc-1 of row a of A as doubles, read once for the batch */
+            const size_t row = (size_t)2 * ((size_t)a * cols + c0);
+            for (int c = 0; c < nc; ++c) {
+                ar[c] = orc_elem(A, a_is_f32, row + 2 * c);
+                ai[c] = orc_elem(A, a_is_f32, row + 2 * c + 1);
+            }
+            for (int r = 0; r < nrows; ++r) {
+                const double vr = vs[r][2 * a], vi = vs[r][2 * a + 1];
+                double *yr = yre[r], *yi = yim[r];
+                for (int c = 0; c < nc; ++c) {
+                    yr[c] += vr * ar[c] - vi * ai[c];
+                    yi[c] += vr * ai[c] + vi * ar[c];
+                }
             }
         }
+        for (int r = 0; r < nrows; ++r)
+            for (int c = 0; c < nc; ++c) {
+                ys[r][2 * (c0 + c)] = yre[r][c];
+                ys[r][2 * (c0 + c) + 1] = yim[r][c];
+            }
     }
 }
 
@@ -342,8 +361,7 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
         double *w = (double *)malloc(sizeof(double) * (size_t)d);
         double *Dm = (double *)malloc(sizeof(double) * 2 * (size_t)d * d);
         double *ytmp = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi);
-        double *arow = (double *)malloc(sizeof(double) * 2 * (size_t)d * chi);
-        if (!vbuf || !ybuf || !w || !Dm || !ytmp || !arow) bad = 1;
+        if (!vbuf || !ybuf || !w || !Dm || !ytmp) bad = 1;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 1)
 #endif
@@ -375,7 +393,7 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
                         yr_[nl] = ybuf + (size_t)j * 2 * d * chi;
                         ++nl;
                     }
-                orc_contract(nl, vr_, cl, d, cr, A[k], a_is_f32, yr_, arow);
+                orc_contract(nl, vr_, cl, d, cr, A[k], a_is_f32, yr_);
                 for (int j = 0; j < nb; ++j) {
                     const int64_t i = i0 + j;
                     const uint64_t n = nlist ? (uint64_t)nlist[i] : (uint64_t)(n0 + i);
@@ -436,7 +454,6 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
         }
         free(vbuf);
         free(ybuf);
-        free(arow);
         free(w);
         free(Dm);
         free(ytmp);

@@ -14,9 +14,34 @@ sides):
 """
 from __future__ import annotations
 
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 
 import oracle
+
+
+class Prefetch:
+    """A ``tensors(k)`` callable for a replay that asks for sites in increasing order: it computes
+    ``f(k)`` for the next ``ahead`` sites in ``workers`` threads while the oracle works on the current
+    ones (the oracle's C loop and torch's copies and casts run without the interpreter lock)."""
+
+    def __init__(self, f, M, ahead=48, workers=4):
+        self.f, self.M, self.ahead = f, M, ahead
+        self.pool = ThreadPoolExecutor(max_workers=workers)
+        self.pending = {}
+
+    def __call__(self, k):
+        for j in range(k, min(self.M, k + self.ahead)):
+            if j not in self.pending:
+                self.pending[j] = self.pool.submit(self.f, j)
+        return self.pending.pop(k).result()
+
+    def close(self):
+        for fut in self.pending.values():
+            fut.cancel()
+        self.pool.shutdown(wait=True)
+        self.pending.clear()
 
 
 def check(bonds, tensors, seed, rows, dev_samples, dev_logprob, tol, dev_trace=None, trace_rows=0,

@@ -5,7 +5,7 @@ The batching workload (64 independent MPS, M ~ U[64, 2048], d in {2, 3, 4, 6}, c
 for every job, bitwise the result of sampling that job alone in the runner's precision
 (tests/test_gpu_batch.py).  So the error of the batched path on a job is measured here by sampling the
 job alone with traced rows and replaying those rows on the oracle, on the tensors the 16-bit store
-represents.  The jobs with the largest M * chi are checked (32 traced rows of 1024 each):
+represents.  The jobs with the largest M * chi are checked (16 traced rows of 1024 each):
 
 * BF16x2 with whole-index accumulation, the arithmetic of the batched persistent kernel: its error is
   printed and bounded loosely (1e-2), not gated at 1e-4.  On chains this long the tensor cores' FP32
@@ -23,7 +23,7 @@ from oracle import quant
 pytestmark = pytest.mark.gpu
 
 N = 1024
-TRACED = 32
+TRACED = 16
 
 
 def _largest(rank):
