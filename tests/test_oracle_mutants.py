@@ -14,10 +14,10 @@ import oracle_pins as P
 SRC = os.path.join(os.path.dirname(oracle.__file__), "oracle.c")
 
 MUTANTS = {
-    "drop_imag_cross_term": ("y[2 * c] += vr * ar - vi * ai;", "y[2 * c] += vr * ar;"),
-    "imag_sign_flip": ("y[2 * c + 1] += vr * ai + vi * ar;", "y[2 * c + 1] += vr * ai - vi * ar;"),
-    "transposed_site_index": ("const size_t row = (size_t)2 * a * cols;",
-                              "const size_t row = (size_t)2 * a * (cols == chi_l ? cols : chi_r);"),
+    "drop_imag_cross_term": ("yr[c] += vr * ar[c] - vi * ai[c];", "yr[c] += vr * ar[c];"),
+    "imag_sign_flip": ("yi[c] += vr * ai[c] + vi * ar[c];", "yi[c] += vr * ai[c] - vi * ar[c];"),
+    "transposed_site_index": ("const size_t row = (size_t)2 * ((size_t)a * cols + c0);",
+                              "const size_t row = (size_t)2 * ((size_t)a * (cols == chi_l ? cols : chi_r) + c0);"),
     "no_cumulative_sum": ("        acc += w[s];\n        C[s] = acc;", "        acc += w[s];\n        C[s] = w[s];"),
     "threshold_not_scaled_by_Z": ("const double t = u * Z;", "const double t = u;"),
     "logprob_without_Z": ("lps[j] += log(w[s]) - log(Z);", "lps[j] += log(w[s]);"),
