@@ -26,7 +26,7 @@ class Prefetch:
     ``f(k)`` for the next ``ahead`` sites in ``workers`` threads while the oracle works on the current
     ones (the oracle's C loop and torch's copies and casts run without the interpreter lock)."""
 
-    def __init__(self, f, M, ahead=48, workers=4):
+    def __init__(self, f, M, ahead=64, workers=4):
         self.f, self.M, self.ahead = f, M, ahead
         self.pool = ThreadPoolExecutor(max_workers=workers)
         self.pending = {}
