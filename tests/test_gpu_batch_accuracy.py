@@ -43,7 +43,8 @@ def test_largest_batching_jobs_against_oracle(rank, precision, accum_chunk, tol)
     j, sp = _largest(rank)
     b, ts, idx = gen.mps_tensors(sp["M"], sp["d"], sp["chi"], base_seed=sp["base_seed"], skew=1.5, pool=4,
                                  device="cuda")
-    rows = np.unique(np.linspace(0, N - 1, TRACED).round().astype(np.int64))
+    # every other row of an even 32-row spread over the call
+    rows = np.unique(np.linspace(0, N - 1, 2 * TRACED).round().astype(np.int64))[::2]
     with F.Sampler(precision=precision, accum_chunk=accum_chunk) as s:
         s.load_chain(ts, site_index=idx)
         smp, lp, tr = s.sample(b, sp["d"], N, sp["sampler_seed"], job=j, trace_list=rows)

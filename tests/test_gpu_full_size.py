@@ -11,7 +11,8 @@ FASTMPS_PARITY_MODES, e.g. "bf16x2:0,bf16x3l:4,fp16x2:8" (precision:accum_chunk)
 
 Replayed rows, the same number in every micro-batch, spread over it and including its last 32 rows:
 512 for FP16x2 (128 per micro-batch) and 256 for FP32 and FP16x3, so that the whole GPU suite stays
-within a 20-minute run (one oracle replay of 1024 rows through this chain is ~3.5e13 flops).
+within a 20-minute run (one oracle replay of 1024 rows through this chain is ~3.5e13 flops).  They are
+a subset of the 1024-row selection.
 FASTMPS_PARITY_ROWS=1024 replays 1024 rows in every mode.  The device traces exactly the replayed
 rows, so every conditional of every replayed row at every site is compared (low-precision modes on the
 tensors their 16-bit store represents; FP32 on the complex64 tensors).  The printed report gives the
@@ -68,14 +69,20 @@ def store_f16(A, planes):
     return torch.complex(parts[0], parts[1]).numpy()
 
 
-def spread_rows(N, total=1024, tail=32):
-    """total rows, the same number in every micro-batch: evenly spread over it, plus its last `tail` rows."""
+def spread_rows(N, total=1024, tail=32, full=1024):
+    """total rows, the same number in every micro-batch, taken from the full-row selection: in every
+    micro-batch, rows evenly spread over it plus its last `tail` rows.  Fewer rows than `full` keep
+    the tail and an evenly strided subset of the spread rows, so a smaller replay checks a subset of
+    the rows of the full one."""
     out = []
     nb = (N + MICRO - 1) // MICRO
+    per_full = max(full, total) // nb
     per_batch = total // nb
     for j in range(nb):
         lo, hi = j * MICRO, min(N, (j + 1) * MICRO)
-        spread = np.linspace(lo, hi - tail - 1, per_batch - tail).round().astype(np.int64)
+        spread = np.linspace(lo, hi - tail - 1, per_full - tail).round().astype(np.int64)
+        if per_batch < per_full:
+            spread = spread[np.linspace(0, spread.size - 1, per_batch - tail).round().astype(np.int64)]
         out.append(np.unique(np.concatenate([spread, np.arange(hi - tail, hi)])))
     rows = np.unique(np.concatenate(out))
     assert rows.size == per_batch * len(out)

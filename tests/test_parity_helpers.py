@@ -21,6 +21,26 @@ def test_spread_rows_cover_every_microbatch_and_its_tail(N, total):
         assert np.isin(np.arange(hi - 32, hi), rows).all()
 
 
+def _spread_rows_1024(N, tail=32):
+    """The 1024-row selection as first written: per micro-batch, 1024 / nb rows evenly spread plus the tail."""
+    out = []
+    nb = (N + fs.MICRO - 1) // fs.MICRO
+    per = 1024 // nb
+    for j in range(nb):
+        lo, hi = j * fs.MICRO, min(N, (j + 1) * fs.MICRO)
+        spread = np.linspace(lo, hi - tail - 1, per - tail).round().astype(np.int64)
+        out.append(np.unique(np.concatenate([spread, np.arange(hi - tail, hi)])))
+    return np.unique(np.concatenate(out))
+
+
+@pytest.mark.parametrize("N", [1 << 17, 1 << 18])
+def test_smaller_replays_check_a_subset_of_the_1024_rows(N):
+    full = fs.spread_rows(N, 1024)
+    assert np.array_equal(full, _spread_rows_1024(N))
+    for total in (256, 512):
+        assert np.isin(fs.spread_rows(N, total), full).all(), total
+
+
 def test_default_modes_fit_their_calls():
     for name, (prec, chunk, N, total, tol, orig_tol) in fs.MODES.items():
         assert fs.spread_rows(N, total).size == total, name
