@@ -347,13 +347,13 @@ int orc_sample_segment(int M, int d, const int *bond, const void *const *A, int 
      * sums are those of its samples taken one by one, so the batch size changes no result) */
     int64_t bsz = B;
 #ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
+    /* threads of this call only (a num_threads clause leaves the process default unchanged) */
+    const int nth = nthreads > 0 ? nthreads : omp_get_max_threads();
     {
-        const int64_t nth = (int64_t)omp_get_max_threads();
         const int64_t per = nth > 0 ? (N + nth - 1) / nth : (int64_t)B;
         if (per < bsz) bsz = per < 1 ? 1 : per;
     }
-#pragma omp parallel reduction(| : bad)
+#pragma omp parallel num_threads(nth) reduction(| : bad)
 #endif
     {
         double *vbuf = (double *)malloc(sizeof(double) * 2 * (size_t)chi * B);

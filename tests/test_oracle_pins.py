@@ -127,6 +127,15 @@ def test_thread_count_independent():
     assert np.array_equal(s1, s2) and np.array_equal(l1, l2)
 
 
+def test_thread_count_of_one_call_does_not_stick():
+    """A call with an explicit thread count (the one-core CPU baseline) leaves the process's default
+    thread count, which later calls and the baseline's reported core count use, unchanged."""
+    b, ts = P._tiny()
+    before = oracle.num_threads()
+    oracle.sample(b, ts, 42, 40, nthreads=1)
+    assert oracle.num_threads() == before
+
+
 def test_row_batching_changes_no_result():
     """Rows are contracted in batches of up to 8 per thread, fewer when the rows would not keep every
     thread busy; a row's sums do not depend on its batch, so 24 rows with 1, 6 and 24 threads (batches of
